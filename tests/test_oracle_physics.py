@@ -1,0 +1,225 @@
+"""Physical checks of the FP64 oracle: the verification programme the paper
+designs (hydrostatic column, added mass of the translating disk, reflection at
+a rigid wall, wave arrival) plus the conservation laws it asserts (mass,
+momentum, energy of the non-dissipative scheme).  CPU only.
+
+Where the paper explains why a check cannot close at the production point
+(stiff equation of state, cavitation cutoff), the check runs in the reduced
+regime the paper names: reduced c0 for the hydrostatic column, cutoff lifted
+and low speed for the added mass.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import casegen
+import oracle
+
+
+def params(**kw):
+    p = casegen.base_params()
+    p.update(kw)
+    return p
+
+
+def lattice_moment(h_over_dx: float) -> float:
+    """M1 = -sum_j dx^2 x_j^2 F(r_j) over the square lattice: the discrete
+    gradient moment that sets the long-wave sound speed c0 * M1 of the
+    discretisation (1 in the continuum)."""
+    dx = 1.0
+    h = h_over_dx * dx
+    n = int(math.ceil(2 * h)) + 1
+    tot = 0.0
+    for i in range(-n, n + 1):
+        for j in range(-n, n + 1):
+            r = math.hypot(i, j)
+            if 0 < r < 2 * h:
+                tot -= dx * dx * (i * dx) ** 2 * oracle.kernel_F(r, h)
+    return tot
+
+
+# ------------------------------------------------------------- hydrostatic
+
+def _hydrostatic(c0, steps, mutation=0, L=0.03):
+    p = params(Lx=L, W=L, dx=1e-3, end_walls=1, Ng=0, c0=c0, gx=0.0, gy=-9.81)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 21)
+    B = p["rho0"] * c0 ** 2 / p["gamma"]
+    pr = p["rho0"] * 9.81 * (0.5 * p["W"] - xy[:, 1])
+    rho = p["rho0"] * (1.0 + pr / B) ** (1.0 / p["gamma"])
+    p["probes"] = [(0.5 * L, 0.0), (0.5 * L, -0.25 * L)]
+    c = oracle.OracleCase(p, xy, None, rho, mutation=mutation)
+    vmax = 0.0
+    for k in range(steps):
+        c.step()
+        if k % 50 == 0:
+            vmax = max(vmax, float(np.abs(c.fluid()["vel"]).max()))
+    pp, _ = c.probes()
+    expect = np.array([p["rho0"] * 9.81 * 0.5 * L, p["rho0"] * 9.81 * 0.75 * L])
+    # average over the last three quarters: the column keeps a slow sloshing
+    # oscillation of a few per cent that averages out
+    return vmax, pp[steps // 4:].mean(0), expect
+
+
+def test_hydrostatic_column_stays_at_rest_full_c0():
+    # at c0 = 1480 m/s the column may not move (the paper notes that this
+    # check cannot discriminate a wrong boundary: rho0 c0^2 / rho0 g H ~ 1e6)
+    vmax, _, _ = _hydrostatic(1480.0, 2000)
+    assert vmax < 1e-3
+
+
+@pytest.mark.parametrize("mutation", [0, oracle.MUT["ghost_printed_sign"]])
+def test_hydrostatic_pressure_reduced_c0(mutation):
+    # reduced c0 = 10 sqrt(g H) makes the column discriminating: the probe
+    # pressure at mid and three-quarter depth is rho0 g depth within 2 %
+    L = 0.03
+    _, got, expect = _hydrostatic(10.0 * math.sqrt(9.81 * L), 4000, mutation, L)
+    err = np.abs(got / expect - 1.0).max()
+    if mutation == 0:
+        assert err < 0.02
+    else:
+        assert err > 0.05  # the printed sign of the body-force term fails it
+
+
+# ----------------------------------------------------------------- added mass
+
+def _added_mass(a0=1e5, Ng=100, dx=1e-3, R=5e-3, T=30e-6):
+    L = 20 * R
+    p = params(Lx=L, W=L, dx=dx, wall_layers=0, Ng=Ng, R_disk=R, x_c0=0.5 * L, y_c0=0.0,
+               motion=2, a_const=a0, gx=0.0, gy=0.0, p_cav=-1e30, t_ramp=0.0)
+    xy = casegen.fluid_lattice(L, L, dx, 0.01, 5, disk=(0.5 * L, 0.0, R))
+    c = oracle.OracleCase(p, xy)
+    Fam = math.pi * R * R * p["rho0"] * a0
+    F, imp = [], 0.0
+    while c.scalars()["t"] < T:
+        dt = c.scalars()["dt"]
+        c.step()
+        s = c.scalars()
+        imp += dt * s["Fdisk_x"]
+        if s["t"] > 0.5 * T:
+            F.append(s["Fdisk_x"] / Fam)
+    return float(np.mean(F)), imp, c.diagnostics()["px"]
+
+
+def test_added_mass_force():
+    """Disk with constant acceleration a0 in a padded domain (20 R), cutoff
+    lifted, U << c0 (Section 2.9).  The planar closed form F = pi R^2 rho0 a0
+    is the incompressible limit; in a compressible planar fluid the acoustic
+    wake of the start-up adds momentum that decays only slowly, so at
+    c0 t / R ~ 5-9 the force lies above it.  Pinned: the ghost force is the
+    rate of change of fluid momentum, is linear in a0, independent of N_g
+    (the ghost line mass rho0 dx 2 pi R does not depend on it) and bracketed
+    by [1, 2.5] times the closed form (a half-factor slip, as in the 3-D
+    sphere result, or a doubled ghost mass falls outside)."""
+    F1, imp, px = _added_mass()
+    assert abs(imp - px) < 0.01 * abs(px)
+    assert 1.0 <= F1 <= 2.5
+    F2, _, _ = _added_mass(a0=2e5)
+    assert abs(F2 / F1 - 1.0) < 0.02
+    F3, _, _ = _added_mass(Ng=200)
+    assert abs(F3 / F1 - 1.0) < 0.02
+
+
+# ---------------------------------------------------- reflection and arrival
+
+def _pulse(alpha=0.02, sig=8e-3, dx=1e-3, W=0.14, y0=0.030, P0=1e6):
+    Lx = 0.06
+    p = params(Lx=Lx, W=W, dx=dx, end_walls=1, Ng=0, gx=0.0, gy=0.0, alpha=alpha)
+    xy = casegen.fluid_lattice(Lx, W, dx, 0.01, 9)
+    B = p["rho0"] * p["c0"] ** 2 / p["gamma"]
+    pr = P0 * np.exp(-0.5 * ((xy[:, 1] - y0) / sig) ** 2)
+    rho = p["rho0"] * (1.0 + pr / B) ** (1.0 / p["gamma"])
+    vel = np.zeros_like(xy)
+    vel[:, 1] = -pr / (p["rho0"] * p["c0"])          # a purely down-going simple wave
+    y1, y2 = y0 - 0.020, y0 - 0.050
+    p["probes"] = [(0.5 * Lx, y1), (0.5 * Lx, y2)]
+    c = oracle.OracleCase(p, xy, vel, rho)
+    c0 = p["c0"]
+    t_ref = (y0 + W + y2) / c0
+    while c.scalars()["t"] < t_ref + 4 * sig / c0:
+        c.step()
+    pp, t = c.probes()
+    return p, pp, t, dict(y0=y0, y1=y1, y2=y2, wall=-0.5 * W, dt=c.scalars()["dt"])
+
+
+def test_rigid_wall_reflects_fully_and_on_time():
+    """Planar 1 MPa pulse at normal incidence on a ghost wall.  The rigid
+    wall is the Z_s -> infinity limit of R_ac = (Z_s - Z_w)/(Z_s + Z_w), so
+    R -> 1 (the paper's steel value 0.92 needs a second material).  The
+    propagation loss (artificial viscosity, dispersion) is measured from the
+    incident pulse at two probes and divided out.  Arrival times follow the
+    discrete long-wave speed c0 * M1 within 2h/c0 + 2 dt."""
+    p, pp, t, g = _pulse()
+    c0 = p["c0"]
+    mid = 0.5 * ((g["y0"] - g["y2"]) / c0 + (g["y0"] - 2 * g["wall"] + g["y2"]) / c0)
+    inc = t < mid
+    P1, P2 = pp[inc, 0].max(), pp[inc, 1].max()
+    Pr = pp[~inc, 1].max()
+    lam = math.log(P1 / P2) / (g["y1"] - g["y2"])
+    extra = 2.0 * (g["y2"] - g["wall"])
+    R = Pr / (P2 * math.exp(-lam * extra))
+    assert abs(R - 1.0) <= 0.05
+    ceff = c0 * lattice_moment(p["h_over_dx"])
+    tol = 2.0 * p["h_over_dx"] * p["dx"] / c0 + 2.0 * g["dt"]
+    t_inc = t[inc][np.argmax(pp[inc, 1])]
+    t_ref = t[~inc][np.argmax(pp[~inc, 1])]
+    assert abs(t_inc - (g["y0"] - g["y2"]) / ceff) <= tol
+    assert abs(t_ref - (g["y0"] - 2 * g["wall"] + g["y2"]) / ceff) <= tol
+
+
+def test_lattice_moment_value():
+    # the discrete moment tends to 1 as h / dx grows; at h = 1.3 dx it is ~0.974
+    assert 0.96 < lattice_moment(1.3) < 0.99
+    assert abs(lattice_moment(2.0) - 1.0) < 2e-3
+
+
+# --------------------------------------------------------------- conservation
+
+def _smooth_energy(cfl, t_end, mutation=0):
+    L = 0.04
+    p = params(Lx=L, W=L, dx=1e-3, wall_layers=0, Ng=0, gx=0.0, gy=0.0, alpha=0.0,
+               mu_lam=0.0, eps_xsph=0.0, p_cav=-1e30, cfl=cfl)
+    xy = casegen.fluid_lattice(L, L, p["dx"], 0.05, 3)
+    vel = np.zeros_like(xy)
+    vel[:, 0] = 5.0 * np.sin(2 * np.pi * xy[:, 0] / L) * np.cos(np.pi * xy[:, 1] / L)
+    vel[:, 1] = 5.0 * np.cos(2 * np.pi * xy[:, 0] / L) * np.sin(np.pi * xy[:, 1] / L)
+    c = oracle.OracleCase(p, xy, vel, None, mutation=mutation)
+    d = c.diagnostics()
+    E0 = d["KE"] + d["E_el"]
+    P0 = np.array([d["px"], d["py"]])
+    while c.scalars()["t"] < t_end:
+        c.step()
+    d = c.diagnostics()
+    return (d["KE"] + d["E_el"] - E0) / E0, np.array([d["px"], d["py"]]) - P0, d
+
+
+def test_energy_conserved_without_dissipation():
+    """Without artificial viscosity, laminar viscosity, XSPH, gravity and
+    cutoff the pair forces are conservative: kinetic + Tait elastic energy is
+    constant up to the integrator's error, which falls at least as dt^2."""
+    e1, dP, d = _smooth_energy(0.2, 70e-6)
+    e2, _, _ = _smooth_energy(0.1, 70e-6)
+    assert abs(e1) < 5e-3
+    assert abs(e2) * 4.0 <= abs(e1)
+    # total momentum of the free patch stays zero up to round-off
+    assert np.abs(dP).max() < 1e-10
+    assert d["mass"] == pytest.approx(1600 * 1000.0 * 1e-6, rel=1e-14)
+
+
+def test_planted_dropped_pj_breaks_energy():
+    e, _, _ = _smooth_energy(0.2, 20e-6, oracle.MUT["drop_pj"])
+    assert abs(e) > 0.1
+
+
+def test_mass_and_count_conserved_in_impact():
+    p = casegen.config_parity()
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
+    c = oracle.OracleCase(p, xy)
+    d0 = c.diagnostics()
+    c.run(p["n_steps"])
+    d1 = c.diagnostics()
+    assert d1["mass"] == d0["mass"]
+    assert d1["n_in"] == d0["n_in"] == xy.shape[0]
+    assert np.isfinite([d1[k] for k in ("KE", "E_el", "p_max", "W_boundary")]).all()
+    assert d1["rho_min"] >= 0.5 * p["rho0"] and d1["rho_max"] <= 1.5 * p["rho0"]

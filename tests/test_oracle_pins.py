@@ -1,0 +1,372 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: quadrature,
+finite differences, an independent numpy float32 brute force, conservation
+laws the paper asserts, exact identities of the ghost operator, closed-form
+projectile kinematics, a value the paper prints, and the physical checks the
+paper designs (hydrostatic column, added mass of a translating cylinder,
+rigid-wall reflection, wave arrival).  The ``planted`` tests turn on one
+deliberate slip inside the oracle (CPU only) and assert that a pin fails.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+
+import casegen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def params(**kw):
+    p = casegen.base_params()
+    p.update(kw)
+    return p
+
+
+def fluid_only(**kw):
+    """A free patch of fluid: no walls, no disk, no gravity."""
+    base = dict(wall_layers=0, Ng=0, gx=0.0, gy=0.0, Lx=0.04, W=0.04, dx=1e-3)
+    base.update(kw)
+    return params(**base)
+
+
+# ----------------------------------------------------------------- kernel
+
+def _norm(h, mutation=0):
+    val, _ = si.quad(lambda r: oracle.kernel_W(r, h, mutation) * 2.0 * math.pi * r, 0.0, 2.0 * h,
+                     epsabs=1e-14, epsrel=1e-12, limit=200)
+    return val
+
+
+@pytest.mark.parametrize("h", [1.3e-3, 2.6e-3, 0.26e-3])
+def test_kernel_unit_mass(h):
+    # integral of W over the plane is 1 (2-D normalisation)
+    assert abs(_norm(h) - 1.0) < 1e-12
+
+
+def test_kernel_support_and_centre():
+    h = 2.6e-3
+    assert oracle.kernel_W(2.0 * h, h) == 0.0
+    assert oracle.kernel_W(2.5 * h, h) == 0.0
+    assert oracle.kernel_F(2.0 * h, h) == 0.0
+    assert math.isclose(oracle.kernel_W(0.0, h), 7.0 / (4.0 * math.pi * h * h), rel_tol=1e-15)
+    # C2 at the edge: W and dW/dr vanish as r -> 2h
+    assert oracle.kernel_W(2.0 * h * (1 - 1e-6), h) < 1e-20 / h ** 2
+
+
+@pytest.mark.parametrize("q", [0.05, 0.3, 0.7, 1.0, 1.4, 1.9])
+def test_kernel_gradient_is_derivative(q):
+    # grad_i W = F(r) r_ij  <=>  F(r) r = dW/dr ; central difference in double
+    h = 2.6e-3
+    r = q * h
+    d = 1e-6 * h
+    fd = (oracle.kernel_W(r + d, h) - oracle.kernel_W(r - d, h)) / (2 * d)
+    an = oracle.kernel_F(r, h) * r
+    assert abs(an - fd) <= 1e-7 * abs(fd)
+    assert an < 0.0
+
+
+def test_planted_kernel_mistakes_fail_pins():
+    h = 2.6e-3
+    assert abs(_norm(h, oracle.MUT["kernel_norm"]) - 1.0) > 0.1
+    r = 0.7 * h
+    d = 1e-6 * h
+    fd = (oracle.kernel_W(r + d, h) - oracle.kernel_W(r - d, h)) / (2 * d)
+    assert abs(oracle.kernel_F(r, h, oracle.MUT["grad_sign"]) * r - fd) > 0.5 * abs(fd)
+
+
+# -------------------------------------------------------------- predicate
+
+def _np_brute(xy32, s2):
+    """Independent float32 brute force with numpy (no fused operations)."""
+    x = xy32[:, 0].astype(np.float32)
+    y = xy32[:, 1].astype(np.float32)
+    dx = x[:, None] - x[None, :]
+    dy = y[:, None] - y[None, :]
+    r2 = dx * dx + dy * dy
+    assert r2.dtype == np.float32
+    m = r2 < np.float32(s2)
+    np.fill_diagonal(m, False)
+    return m
+
+
+def test_predicate_matches_numpy_float32_and_is_symmetric():
+    rng = np.random.default_rng(1)
+    s = 2 * 1.3e-3
+    s2 = np.float32(s * s)
+    xy = (rng.random((600, 2)) * 0.03).astype(np.float32)
+    m = _np_brute(xy, s2)
+    assert (m == m.T).all()
+    off, ids = oracle.brute_neighbours(xy, s2)
+    for i in range(xy.shape[0]):
+        assert np.array_equal(ids[off[i]:off[i + 1]], np.nonzero(m[i])[0])
+
+
+def test_predicate_boundary_is_strict():
+    s2 = np.float32(4.0)
+    assert not oracle.predicate32(0.0, 0.0, 2.0, 0.0, float(s2))      # r2 == s2: not a neighbour
+    assert oracle.predicate32(0.0, 0.0, float(np.nextafter(np.float32(2), np.float32(0))), 0.0,
+                              float(s2))
+    assert oracle.predicate32(0.1, 0.2, 0.1, 0.2, float(s2))           # coincident points are
+
+
+def _case_neighbour_sets(p, xy, brute):
+    c = oracle.OracleCase(p, xy, brute=brute)
+    off, ids = c.neighbours()
+    return c, off, ids
+
+
+@pytest.mark.parametrize("kind", ["lattice", "random", "cell_edges"])
+def test_cell_list_equals_brute_force(kind):
+    p = params(Lx=0.03, W=0.03, dx=1e-3)
+    if kind == "lattice":
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 7)
+    elif kind == "random":
+        rng = np.random.default_rng(3)
+        xy = np.stack([rng.random(900) * p["Lx"], (rng.random(900) - 0.5) * p["W"]], 1)
+    else:
+        # points exactly on multiples of the support radius and on lattice lines
+        s = 2 * p["h_over_dx"] * p["dx"]
+        g = np.arange(0, 11) * s
+        X, Y = np.meshgrid(g[g < p["Lx"]], g[g < p["W"] / 2] - 0.0)
+        xy = np.stack([X.ravel(), Y.ravel()], 1)
+        xy = np.concatenate([xy, xy + [0.5 * s, 0.0], xy + [0.0, -0.5 * s]])
+    c1, off1, ids1 = _case_neighbour_sets(p, xy, brute=False)
+    c2, off2, ids2 = _case_neighbour_sets(p, xy, brute=True)
+    assert np.array_equal(off1, off2) and np.array_equal(ids1, ids2)
+    # independent check of the fluid-fluid block with numpy float32
+    nf = c1.nf
+    m = _np_brute(xy.astype(np.float32), oracle.support_s2(p))
+    for i in range(0, nf, 7):
+        row = ids1[off1[i]:off1[i + 1]]
+        assert np.array_equal(row[row < nf], np.nonzero(m[i])[0])
+
+
+# ------------------------------------------------------- pair-sum invariants
+
+def _random_patch(seed=5, v_amp=20.0, rho_rel=0.01, **kw):
+    p = fluid_only(**kw)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.05, seed)
+    vel, rho = casegen.perturbed_state(xy.shape[0], seed, v_amp, p["rho0"], rho_rel)
+    return p, xy, vel, rho
+
+
+def _momentum_residual(mutation=0):
+    p, xy, vel, rho = _random_patch()
+    c = oracle.OracleCase(p, xy, vel, rho, mutation=mutation)
+    f = c.fluid()
+    m = p["rho0"] * p["dx"] ** 2
+    tot = m * f["acc"].sum(0)
+    scale = m * np.abs(f["acc"]).sum()
+    return np.abs(tot).max() / scale
+
+
+def test_momentum_is_antisymmetric():
+    # pair forces cancel: sum_i m_i a_i = 0 without ghosts and gravity
+    assert _momentum_residual() < 1e-13
+
+
+def test_planted_dropped_pj_breaks_antisymmetry():
+    assert _momentum_residual(oracle.MUT["drop_pj"]) > 1e-3
+
+
+def test_galilean_invariance():
+    p, xy, vel, rho = _random_patch()
+    a = oracle.OracleCase(p, xy, vel, rho).fluid()
+    b = oracle.OracleCase(p, xy, vel + np.array([37.0, -11.0]), rho).fluid()
+    for k in ("acc", "drho", "X"):
+        scale = np.abs(a[k]).max()
+        assert np.abs(a[k] - b[k]).max() <= 1e-9 * scale
+
+
+def _diss_rate(mutation=0, expanding=False):
+    p, xy, vel, rho = _random_patch(v_amp=50.0)
+    if expanding:
+        # v = kappa (r - r_c): every pair separates, v_ij . r_ij = kappa r^2 > 0
+        vel = 2.0e3 * (xy - xy.mean(0))
+    c = oracle.OracleCase(p, xy, vel, rho, mutation=mutation)
+    return c.scalars()["diss_rate"]
+
+
+def test_artificial_viscosity_only_dissipates():
+    assert _diss_rate() > 0.0
+
+
+def test_artificial_viscosity_off_under_expansion():
+    # the switch: Pi_ij = 0 when v_ij . r_ij >= 0, so a purely expanding field
+    # dissipates nothing
+    assert _diss_rate(expanding=True) == 0.0
+
+
+def test_planted_av_switch_fails_expansion_pin():
+    assert _diss_rate(oracle.MUT["av_sign"], expanding=True) > 0.0
+
+
+def test_rest_state_is_exact():
+    # no gravity, rho = rho0, v = 0, closed box of ghost walls, disk at rest
+    p = params(Lx=0.03, W=0.03, dx=1e-3, end_walls=1, gx=0.0, gy=0.0, v0=0.0,
+               x_c0=0.015, y_c0=0.0, R_disk=3e-3)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 11, disk=(0.015, 0.0, 3e-3))
+    c = oracle.OracleCase(p, xy)
+    f0 = c.fluid()
+    assert np.all(f0["acc"] == 0.0) and np.all(f0["drho"] == 0.0)
+    c.run(20)
+    f1 = c.fluid()
+    assert np.array_equal(f0["xy"], f1["xy"]) and np.all(f1["vel"] == 0.0)
+    assert np.all(f1["rho"] == p["rho0"])
+
+
+# ------------------------------------------------------------ ghost operator
+
+def _linear_field_case(mutation=0, disk=False):
+    """Fluid whose pressure is linear with gradient rho0 (g - a): the ghost
+    formula must reproduce the linear field at every ghost with support."""
+    p = params(Lx=0.03, W=0.03, dx=1e-3, end_walls=1, gx=0.0, gy=-9.81e4)
+    if disk:
+        p.update(Ng=60, R_disk=4e-3, x_c0=0.015, y_c0=0.0, motion=2, a_const=3.0e4,
+                 wall_layers=0, end_walls=0, gy=-1.0e4)
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.02, 13, disk=(0.015, 0.0, 4e-3))
+    else:
+        p.update(Ng=0)
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.02, 13)
+    B = p["rho0"] * p["c0"] ** 2 / p["gamma"]
+    ax = p["a_const"] if disk else 0.0  # t = 0: a = a_const
+    G = np.array([p["gx"] - ax, p["gy"]])
+    p_lin = lambda r: 5.0e6 + p["rho0"] * (r @ G)   # stays above the cutoff
+    pj = p_lin(xy)
+    rho = p["rho0"] * (1.0 + pj / B) ** (1.0 / p["gamma"])
+    c = oracle.OracleCase(p, xy, None, rho, mutation=mutation)
+    g = c.ghosts()
+    off, ids = c.neighbours()
+    has = np.diff(off)[c.nf:] > 0
+    expect = p_lin(g["xy"])
+    err = np.abs(g["p"] - expect)[has]
+    # the extrapolation is exact for uniform rho; rho varies by ~|dp|/c0^2
+    scale = p["rho0"] * np.abs(G).max() * 2 * p["h_over_dx"] * p["dx"]
+    # the identity is exact for uniform rho; here rho_j / rho0 - 1 = O(p / (gamma B))
+    # enters the body-force term, which bounds the admissible error
+    tol = 2.0 * np.abs(rho / p["rho0"] - 1.0).max() + 1e-9
+    return err.max() / scale, has.sum(), tol
+
+
+@pytest.mark.parametrize("disk", [False, True])
+def test_ghost_pressure_reproduces_linear_field(disk):
+    rel, n, tol = _linear_field_case(disk=disk)
+    assert n > 20
+    assert tol < 0.01
+    assert rel < tol
+
+
+@pytest.mark.parametrize("disk", [False, True])
+def test_planted_printed_sign_fails_linear_field(disk):
+    rel, _, _ = _linear_field_case(oracle.MUT["ghost_printed_sign"], disk=disk)
+    assert rel > 0.1
+
+
+def _ghost_velocity_error(mutation=0):
+    p = params(Lx=0.03, W=0.03, dx=1e-3, gx=0.0, gy=0.0, Ng=80, R_disk=4e-3, x_c0=0.015,
+               motion=2, a_const=1.0e6)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.02, 17, disk=(0.015, 0.0, 4e-3))
+    u = np.array([3.0, -2.0])
+    c = oracle.OracleCase(p, xy, np.tile(u, (xy.shape[0], 1)), None, mutation=mutation)
+    c.run(3)
+    s = c.scalars()
+    g = c.ghosts()
+    f = c.fluid()
+    off, ids = c.neighbours()
+    err = 0.0
+    for k in range(c.ngh):
+        gi = c.nf + k
+        nb = ids[off[gi]:off[gi + 1]]
+        if nb.size == 0:
+            continue
+        vw = np.array([s["vproj"], 0.0]) if g["kind"][k] == 3 else np.zeros(2)
+        # the fluid keeps (almost) its uniform velocity over 3 steps; compare with
+        # the Shepard mean taken from the oracle's own half-step velocities
+        vbar = f["vel"][nb].mean(0)
+        err = max(err, np.abs(g["vel"][k] - (2 * vw - vbar)).max() / (np.abs(vw).max() + 5.0))
+    return err
+
+
+def test_ghost_velocity_mirrors_fluid():
+    assert _ghost_velocity_error() < 0.05
+
+
+def test_planted_ghost_velocity_fails():
+    assert _ghost_velocity_error(oracle.MUT["ghost_vel"]) > 0.5
+
+
+def test_empty_ghost_takes_wall_state():
+    p = params(Lx=0.02, W=0.02, dx=1e-3, gx=0.0, gy=0.0, x_c0=-0.01, v0=0.0)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 3)
+    c = oracle.OracleCase(p, xy)
+    g = c.ghosts()
+    off, _ = c.neighbours()
+    empty = np.diff(off)[c.nf:] == 0
+    assert empty.sum() > 0
+    assert np.all(g["p"][empty] == 0.0) and np.all(g["rho"][empty] == p["rho0"])
+    assert np.all(g["vel"][empty] == 0.0)
+
+
+# -------------------------------------------------------------- kinematics
+
+@pytest.mark.parametrize("motion,t_ramp,tau", [(0, 5e-6, 200e-6), (0, 0.0, 200e-6),
+                                              (0, 5e-6, 0.0), (1, 5e-6, 0.0), (2, 0.0, 0.0)])
+def test_kinematics_closed_forms(motion, t_ramp, tau):
+    p = params(motion=motion, t_ramp=t_ramp, tau=tau, a_const=2.0e6)
+    x0 = oracle.kinematics(p, 0.0)[0]
+    for t in (1e-6, 4.9e-6, 5e-6, 7.3e-6, 40e-6, 150e-6):
+        x, v, a = oracle.kinematics(p, t)
+        vint, _ = si.quad(lambda s: oracle.kinematics(p, s)[1], 0.0, t, points=[t_ramp] if
+                          0 < t_ramp < t else None, epsabs=0, epsrel=1e-13, limit=200)
+        assert abs((x - x0) - vint) <= 1e-11 * abs(vint) + 1e-18
+        d = 1e-10
+        if abs(t - t_ramp) > 2 * d:
+            fd = (oracle.kinematics(p, t + d)[1] - oracle.kinematics(p, t - d)[1]) / (2 * d)
+            assert abs(a - fd) <= 1e-6 * abs(a) + 1e-3
+
+
+def test_kinematics_values():
+    p = params()
+    x, v, a = oracle.kinematics(p, 5e-6)
+    assert math.isclose(v, 900.0 * math.exp(-5e-6 / 200e-6), rel_tol=1e-15)
+    x, v, a = oracle.kinematics(p, 2.5e-6)
+    assert math.isclose(v, 450.0 * math.exp(-2.5e-6 / 200e-6), rel_tol=1e-15)
+
+
+# -------------------------------------------------- values the paper prints
+
+def _golden():
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        return json.load(f)
+
+
+def test_cfl_step_matches_paper_value():
+    g = _golden()["cfl_dt"]
+    p = params(dx=g["h"] / 1.3, h_over_dx=1.3, c0=g["c0"], v0=g["v0"], cfl=g["C"], dt_mode=1,
+               Lx=0.02, W=0.02)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 1)
+    c = oracle.OracleCase(p, xy)
+    assert abs(c.scalars()["dt"] - g["dt"]) <= g["rel_tol"] * g["dt"]
+
+
+def test_reflection_coefficient_value():
+    # the target a two-material wall would have to meet; the rigid ghost wall
+    # reflects with R -> 1 (see the reflection test below)
+    g = _golden()["reflection"]
+    Zs, Zw = g["rho_s"] * g["c_s"], g["rho0"] * g["c0"]
+    assert abs((Zs - Zw) / (Zs + Zw) - g["R"]) <= g["abs_tol"]
+    assert abs(Zs / Zw - g["Z_ratio"]) <= 0.5
+
+
+def test_hydrostatic_ratio_and_suction_values():
+    g = _golden()
+    h = g["hydrostatic_ratio"]
+    assert abs(h["rho0"] * h["C"] ** 2 / (h["rho0"] * 9.81 * h["H"]) - h["ratio"]) < 0.05e6
+    s = g["suction_peak"]
+    assert abs(s["rho0"] * s["U"] ** 2 * (0.5 - 2.0) - s["p"]) < 1e-6 * abs(s["p"])
