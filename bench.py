@@ -1,0 +1,323 @@
+"""Benchmark of the planar WCSPH hydrodynamic-ram step on B300.
+
+Workload: the 300 x 150 mm channel at dx = 0.2 mm (1,125,000 fluid particles,
+3 ghost layers per wall, 5 mm disk entering at 900 m/s with tau = 200 us),
+stepped from t = 0 (impact phase).  One "step" is one pass of the whole hot
+path: drift, counting sort, ghosts, fused interaction pass, probes and the CFL
+gate, replayed from a CUDA graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With --gpus N > 1 (launched by torchrun) every rank runs
+an independent replica of the case (the path does not shard across GPUs), and
+the value is the aggregate particle-steps/s over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import casegen  # noqa: E402
+
+METRIC = "particle-steps/s at 1M particles"
+UNIT = "particle-steps/s"
+DX = 2e-4
+ALG_BYTES_PER_PARTICLE = 40      # {x, y, vx, vy, rho} read and written once
+FLOP_PER_PAIR = 58               # pair terms of the interaction pass
+FLOP_PER_CANDIDATE = 6           # float predicate of one candidate
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_pass_c2_dx0.2mm_traffic.txt")
+
+
+def workload(dx=DX, Lx=None):
+    p = casegen.config_scaling(dx)
+    if Lx is not None:
+        p["Lx"] = Lx
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
+    return p, xy.astype(np.float32)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz=2032.0, sms=148, lanes=128):
+    """FP32 peak from unit counts: SMs x FP32 lanes x 2 flop (FMA) x clock."""
+    return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def read_traffic(src_hash):
+    """dram bytes per launch of k_pass from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    vals = {}
+    with open(PROFILE_TRAFFIC) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2609_05494_b300", "csrc", "hram_device.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def cpu_baseline(seconds=15.0, Lx=0.075):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample of the
+    workload: the first Lx of the channel at the same spacing, from t = 0."""
+    import oracle
+    p, xy = workload(DX, Lx=Lx)
+    t0 = time.perf_counter()
+    o = oracle.OracleCase(p, xy.astype(np.float64))
+    t1 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step()
+        steps += 1
+        if time.perf_counter() - t1 >= seconds:
+            break
+    el = time.perf_counter() - t1
+    return {"value": xy.shape[0] * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d mm of the 300 mm channel at dx = 0.2 mm (%d fluid particles), "
+                      "%d steps from t = 0 after %.1f s set-up" % (round(Lx * 1e3), xy.shape[0],
+                                                                     steps, t1 - t0)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    Lx = 0.0375
+    p, xy = workload(DX, Lx=Lx)
+    o = oracle.OracleCase(p, xy.astype(np.float64))
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    el = time.perf_counter() - t0
+    value = xy.shape[0] * args.steps / el
+    sample = ("FP64 C oracle, 1 host thread, on the first %.1f mm of the 300 mm channel at "
+              "dx = 0.2 mm (%d fluid particles) from t = 0" % (Lx * 1e3, xy.shape[0]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "c2-dx0.2mm sample", "particles": int(xy.shape[0]),
+                       "dx_mm": 0.2, "channel_mm": [Lx * 1e3, 150.0]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--dx", type=float, default=DX)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2609_05494_b300 import Case
+
+    p, xy = workload(args.dx)
+    n = xy.shape[0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        case = Case(p, xy, stream=stream, timing=True, probe_capacity=args.steps + args.warmup + 8)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # pairs per step (for the flop count), from the neighbour lists of the start state
+    off, _ = case.neighbours()
+    pairs_fluid_rows = int(off[n] - off[0])
+    for _ in range(args.warmup):
+        case.step()
+    case.sync()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pass_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)               # write 256 MB > L2 between timed steps
+                ev[k][0].record(stream)
+                case.step()
+                ev[k][1].record(stream)
+            stream.synchronize()
+            pass_ms.append(case.kernel_times()["pass"])
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    groups = case.kernel_times()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    status = case.sync()
+
+    # end to end through the C-ABI with host buffers (pinned), K steps
+    vel0 = np.zeros_like(xy)
+    rho0 = np.full(n, p["rho0"], np.float32)
+    h_xy = torch.from_numpy(xy).pin_memory().numpy()
+    h_v = torch.from_numpy(vel0).pin_memory().numpy()
+    h_r = torch.from_numpy(rho0).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    case.set_state(h_xy, h_v, h_r)
+    case.run(args.steps)
+    probes = case.probe_pressure()
+    final = case.get_state()
+    e2e_s = time.perf_counter() - t0
+    h2d = h_xy.nbytes + h_v.nbytes + h_r.nbytes
+    d2h = probes.nbytes + sum(v.nbytes for v in final.values())
+
+    if rank != 0:
+        case.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pk, src = peaks()
+    value = world * n * args.steps / (total_ms * 1e-3)
+    t_pass = statistics.mean(pass_ms) * 1e-3
+    flops = pairs_fluid_rows * FLOP_PER_PAIR
+    alu_peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0))
+    achieved_tf = flops / t_pass / 1e12
+    hbm_achieved = ALG_BYTES_PER_PARTICLE * n / t_pass / 1e9
+    traffic = read_traffic(kernel_source_hash())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c2-dx0.2mm: 300 x 150 mm channel, dx = 0.2 mm, %d fluid "
+                               "particles, disk 5 mm at 900 m/s, impact phase from t = 0" % n,
+                   "particles": n, "dx_mm": args.dx * 1e3, "parallelism": "replicas" if world > 1
+                   else "single", "l2": "256 MB buffer written between timed steps",
+                   "status": status},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": 9 * args.steps,
+        "roofline": {"kernel": "k_pass", "bound": "alu", "achieved": achieved_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
+                     "traffic": traffic,
+                     "peak_source": "FP32 from unit counts: 148 SM x 128 lanes x 2 x %.0f MHz"
+                                    % pk.get("sm_max_mhz", 2032.0),
+                     "flop_per_launch": flops, "pass_ms": t_pass * 1e3},
+        "roofline_hbm": {"kernel": "k_pass", "bound": "hbm", "achieved": hbm_achieved,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": hbm_achieved / pk["hbm_gbs"],
+                         "step_frac": ALG_BYTES_PER_PARTICLE * value / world / 1e9 / pk["hbm_gbs"],
+                         "peak_source": src, "bytes_per_particle": ALG_BYTES_PER_PARTICLE},
+        "kernel_groups_ms": groups,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    case.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * hram.h -- C-ABI of the B300 (sm_103a) planar WCSPH hydrodynamic-ram step.
+ *
+ * The library advances one case of the planar weakly compressible SPH model of
+ * Alam, Biswas & Chakraborty ("Verification, Sensitivity, and Operating Limits
+ * of a GPU-Accelerated Planar WCSPH Model for Hydrodynamic Ram"): a water
+ * channel with Adami ghost walls, penetrated by a rigid disk with prescribed,
+ * decelerating motion.  One step is U^{n+1} = T(L(G(U^n))) (Section 4.6):
+ * ghost extrapolation G (Section 2.6, eqs. adami-p / adami-v), the fused
+ * interaction sums L (Section 2.2: XSPH, momentum with Monaghan artificial
+ * viscosity and a laminar term, continuity density, Tait pressure with the
+ * cavitation cutoff) and the kick-drift-kick time advance T with the CFL gate
+ * (Section 2.5, eq. cfl).  Every step runs in CUDA kernels on the device; the
+ * host only launches a captured CUDA graph.
+ *
+ * Conventions for every call:
+ *   - SI units.  Fluid x in [0, Lx], y in [-W/2, W/2]; the disk moves along +x.
+ *   - Host pointers are owned by the caller and are not retained after the
+ *     call returns.  Arrays of 2-vectors are interleaved (x0, y0, x1, y1, ...).
+ *     Per-particle arrays are in fluid-ID order (the order given at init).
+ *   - All device work runs on the stream passed to hr_init_case, so it is
+ *     ordered with the caller's other work on that stream.
+ *   - Every call returns an int status: 0 = HR_OK, negative = error (the case
+ *     may no longer be advanced), positive = warning bits (the state is valid).
+ *     Device-side errors are sticky: once seen they are returned by every
+ *     later call that synchronises.
+ *   - No call reads the CUDA state of other cases; a case is not thread-safe.
+ */
+#ifndef HRAM_H
+#define HRAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HR_MAX_PROBES 16
+
+/* status codes */
+#define HR_OK 0
+#define HR_EINVAL (-1)    /* bad argument or parameter */
+#define HR_ENOMEM (-2)    /* device allocation failed or workspace too small */
+#define HR_ECUDA (-3)     /* a CUDA call failed */
+#define HR_ENAN (-4)      /* NaN or Inf appeared in the fluid state */
+#define HR_EDT (-5)       /* time step underflow (dt < 1e-14 s) */
+#define HR_ERANGE (-7)    /* caller buffer too small */
+#define HR_EIO (-8)       /* file error in save / load */
+/* warning bits (positive) */
+#define HR_WPENETRATION 1 /* fluid particles inside the disk circle */
+#define HR_WOUTSIDE 2     /* particles left the computational box and were frozen */
+#define HR_WPROBEFULL 4   /* probe history capacity reached; later samples dropped */
+
+/* flags */
+#define HR_FLAG_TIMING 1  /* record CUDA events around the step's kernels */
+
+/* Case parameters.  Field meanings follow the paper's notation.
+ *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)
+ *  Lx, W           channel length and width
+ *  wall_layers     ghost layers per side wall (0 = no side walls)
+ *  end_walls       1 = also close x = 0 and x = Lx with ghost walls
+ *  R_disk, v0, tau, t_ramp, x_c0, y_c0   disk radius, entry speed, decay time,
+ *                  ramp time (Section 2.6.3), initial centre
+ *  Ng              disk ghost count (Section 2.6.1); 0 = no disk
+ *  motion          0 ramp x exponential decay, 1 ramp + quadratic drag
+ *                  (Section 2.7, drag_M, drag_Cd, drag_R), 2 constant
+ *                  acceleration a_const from rest
+ *  rho0, c0, gamma Tait equation of state; p_cav cavitation cutoff
+ *  alpha, eta2     artificial viscosity (eq. artificial-viscosity)
+ *  eps_xsph        XSPH blending (eq. xsph); mu_lam dynamic viscosity
+ *  gx, gy          body force; cfl the CFL number (eq. cfl)
+ *  dt_mode         0 adaptive dt, 1 fixed dt = cfl h / (c0 + v0)
+ *  rho_lo, rho_hi  density band as fractions of rho0 (0.5, 1.5)
+ *  box_pad         computational-box padding (<= 0: default)
+ *  cell_factor     cell side / 2h (>= 1.001)
+ *  probe_xy        wall probe points, n_probes of them
+ *  probe_capacity  probe history rows kept on the device
+ *  diag_every      record FP64 diagnostics every k steps (0 = never)
+ *  flags           HR_FLAG_* */
+typedef struct hr_params {
+    double dx, h_over_dx, Lx, W;
+    int32_t wall_layers, end_walls;
+    double R_disk, v0, tau, t_ramp, x_c0, y_c0;
+    int32_t Ng, motion;
+    double a_const, drag_M, drag_Cd, drag_R;
+    double rho0, c0, gamma, p_cav, alpha, eta2, eps_xsph, mu_lam, gx, gy, cfl;
+    int32_t dt_mode, n_probes;
+    double rho_lo, rho_hi, box_pad, cell_factor;
+    double probe_xy[2 * HR_MAX_PROBES];
+    int64_t probe_capacity;
+    int32_t diag_every, flags;
+} hr_params;
+
+/* FP64 diagnostics (Section 2.10 and eq. energy-audit of Section 4.7). */
+typedef struct hr_diag {
+    double mass, px, py, KE, PE, E_el;
+    double rho_min, rho_max, p_min, p_max, vmax_fluid;
+    double n_in, penetrated, t, dt;
+    double W_boundary, wall_impulse, dissipation, step;
+} hr_diag;
+
+typedef struct hr_case hr_case; /* opaque; owns or borrows all device memory */
+
+/* Device bytes a case needs (one block, 256-byte aligned sub-buffers).
+ * n_fluid: fluid particle count.  Returns HR_EINVAL for bad parameters. */
+int hr_workspace_bytes(const hr_params *p, int64_t n_fluid, size_t *bytes);
+
+/* Creates a case.  xy: n_fluid initial positions (float, host, ID order);
+ * vel (n_fluid x 2) and rho (n_fluid) may be NULL for rest at rho0.
+ * d_workspace: device memory of at least hr_workspace_bytes bytes owned by
+ * the caller (it must outlive the case), or NULL to let the library allocate.
+ * cuda_stream: a cudaStream_t (0 = legacy default stream).  Computes the
+ * initial a, D rho, XSPH sums and dt (t = 0), captures the step graph and
+ * synchronises.  On failure *out is NULL and nothing is retained. */
+int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const float *vel,
+                 const float *rho, void *d_workspace, size_t workspace_bytes,
+                 void *cuda_stream, hr_case **out);
+
+/* One step (graph replay), asynchronous.  Returns the last known status. */
+int hr_step(hr_case *c);
+
+/* n_steps steps; with t_end > 0 stops at the first step that reaches t_end
+ * (n_steps <= 0 then means "until t_end").  Synchronises and returns the
+ * device status. */
+int hr_run(hr_case *c, int64_t n_steps, double t_end);
+
+/* Waits for the case's work and returns the device status. */
+int hr_sync(hr_case *c);
+
+/* Probe pressure history, row k = [p_probe0 .. p_probe(n-1)] after step k+1
+ * (float, host, cap_rows x n_probes).  *n_rows = rows recorded. */
+int hr_probe_pressure(hr_case *c, float *host_out, int64_t cap_rows, int64_t *n_rows);
+
+/* Simulated time after step k+1 (double, host). */
+int hr_probe_times(hr_case *c, double *host_out, int64_t cap, int64_t *n);
+
+/* FP64 diagnostics of the current state (synchronises). */
+int hr_diagnostics(hr_case *c, hr_diag *out);
+
+/* Recorded periodic diagnostics (diag_every > 0): rows of 19 doubles in
+ * hr_diag field order.  *n_rows = rows recorded. */
+int hr_diag_history(hr_case *c, double *host_out, int64_t cap_rows, int64_t *n_rows);
+
+/* Current fluid state in ID order (any pointer may be NULL).  xy, vel: cap x 2;
+ * rho, p: cap.  cap must be >= n_fluid (else HR_ERANGE).  Synchronises. */
+int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_t cap);
+
+/* Replaces the fluid state (ID order, n == n_fluid), resets t = 0, the step
+ * counter, probe history and accumulators, and recomputes a, D rho, X, dt as
+ * hr_init_case does.  vel or rho may be NULL (rest, rho0). */
+int hr_set_state(hr_case *c, const float *xy, const float *vel, const float *rho, int64_t n);
+
+/* Ghost state of the last step (wall ghosts in wall-ID order, then disk
+ * ghosts): xy, vel cap x 2; p, rho cap.  Synchronises. */
+int hr_get_ghosts(hr_case *c, float *xy, float *p, float *rho, float *vel, int64_t cap);
+
+/* Scalars: t, dt, step, xc, yc, vproj, aproj, Fdisk_x, Fdisk_y, Fwall,
+ * W_boundary, wall_impulse, dissipation, diss_rate (14 doubles). */
+int hr_get_scalars(hr_case *c, double *out, int n);
+
+/* Counts: n_fluid, n_wall, n_disk, ncx, ncy, pass_blocks (6 int64). */
+int hr_case_info(hr_case *c, int64_t *out, int n);
+
+/* Neighbour sets of the current state as CSR over all points (fluid IDs,
+ * then wall ghosts, then disk ghosts; fluid rows list fluid and ghost
+ * neighbours, ghost rows list fluid neighbours; ids ascending).  offsets has
+ * n_points + 1 entries.  With ids == NULL or cap too small only *n_pairs is
+ * set (and HR_ERANGE returned when ids != NULL).  Synchronises. */
+int hr_debug_neighbors(hr_case *c, int64_t *offsets, int32_t *ids, int64_t cap,
+                       int64_t *n_pairs);
+
+/* Durations (ms) of the last replayed step's kernel groups when the case was
+ * created with HR_FLAG_TIMING: drift, sort, ghost, pass, finalize. */
+int hr_kernel_times(hr_case *c, float *ms, int n);
+
+/* Checkpoint / resume of the full state (positions, velocities, densities,
+ * derivatives, time, dt, accumulators, probe history) in a binary file.
+ * A loaded case continues bit-for-bit as the saved one would have. */
+int hr_save_state(hr_case *c, const char *path);
+int hr_load_state(hr_case *c, const char *path);
+
+void hr_destroy(hr_case *c);
+const char *hr_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HRAM_H */

@@ -1,0 +1,224 @@
+"""Python interface of the B300 planar WCSPH hydrodynamic-ram library.
+
+:class:`Case` wraps one ``hr_case`` of the C-ABI (include/hram.h).  PyTorch is
+used only for device memory (the case's workspace) and the CUDA stream; all
+arithmetic of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import HrDiag, HrParams, check, lib
+
+DIAG_FIELDS = tuple(n for n, _ in HrDiag._fields_)
+SCALAR_FIELDS = ("t", "dt", "step", "xc", "yc", "vproj", "aproj", "Fdisk_x", "Fdisk_y",
+                 "Fwall", "W_boundary", "wall_impulse", "dissipation", "diss_rate")
+KERNEL_GROUPS = ("drift", "sort", "ghost", "pass", "finalize")
+
+
+def make_params(d: dict, flags: int = 0, probe_capacity: int = 1 << 16,
+                diag_every: int = 0) -> HrParams:
+    """C parameter struct from a parameter dict (keys as in casegen)."""
+    p = HrParams()
+    skip = ("probe_xy", "n_probes", "probe_capacity", "diag_every", "flags")
+    for name, ctype in HrParams._fields_:
+        if name in skip:
+            continue
+        setattr(p, name, int(d[name]) if ctype in (C.c_int32, C.c_int64) else float(d[name]))
+    probes = list(d.get("probes", []))
+    if len(probes) > _lib.MAX_PROBES:
+        raise ValueError("at most %d probes" % _lib.MAX_PROBES)
+    p.n_probes = len(probes)
+    for k, (x, y) in enumerate(probes):
+        p.probe_xy[2 * k] = float(x)
+        p.probe_xy[2 * k + 1] = float(y)
+    p.probe_capacity = int(probe_capacity)
+    p.diag_every = int(diag_every)
+    p.flags = int(flags)
+    return p
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Case:
+    """One simulated case on the GPU.
+
+    params: dict of parameters (see casegen.base_params); xy: (N, 2) initial
+    positions in fluid-ID order; vel (N, 2) / rho (N,) optional.  The device
+    workspace is a torch uint8 tensor unless ``torch_workspace`` is False, in
+    which case the library allocates it.
+    """
+
+    def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
+                 probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True):
+        L = lib()
+        xy = _f32(xy)
+        n = xy.shape[0]
+        if xy.shape != (n, 2):
+            raise ValueError("xy must be (N, 2)")
+        self.n = n
+        self.params = dict(params)
+        self._p = make_params(params, _lib.HR_FLAG_TIMING if timing else 0, probe_capacity,
+                              diag_every)
+        self.n_probes = self._p.n_probes
+        nbytes = C.c_size_t(0)
+        check(L.hr_workspace_bytes(C.byref(self._p), n, C.byref(nbytes)), "hr_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self._ws = None
+        ws_ptr = None
+        if torch_workspace:
+            import torch
+            self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+            ws_ptr = self._ws.data_ptr()
+        self._stream = _stream_handle(stream)
+        h = C.c_void_p()
+        rc = L.hr_init_case(C.byref(self._p), _ptr(xy), n, _ptr(_f32(vel, (n, 2))),
+                            _ptr(_f32(rho, (n,))), ws_ptr, nbytes.value, self._stream, C.byref(h))
+        check(rc, "hr_init_case")
+        self._h = h
+        self.last_status = rc
+        info = self.info()
+        self.n_wall, self.n_disk = info["n_wall"], info["n_disk"]
+
+    # -- lifecycle
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h:
+            lib().hr_destroy(h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stepping
+    def step(self) -> int:
+        self.last_status = check(lib().hr_step(self._h), "hr_step")
+        return self.last_status
+
+    def run(self, n_steps: int, t_end: float = 0.0) -> int:
+        self.last_status = check(lib().hr_run(self._h, int(n_steps), float(t_end)), "hr_run")
+        return self.last_status
+
+    def sync(self) -> int:
+        self.last_status = check(lib().hr_sync(self._h), "hr_sync")
+        return self.last_status
+
+    # -- outputs
+    def probe_pressure(self) -> np.ndarray:
+        L = lib()
+        n = C.c_int64(0)
+        check(L.hr_probe_pressure(self._h, None, 0, C.byref(n)), "hr_probe_pressure")
+        out = np.zeros((n.value, max(self.n_probes, 1)), dtype=np.float32)
+        check(L.hr_probe_pressure(self._h, _ptr(out), n.value, C.byref(n)), "hr_probe_pressure")
+        return out[:, :self.n_probes]
+
+    def probe_times(self) -> np.ndarray:
+        L = lib()
+        n = C.c_int64(0)
+        check(L.hr_probe_times(self._h, None, 0, C.byref(n)), "hr_probe_times")
+        out = np.zeros(n.value, dtype=np.float64)
+        check(L.hr_probe_times(self._h, _ptr(out), n.value, C.byref(n)), "hr_probe_times")
+        return out
+
+    def diagnostics(self) -> dict:
+        d = HrDiag()
+        check(lib().hr_diagnostics(self._h, C.byref(d)), "hr_diagnostics")
+        return {k: getattr(d, k) for k in DIAG_FIELDS}
+
+    def diag_history(self) -> np.ndarray:
+        L = lib()
+        n = C.c_int64(0)
+        check(L.hr_diag_history(self._h, None, 0, C.byref(n)), "hr_diag_history")
+        out = np.zeros((n.value, len(DIAG_FIELDS)))
+        check(L.hr_diag_history(self._h, _ptr(out), n.value, C.byref(n)), "hr_diag_history")
+        return out
+
+    def get_state(self) -> dict:
+        n = self.n
+        out = dict(xy=np.empty((n, 2), np.float32), vel=np.empty((n, 2), np.float32),
+                   rho=np.empty(n, np.float32), p=np.empty(n, np.float32))
+        check(lib().hr_get_state(self._h, _ptr(out["xy"]), _ptr(out["vel"]), _ptr(out["rho"]),
+                                 _ptr(out["p"]), n), "hr_get_state")
+        return out
+
+    def set_state(self, xy, vel=None, rho=None) -> int:
+        n = self.n
+        self.last_status = check(lib().hr_set_state(self._h, _ptr(_f32(xy, (n, 2))),
+                                                    _ptr(_f32(vel, (n, 2))),
+                                                    _ptr(_f32(rho, (n,))), n), "hr_set_state")
+        return self.last_status
+
+    def ghosts(self) -> dict:
+        g = self.n_wall + self.n_disk
+        out = dict(xy=np.empty((g, 2), np.float32), p=np.empty(g, np.float32),
+                   rho=np.empty(g, np.float32), vel=np.empty((g, 2), np.float32))
+        check(lib().hr_get_ghosts(self._h, _ptr(out["xy"]), _ptr(out["p"]), _ptr(out["rho"]),
+                                  _ptr(out["vel"]), g), "hr_get_ghosts")
+        return out
+
+    def scalars(self) -> dict:
+        s = np.empty(len(SCALAR_FIELDS))
+        check(lib().hr_get_scalars(self._h, _ptr(s), len(SCALAR_FIELDS)), "hr_get_scalars")
+        return dict(zip(SCALAR_FIELDS, s.tolist()))
+
+    def info(self) -> dict:
+        v = np.empty(6, dtype=np.int64)
+        check(lib().hr_case_info(self._h, _ptr(v), 6), "hr_case_info")
+        return dict(zip(("n_fluid", "n_wall", "n_disk", "ncx", "ncy", "pass_blocks"),
+                        (int(x) for x in v)))
+
+    def neighbours(self) -> tuple[np.ndarray, np.ndarray]:
+        """CSR over all points (fluid IDs, wall ghosts, disk ghosts), ids ascending."""
+        L = lib()
+        npts = self.n + self.n_wall + self.n_disk
+        off = np.empty(npts + 1, dtype=np.int64)
+        n = C.c_int64(0)
+        check(L.hr_debug_neighbors(self._h, _ptr(off), None, 0, C.byref(n)), "hr_debug_neighbors")
+        ids = np.empty(max(n.value, 1), dtype=np.int32)
+        check(L.hr_debug_neighbors(self._h, _ptr(off), _ptr(ids), n.value, C.byref(n)),
+              "hr_debug_neighbors")
+        return off, ids[:n.value]
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(len(KERNEL_GROUPS), dtype=np.float32)
+        check(lib().hr_kernel_times(self._h, _ptr(ms), len(KERNEL_GROUPS)), "hr_kernel_times")
+        return dict(zip(KERNEL_GROUPS, ms.tolist()))
+
+    def save(self, path: str) -> None:
+        check(lib().hr_save_state(self._h, str(path).encode()), "hr_save_state")
+
+    def load(self, path: str) -> None:
+        check(lib().hr_load_state(self._h, str(path).encode()), "hr_load_state")

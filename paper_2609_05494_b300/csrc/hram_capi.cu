@@ -1,0 +1,1110 @@
+// hram_capi.cu -- step engine and C-ABI of the B300 planar WCSPH
+// hydrodynamic-ram library (declarations and documentation in hram.h).
+//
+// A case owns (or borrows) one device workspace carved into the buffers of
+// hram_device.cuh.  hr_init_case builds the static ghost geometry on the host
+// in FP64, uploads it, evaluates the initial state (a "prime" pass: the step
+// kernels with dt = 0), and captures one step as a CUDA graph on a private
+// stream; hr_step replays that graph on the caller's stream.
+#include "hram_device.cuh"
+#include "hram.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+using namespace hr;
+
+namespace {
+
+constexpr int kDiagFields = 19;
+constexpr int kDiagThreads = 256;
+constexpr int kTimingEvents = 6;
+
+// ------------------------------------------------ auxiliary device kernels
+
+// FP64 diagnostics, stage 1: per-block partial sums over the fluid.
+// partial layout (16 doubles): px, py, KE, PE, E_el, rho_min, rho_max, p_min,
+// p_max, vmax, n_in, penetrated, (unused x4)
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Consts K, Bufs B, double *part)
+{
+    __shared__ double sm[kDiagThreads / 32][12];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double v[12] = {0, 0, 0, 0, 0, 1e300, -1e300, 1e300, -1e300, 0, 0, 0};
+    if (i < K.nf) {
+        const float2 r = B.s_pos[i];
+        if (!outside_box(K, r.x, r.y)) {
+            const float2 u = B.st_vel[i];
+            const double d = (double)B.st_rho[i];
+            const double m = (double)K.m, rho0 = (double)K.rho0, g = (double)K.gamma;
+            const double vx = u.x, vy = u.y, v2 = vx * vx + vy * vy;
+            const double x = 1.0 + d;
+            // Tait elastic energy per unit mass, written in the deviation d
+            const double e = ((double)K.B / rho0) *
+                             (expm1((g - 1.0) * log1p(d)) / (g - 1.0) + 1.0 / x - 1.0);
+            v[0] = m * vx;
+            v[1] = m * vy;
+            v[2] = 0.5 * m * v2;
+            v[3] = -m * ((double)K.gx * r.x + (double)K.gy * r.y);
+            v[4] = m * e;
+            v[5] = v[6] = rho0 * x;
+            v[7] = v[8] = (double)tait_p(K, (float)d);
+            v[9] = sqrt(v2);
+            v[10] = 1.0;
+            const float dx = r.x - (float)B.S->xc, dy = r.y - (float)B.S->yc;
+            v[11] = (K.ng > 0 && dx * dx + dy * dy < K.R2) ? 1.0 : 0.0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double a = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b = __shfl_xor_sync(0xffffffffu, a, o);
+            if (k == 5 || k == 7) a = fmin(a, b);
+            else if (k == 6 || k == 8 || k == 9) a = fmax(a, b);
+            else a += b;
+        }
+        if (lane == 0) sm[w][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int k = threadIdx.x;
+        double a = sm[0][k];
+        for (int q = 1; q < kDiagThreads / 32; ++q) {
+            const double b = sm[q][k];
+            if (k == 5 || k == 7) a = fmin(a, b);
+            else if (k == 6 || k == 8 || k == 9) a = fmax(a, b);
+            else a += b;
+        }
+        part[(size_t)blockIdx.x * 16 + k] = a;
+    }
+}
+
+// Stage 2 (one block): reduce the partials in block order and write an
+// hr_diag record (19 doubles) to out[0] and, when rec >= 0, to hist[rec].
+__global__ void k_diag_final(Consts K, Bufs B, const double *part, int nblocks, double *out,
+                             double *hist, long long rec, long long hist_cap)
+{
+    if (threadIdx.x != 0) return;
+    double a[12] = {0, 0, 0, 0, 0, 1e300, -1e300, 1e300, -1e300, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int k = 0; k < 12; ++k) {
+            const double x = part[(size_t)b * 16 + k];
+            if (k == 5 || k == 7) a[k] = fmin(a[k], x);
+            else if (k == 6 || k == 8 || k == 9) a[k] = fmax(a[k], x);
+            else a[k] += x;
+        }
+    const Scalars *S = B.S;
+    double d[kDiagFields] = {(double)K.nf * (double)K.m, a[0], a[1], a[2], a[3], a[4], a[5],
+                             a[6], a[7], a[8], a[9], a[10], a[11], S->t, S->dt, S->Wb,
+                             S->impulse, S->diss, (double)S->step};
+    for (int k = 0; k < kDiagFields; ++k) out[k] = d[k];
+    if (rec >= 0 && rec < hist_cap)
+        for (int k = 0; k < kDiagFields; ++k) hist[(size_t)rec * kDiagFields + k] = d[k];
+}
+
+// Sorted state -> fluid-ID order.
+__global__ void k_unsort(Consts K, Bufs B, float2 *xy, float2 *vel, float *rho, float *p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    const int id = B.s_id[i];
+    const float d = B.st_rho[i];
+    xy[id] = B.s_pos[i];
+    vel[id] = B.st_vel[i];
+    rho[id] = K.rho0 * (1.0f + d);
+    p[id] = tait_p(K, d);
+}
+
+// Debug neighbour enumeration with the same candidate loops and predicate
+// as k_ghost and k_pass.  Row r of the output (global point order: fluid by
+// slot, then wall ghosts by sorted index, then disk ghosts): count[r] when
+// ids == nullptr, else the neighbours' global IDs at off[r].
+__global__ void k_neighbors(Consts K, Bufs B, int *count, const long long *off, int *ids)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npts = K.nf + K.nw + K.ng;
+    if (r >= npts) return;
+    long long pos = ids ? off[r] : 0;
+    int n = 0;
+    auto emit = [&](int gid) {
+        if (ids) ids[pos + n] = gid;
+        ++n;
+    };
+    if (r < K.nf) {
+        const float2 ri = B.s_pos[r];
+        if (!outside_box(K, ri.x, ri.y)) {
+            const int c = cell_of(K, ri.x, ri.y);
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = B.s_pos[j];
+                if (j != r && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) emit(B.s_id[j]);
+            });
+            if (K.nw > 0)
+                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                    const float2 rg = B.gw_pos[k];
+                    if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) emit(K.nf + B.gw_id[k]);
+                });
+            if (K.ng > 0 && near_disk(K, ri.x, ri.y, (float)B.S->xc, (float)B.S->yc))
+                for (int k = 0; k < K.ng; ++k) {
+                    const float2 rg = B.gd_pos[k];
+                    if (!outside_box(K, rg.x, rg.y) && in_support(ri.x, ri.y, rg.x, rg.y, K.s2))
+                        emit(K.nf + K.nw + k);
+                }
+        }
+    } else {
+        const int g = r - K.nf;
+        const float2 rg = g < K.nw ? B.gw_pos[g] : B.gd_pos[g - K.nw];
+        if (!outside_box(K, rg.x, rg.y)) {
+            const int c = cell_of(K, rg.x, rg.y);
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = B.s_pos[j];
+                if (in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) emit(B.s_id[j]);
+            });
+        }
+    }
+    if (!ids) count[r] = n;
+}
+
+// Wall-ghost cell keys with the device's own cell arithmetic.
+__global__ void k_wall_keys(Consts K, const float2 *pos, int n, int *key)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) key[k] = cell_of(K, pos[k].x, pos[k].y);
+}
+
+// ------------------------------------------------------------ host helpers
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t total = 0;
+    size_t add(size_t bytes)
+    {
+        const size_t off = total;
+        total += align256(bytes > 0 ? bytes : 1);
+        return off;
+    }
+};
+
+struct Geometry {
+    std::vector<double> wx, wy, wnx, wny;
+    std::vector<int> wkind;
+};
+
+// Wall ghosts in wall-ID order: lower band (layer-major), upper band, then
+// with closed ends the left and right bands.  Layer k at W/2 + (k - 1/2) dx.
+Geometry make_walls(const hr_params &P)
+{
+    Geometry G;
+    const int L = P.wall_layers;
+    if (L <= 0) return G;
+    const long long nx = llround(P.Lx / P.dx), ny = llround(P.W / P.dx);
+    const long long i0 = P.end_walls ? -L : 0, i1 = nx + (P.end_walls ? L : 0);
+    for (int band = 0; band < 2; ++band)
+        for (int k = 1; k <= L; ++k)
+            for (long long i = i0; i < i1; ++i) {
+                G.wx.push_back(((double)i + 0.5) * P.dx);
+                G.wy.push_back(band == 0 ? -0.5 * P.W - ((double)k - 0.5) * P.dx
+                                         : 0.5 * P.W + ((double)k - 0.5) * P.dx);
+                G.wnx.push_back(0.0);
+                G.wny.push_back(band == 0 ? -1.0 : 1.0);
+                G.wkind.push_back(KIND_SIDE);
+            }
+    if (P.end_walls)
+        for (int band = 0; band < 2; ++band)
+            for (int k = 1; k <= L; ++k)
+                for (long long j = 0; j < ny; ++j) {
+                    G.wx.push_back(band == 0 ? -((double)k - 0.5) * P.dx
+                                             : P.Lx + ((double)k - 0.5) * P.dx);
+                    G.wy.push_back(-0.5 * P.W + ((double)j + 0.5) * P.dx);
+                    G.wnx.push_back(band == 0 ? -1.0 : 1.0);
+                    G.wny.push_back(0.0);
+                    G.wkind.push_back(KIND_END);
+                }
+    return G;
+}
+
+int validate(const hr_params *P, long long nf)
+{
+    if (!P || nf <= 0 || nf > (1LL << 30)) return HR_EINVAL;
+    if (!(P->dx > 0) || !(P->h_over_dx > 0) || !(P->Lx > 0) || !(P->W > 0)) return HR_EINVAL;
+    if (P->wall_layers < 0 || P->wall_layers > 8 || P->Ng < 0 || P->Ng > 1024) return HR_EINVAL;
+    if (P->n_probes < 0 || P->n_probes > HR_MAX_PROBES) return HR_EINVAL;
+    if (!(P->rho0 > 0) || !(P->c0 > 0) || !(P->gamma > 1) || !(P->cfl > 0)) return HR_EINVAL;
+    if (!(P->rho_lo > 0) || !(P->rho_hi > P->rho_lo)) return HR_EINVAL;
+    if (P->motion < 0 || P->motion > 2 || P->dt_mode < 0 || P->dt_mode > 1) return HR_EINVAL;
+    if (P->motion == 1 && !(P->drag_M > 0)) return HR_EINVAL;
+    if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
+    if (P->cell_factor < 1.0) return HR_EINVAL;
+    return HR_OK;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- the case
+
+struct hr_case {
+    hr_params P;
+    Consts K;
+    Bufs B;
+    long long nf = 0, nw = 0, ng = 0;
+    int n_tiles = 0, pass_blocks = 0, ghost_blocks = 0, drift_blocks = 0, diag_blocks = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[kTimingEvents] = {};
+    bool timing = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    // host copies / extra device buffers
+    std::vector<int> wall_id_of_sorted;
+    std::vector<float> wall_xy_sorted;
+    double *diag_part = nullptr, *diag_out = nullptr, *diag_hist = nullptr;
+    long long diag_cap = 0, diag_rec = 0;
+    float *io = nullptr;  // nf x 6 floats for state transfers
+    long long host_step = 0;
+    int sticky = 0;
+};
+
+namespace {
+
+// Derived constants (FP64 on the host, then rounded once).
+void make_consts(hr_case *c)
+{
+    const hr_params &P = c->P;
+    Consts &K = c->K;
+    std::memset(&K, 0, sizeof K);
+    const double h = P.h_over_dx * P.dx;
+    const double s = 2.0 * h;
+    const double dc = s * (P.cell_factor > 1.001 ? P.cell_factor : 1.001);
+    double padx, pady;
+    if (P.box_pad > 0.0) {
+        padx = pady = P.box_pad;
+    } else {
+        padx = 0.5 * P.Lx;
+        pady = P.wall_layers > 0 ? (P.wall_layers + 2) * P.dx + s : 0.5 * P.W;
+        if (P.end_walls && P.wall_layers > 0) padx = (P.wall_layers + 2) * P.dx + s;
+    }
+    const double xlo = -padx, xhi = P.Lx + padx, ylo = -0.5 * P.W - pady, yhi = 0.5 * P.W + pady;
+    K.x0 = (float)(xlo - dc);
+    K.y0 = (float)(ylo - dc);
+    K.inv_dc = (float)(1.0 / dc);
+    K.ncx = (int)std::floor((xhi - xlo) / dc) + 3;
+    K.ncy = (int)std::floor((yhi - ylo) / dc) + 3;
+    K.ncell = K.ncx * K.ncy;
+    K.xlo = (float)xlo;
+    K.xhi = (float)xhi;
+    K.ylo = (float)ylo;
+    K.yhi = (float)yhi;
+    K.W2 = (float)(0.5 * P.W);
+    K.Lx = (float)P.Lx;
+    K.side_walls = P.wall_layers > 0;
+    K.end_walls = P.end_walls && P.wall_layers > 0;
+    const double ad = 7.0 / (4.0 * M_PI * h * h);
+    K.h = (float)h;
+    K.s2 = (float)(s * s);
+    K.half_inv_h = (float)(0.5 / h);
+    K.two_inv_h = (float)(2.0 / h);
+    K.Wc = (float)ad;
+    K.Fc = (float)(-5.0 * ad / (h * h));
+    K.m = (float)(P.rho0 * P.dx * P.dx);
+    K.rho0 = (float)P.rho0;
+    K.inv_rho0 = (float)(1.0 / P.rho0);
+    K.B = (float)(P.rho0 * P.c0 * P.c0 / P.gamma);
+    K.c0 = (float)P.c0;
+    K.p_cav = (float)std::max(P.p_cav, -1e30);
+    K.alpha_h = (float)(P.alpha * h);
+    K.eh2 = (float)(P.eta2 * h * h);
+    K.nu4 = (float)(4.0 * P.mu_lam / P.rho0);
+    K.eps_xsph = (float)P.eps_xsph;
+    K.gx = (float)P.gx;
+    K.gy = (float)P.gy;
+    K.d_lo = (float)(P.rho_lo - 1.0);
+    K.d_hi = (float)(P.rho_hi - 1.0);
+    K.gamma = (float)P.gamma;
+    K.half_gm1 = (float)(0.5 * (P.gamma - 1.0));
+    K.inv_rho0c02 = (float)(1.0 / (P.rho0 * P.c0 * P.c0));
+    K.gamma7 = P.gamma == 7.0;
+    K.nf = (int)c->nf;
+    K.nw = (int)c->nw;
+    K.ng = (int)c->ng;
+    K.m_wall = (float)(P.rho0 * P.dx * P.dx);
+    K.m_disk = P.Ng > 0 ? (float)(P.rho0 * P.dx * (2.0 * M_PI * P.R_disk / (double)P.Ng)) : 0.f;
+    K.R = (float)P.R_disk;
+    K.R2 = (float)(P.R_disk * P.R_disk);
+    const double reach = P.R_disk + 1.02 * s;
+    K.disk_reach2 = (float)(reach * reach);
+    K.cfl_h = P.cfl * h;
+    K.c0d = P.c0;
+    K.v0 = P.v0;
+    K.tau = P.tau;
+    K.t_ramp = P.t_ramp;
+    K.x_c0 = P.x_c0;
+    K.y_c0 = P.y_c0;
+    K.a_const = P.a_const;
+    K.drag_k = P.motion == 1 ? P.drag_Cd * P.rho0 * M_PI * P.drag_R * P.drag_R / (2.0 * P.drag_M)
+                             : 0.0;
+    K.dt_mode = P.dt_mode;
+    K.motion = P.motion;
+    K.n_probes = P.n_probes;
+    for (int k = 0; k < P.n_probes; ++k) {
+        K.probe_x[k] = (float)P.probe_xy[2 * k];
+        K.probe_y[k] = (float)P.probe_xy[2 * k + 1];
+    }
+    K.probe_cap = P.probe_capacity > 0 ? P.probe_capacity : (1LL << 16);
+    c->drift_blocks = (int)((c->nf + 255) / 256);
+    c->pass_blocks = (int)((c->nf + kPassThreads - 1) / kPassThreads);
+    c->ghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + 255) / 256);
+    c->n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
+    c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
+    K.n_pass_blocks = c->pass_blocks;
+    K.n_ghost_blocks = c->ghost_blocks;
+}
+
+struct Offsets {
+    size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_acc, st_X, u_pos, u_vel, u_rd,
+        u_id, u_key, u_slot, cell_count, cell_start, tile_sum, perm_tmp, gw_pos, gw_nrm,
+        gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
+        probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io;
+    size_t total;
+};
+
+Offsets plan(const hr_case *c)
+{
+    const Consts &K = c->K;
+    const size_t n = (size_t)c->nf, ng = (size_t)(c->nw + c->ng), nc = (size_t)K.ncell;
+    Layout L;
+    Offsets o;
+    o.s_pos = L.add(n * 8);
+    o.s_vel = L.add(n * 8);
+    o.s_aux = L.add(n * 16);
+    o.s_rd = L.add(n * 8);
+    o.s_id = L.add(n * 4);
+    o.st_vel = L.add(n * 8);
+    o.st_rho = L.add(n * 4);
+    o.st_acc = L.add(n * 16);
+    o.st_X = L.add(n * 8);
+    o.u_pos = L.add(n * 8);
+    o.u_vel = L.add(n * 8);
+    o.u_rd = L.add(n * 16);
+    o.u_id = L.add(n * 4);
+    o.u_key = L.add(n * 4);
+    o.u_slot = L.add(n * 4);
+    o.cell_count = L.add((nc + 1) * 4);
+    o.cell_start = L.add((nc + 2) * 4);
+    o.tile_sum = L.add((size_t)c->n_tiles * 4);
+    o.perm_tmp = L.add(n * 4);
+    o.gw_pos = L.add((size_t)c->nw * 8);
+    o.gw_nrm = L.add((size_t)c->nw * 8);
+    o.gw_kind = L.add((size_t)c->nw * 4);
+    o.gw_id = L.add((size_t)c->nw * 4);
+    o.wall_start = L.add((nc + 1) * 4);
+    o.disk_off = L.add((size_t)c->ng * 16);
+    o.gd_pos = L.add((size_t)c->ng * 8);
+    o.g_vel = L.add(ng * 8);
+    o.g_aux = L.add(ng * 16);
+    o.ghost_vmax = L.add((size_t)c->ghost_blocks * 4);
+    o.pass_part = L.add((size_t)c->pass_blocks * sizeof(PassPartial));
+    o.probe_hist = L.add((size_t)K.probe_cap * (size_t)std::max(K.n_probes, 1) * 4);
+    o.probe_t = L.add((size_t)K.probe_cap * 8);
+    o.S = L.add(sizeof(Scalars));
+    o.diag_part = L.add((size_t)c->diag_blocks * 16 * 8);
+    o.diag_out = L.add(kDiagFields * 8);
+    const long long dcap = c->P.diag_every > 0 ? 4096 : 1;
+    o.diag_hist = L.add((size_t)dcap * kDiagFields * 8);
+    o.io = L.add(n * 6 * 4);
+    o.total = L.total;
+    return o;
+}
+
+template <class T>
+T *at(void *base, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+void bind(hr_case *c, const Offsets &o)
+{
+    void *w = c->ws;
+    Bufs &B = c->B;
+    B.s_pos = at<float2>(w, o.s_pos);
+    B.s_vel = at<float2>(w, o.s_vel);
+    B.s_aux = at<float4>(w, o.s_aux);
+    B.s_rd = at<float2>(w, o.s_rd);
+    B.s_id = at<int>(w, o.s_id);
+    B.st_vel = at<float2>(w, o.st_vel);
+    B.st_rho = at<float>(w, o.st_rho);
+    B.st_acc = at<float4>(w, o.st_acc);
+    B.st_X = at<float2>(w, o.st_X);
+    B.u_pos = at<float2>(w, o.u_pos);
+    B.u_vel = at<float2>(w, o.u_vel);
+    B.u_rd = at<float4>(w, o.u_rd);
+    B.u_id = at<int>(w, o.u_id);
+    B.u_key = at<int>(w, o.u_key);
+    B.u_slot = at<int>(w, o.u_slot);
+    B.cell_count = at<int>(w, o.cell_count);
+    B.cell_start = at<int>(w, o.cell_start);
+    B.tile_sum = at<int>(w, o.tile_sum);
+    B.perm_tmp = at<int>(w, o.perm_tmp);
+    B.gw_pos = at<float2>(w, o.gw_pos);
+    B.gw_nrm = at<float2>(w, o.gw_nrm);
+    B.gw_kind = at<int>(w, o.gw_kind);
+    B.gw_id = at<int>(w, o.gw_id);
+    B.wall_start = at<int>(w, o.wall_start);
+    B.disk_off = at<double2>(w, o.disk_off);
+    B.gd_pos = at<float2>(w, o.gd_pos);
+    B.g_vel = at<float2>(w, o.g_vel);
+    B.g_aux = at<float4>(w, o.g_aux);
+    B.ghost_vmax = at<float>(w, o.ghost_vmax);
+    B.pass_part = at<PassPartial>(w, o.pass_part);
+    B.probe_hist = at<float>(w, o.probe_hist);
+    B.probe_t = at<double>(w, o.probe_t);
+    B.S = at<Scalars>(w, o.S);
+    c->diag_part = at<double>(w, o.diag_part);
+    c->diag_out = at<double>(w, o.diag_out);
+    c->diag_hist = at<double>(w, o.diag_hist);
+    c->diag_cap = c->P.diag_every > 0 ? 4096 : 1;
+    c->io = at<float>(w, o.io);
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) {                                    \
+            std::fprintf(stderr, "hram: %s failed: %s\n", #call,    \
+                         cudaGetErrorString(e_));                   \
+            return HR_ECUDA;                                        \
+        }                                                           \
+    } while (0)
+
+// The kernels of one step (prime = 1: evaluate without advancing).
+int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events)
+{
+    const Consts &K = c->K;
+    const Bufs &B = c->B;
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
+    k_scan_tiles<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
+    k_scan_mid<<<1, kScanThreads, 0, s>>>(K, B, c->n_tiles, prime);
+    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
+    k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
+    k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B);
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
+    k_ghost<<<c->ghost_blocks, 256, 0, s>>>(K, B);
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
+    k_pass<<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
+    k_finalize<<<1, kFinalizeThreads, 0, s>>>(K, B, prime);
+    if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
+    CK(cudaGetLastError());
+    return HR_OK;
+}
+
+int capture(hr_case *c)
+{
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_step(c, c->cap, 0, c->timing);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (rc != HR_OK) return rc;
+    CK(e);
+    c->graph = g;
+    CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    return HR_OK;
+}
+
+int device_status(hr_case *c)
+{
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    int st = 0;
+    CK(cudaMemcpy(&st, &c->B.S->status, sizeof(int), cudaMemcpyDeviceToHost));
+    int rc = st & (HR_WPENETRATION | HR_WOUTSIDE | HR_WPROBEFULL);
+    if (st & ST_NAN) rc = HR_ENAN;
+    else if (st & ST_DT) rc = HR_EDT;
+    if (rc < 0) c->sticky = rc;
+    return c->sticky < 0 ? c->sticky : rc;
+}
+
+// Uploads a fluid state in ID order (identity permutation), zero derivatives.
+int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho)
+{
+    const size_t n = (size_t)c->nf;
+    std::vector<float> d(n), v(2 * n, 0.0f);
+    std::vector<int> id(n);
+    std::iota(id.begin(), id.end(), 0);
+    for (size_t i = 0; i < n; ++i) d[i] = rho ? (float)((double)rho[i] / c->P.rho0 - 1.0) : 0.0f;
+    if (vel) std::memcpy(v.data(), vel, 2 * n * sizeof(float));
+    CK(cudaMemcpyAsync(c->B.s_pos, xy, n * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B.st_vel, v.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B.st_rho, d.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->B.st_acc, 0, n * 16, c->stream));
+    CK(cudaMemsetAsync(c->B.st_X, 0, n * 8, c->stream));
+    CK(cudaMemsetAsync(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4, c->stream));
+    Scalars S;
+    std::memset(&S, 0, sizeof S);
+    CK(cudaMemcpyAsync(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->host_step = 0;
+    c->diag_rec = 0;
+    c->sticky = 0;
+    return HR_OK;
+}
+
+int prime(hr_case *c)
+{
+    const int rc = launch_step(c, c->stream, 1, false);
+    if (rc != HR_OK) return rc;
+    return device_status(c);
+}
+
+int build_walls(hr_case *c, const Geometry &G)
+{
+    const int nw = (int)c->nw;
+    if (nw == 0) {
+        std::vector<int> ws((size_t)c->K.ncell + 1, 0);
+        CK(cudaMemcpy(c->B.wall_start, ws.data(), ws.size() * 4, cudaMemcpyHostToDevice));
+        return HR_OK;
+    }
+    std::vector<float2> pos(nw);
+    for (int k = 0; k < nw; ++k) pos[k] = make_float2((float)G.wx[k], (float)G.wy[k]);
+    // keys with the device's cell arithmetic
+    int *dkey = nullptr;
+    float2 *dpos = nullptr;
+    CK(cudaMalloc(&dkey, nw * 4));
+    CK(cudaMalloc(&dpos, nw * 8));
+    CK(cudaMemcpy(dpos, pos.data(), nw * 8, cudaMemcpyHostToDevice));
+    k_wall_keys<<<(nw + 255) / 256, 256>>>(c->K, dpos, nw, dkey);
+    std::vector<int> key(nw);
+    cudaError_t e = cudaMemcpy(key.data(), dkey, nw * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dkey);
+    cudaFree(dpos);
+    CK(e);
+    std::vector<int> order(nw);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::vector<float2> spos(nw), snrm(nw);
+    std::vector<int> skind(nw), sid(nw), start((size_t)c->K.ncell + 1, 0);
+    for (int k = 0; k < nw; ++k) {
+        const int o = order[k];
+        spos[k] = pos[o];
+        snrm[k] = make_float2((float)G.wnx[o], (float)G.wny[o]);
+        skind[k] = G.wkind[o];
+        sid[k] = o;
+        start[key[o] + 1]++;
+    }
+    for (int q = 0; q < c->K.ncell; ++q) start[q + 1] += start[q];
+    c->wall_id_of_sorted = sid;
+    CK(cudaMemcpy(c->B.gw_pos, spos.data(), nw * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.gw_nrm, snrm.data(), nw * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.gw_kind, skind.data(), nw * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.gw_id, sid.data(), nw * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.wall_start, start.data(), start.size() * 4, cudaMemcpyHostToDevice));
+    return HR_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+
+extern "C" {
+
+int hr_workspace_bytes(const hr_params *p, int64_t n_fluid, size_t *bytes)
+{
+    if (!bytes) return HR_EINVAL;
+    const int v = validate(p, n_fluid);
+    if (v != HR_OK) return v;
+    hr_case tmp;
+    tmp.P = *p;
+    tmp.nf = n_fluid;
+    tmp.nw = (long long)make_walls(*p).wx.size();
+    tmp.ng = p->Ng;
+    make_consts(&tmp);
+    *bytes = plan(&tmp).total;
+    return HR_OK;
+}
+
+int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const float *vel,
+                 const float *rho, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+                 hr_case **out)
+{
+    if (!out) return HR_EINVAL;
+    *out = nullptr;
+    if (!xy) return HR_EINVAL;
+    int rc = validate(p, n_fluid);
+    if (rc != HR_OK) return rc;
+    hr_case *c = new hr_case();
+    c->P = *p;
+    c->nf = n_fluid;
+    const Geometry G = make_walls(*p);
+    c->nw = (long long)G.wx.size();
+    c->ng = p->Ng;
+    make_consts(c);
+    const Offsets o = plan(c);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->timing = (p->flags & HR_FLAG_TIMING) != 0;
+    auto fail = [&](int code) {
+        hr_destroy(c);
+        return code;
+    };
+    if (d_workspace) {
+        if (workspace_bytes < o.total) return fail(HR_ENOMEM);
+        c->ws = d_workspace;
+        c->ws_bytes = workspace_bytes;
+    } else {
+        if (cudaMalloc(&c->ws, o.total) != cudaSuccess) {
+            cudaGetLastError();
+            c->ws = nullptr;
+            return fail(HR_ENOMEM);
+        }
+        c->own_ws = true;
+        c->ws_bytes = o.total;
+    }
+    bind(c, o);
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(HR_ECUDA);
+    for (int k = 0; k < kTimingEvents; ++k)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(HR_ECUDA);
+    if ((rc = build_walls(c, G)) != HR_OK) return fail(rc);
+    if (c->ng > 0) {
+        std::vector<double2> off((size_t)c->ng);
+        for (long long k = 0; k < c->ng; ++k) {
+            const double th = 2.0 * M_PI * (double)k / (double)c->ng;
+            off[k] = make_double2(p->R_disk * std::cos(th), p->R_disk * std::sin(th));
+        }
+        if (cudaMemcpy(c->B.disk_off, off.data(), off.size() * 16, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(HR_ECUDA);
+    }
+    if ((rc = upload_state(c, xy, vel, rho)) != HR_OK) return fail(rc);
+    rc = prime(c);
+    if (rc < 0) return fail(rc);
+    const int rc2 = capture(c);
+    if (rc2 != HR_OK) return fail(rc2);
+    *out = c;
+    return rc;
+}
+
+int hr_step(hr_case *c)
+{
+    if (!c || !c->exec) return HR_EINVAL;
+    if (c->sticky < 0) return c->sticky;
+    if (cudaGraphLaunch(c->exec, c->stream) != cudaSuccess) return c->sticky = HR_ECUDA;
+    c->host_step++;
+    if (c->P.diag_every > 0 && c->host_step % c->P.diag_every == 0) {
+        k_diag_partial<<<c->diag_blocks, kDiagThreads, 0, c->stream>>>(c->K, c->B, c->diag_part);
+        k_diag_final<<<1, 32, 0, c->stream>>>(c->K, c->B, c->diag_part, c->diag_blocks,
+                                              c->diag_out, c->diag_hist, c->diag_rec,
+                                              c->diag_cap);
+        c->diag_rec++;
+    }
+    return HR_OK;
+}
+
+int hr_sync(hr_case *c)
+{
+    if (!c) return HR_EINVAL;
+    return device_status(c);
+}
+
+int hr_run(hr_case *c, int64_t n_steps, double t_end)
+{
+    if (!c) return HR_EINVAL;
+    if (t_end <= 0.0) {
+        for (int64_t k = 0; k < n_steps; ++k) {
+            const int rc = hr_step(c);
+            if (rc < 0) return rc;
+        }
+        return device_status(c);
+    }
+    int64_t done = 0;
+    for (;;) {
+        double sc[2];
+        if (cudaMemcpyAsync(sc, &c->B.S->t, 16, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return HR_ECUDA;
+        const int st = device_status(c);
+        if (st < 0) return st;
+        if (sc[0] >= t_end || (n_steps > 0 && done >= n_steps)) return st;
+        // steps that cannot overshoot t_end: dt only shrinks by the CFL gate
+        int64_t k = (int64_t)std::floor((t_end - sc[0]) / sc[1]);
+        k = std::max<int64_t>(1, std::min<int64_t>(k / 2, 256));
+        if (n_steps > 0) k = std::min<int64_t>(k, n_steps - done);
+        for (int64_t q = 0; q < k; ++q) {
+            const int rc = hr_step(c);
+            if (rc < 0) return rc;
+        }
+        done += k;
+    }
+}
+
+int hr_probe_pressure(hr_case *c, float *host_out, int64_t cap_rows, int64_t *n_rows)
+{
+    if (!c) return HR_EINVAL;
+    const int st = device_status(c);
+    long long n = 0;
+    if (cudaMemcpy(&n, &c->B.S->hist_n, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (n_rows) *n_rows = n;
+    if (host_out && c->K.n_probes > 0) {
+        if (cap_rows < n) return HR_ERANGE;
+        if (n > 0 && cudaMemcpy(host_out, c->B.probe_hist, (size_t)n * c->K.n_probes * 4,
+                                cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HR_ECUDA;
+    }
+    return st;
+}
+
+int hr_probe_times(hr_case *c, double *host_out, int64_t cap, int64_t *n_out)
+{
+    if (!c) return HR_EINVAL;
+    const int st = device_status(c);
+    long long n = 0;
+    if (cudaMemcpy(&n, &c->B.S->hist_n, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (n_out) *n_out = n;
+    if (host_out) {
+        if (cap < n) return HR_ERANGE;
+        if (n > 0 &&
+            cudaMemcpy(host_out, c->B.probe_t, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HR_ECUDA;
+    }
+    return st;
+}
+
+int hr_diagnostics(hr_case *c, hr_diag *out)
+{
+    if (!c || !out) return HR_EINVAL;
+    k_diag_partial<<<c->diag_blocks, kDiagThreads, 0, c->stream>>>(c->K, c->B, c->diag_part);
+    k_diag_final<<<1, 32, 0, c->stream>>>(c->K, c->B, c->diag_part, c->diag_blocks, c->diag_out,
+                                          c->diag_hist, -1, c->diag_cap);
+    const int st = device_status(c);
+    double d[kDiagFields];
+    if (cudaMemcpy(d, c->diag_out, sizeof d, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HR_ECUDA;
+    std::memcpy(out, d, sizeof d);
+    return st;
+}
+
+int hr_diag_history(hr_case *c, double *host_out, int64_t cap_rows, int64_t *n_rows)
+{
+    if (!c) return HR_EINVAL;
+    const int st = device_status(c);
+    const long long n = std::min(c->diag_rec, c->diag_cap);
+    if (n_rows) *n_rows = n;
+    if (host_out) {
+        if (cap_rows < n) return HR_ERANGE;
+        if (n > 0 && cudaMemcpy(host_out, c->diag_hist, (size_t)n * kDiagFields * 8,
+                                cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HR_ECUDA;
+    }
+    return st;
+}
+
+int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_t cap)
+{
+    if (!c) return HR_EINVAL;
+    if (cap < c->nf) return HR_ERANGE;
+    const size_t n = (size_t)c->nf;
+    float2 *dxy = reinterpret_cast<float2 *>(c->io);
+    float2 *dv = dxy + n;
+    float *dr = reinterpret_cast<float *>(dv + n);
+    float *dp = dr + n;
+    k_unsort<<<c->drift_blocks, 256, 0, c->stream>>>(c->K, c->B, dxy, dv, dr, dp);
+    const int st = device_status(c);
+    if (st < 0 && st != HR_ENAN) return st;
+    if (xy && cudaMemcpy(xy, dxy, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (vel && cudaMemcpy(vel, dv, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (rho && cudaMemcpy(rho, dr, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (p && cudaMemcpy(p, dp, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    return st;
+}
+
+int hr_set_state(hr_case *c, const float *xy, const float *vel, const float *rho, int64_t n)
+{
+    if (!c || !xy || n != c->nf) return HR_EINVAL;
+    const int s0 = device_status(c);
+    if (s0 == HR_ECUDA) return s0;
+    int rc = upload_state(c, xy, vel, rho);
+    if (rc != HR_OK) return rc;
+    return prime(c);
+}
+
+int hr_get_ghosts(hr_case *c, float *xy, float *p, float *rho, float *vel, int64_t cap)
+{
+    if (!c) return HR_EINVAL;
+    const long long ngh = c->nw + c->ng;
+    if (cap < ngh) return HR_ERANGE;
+    const int st = device_status(c);
+    std::vector<float2> gv((size_t)ngh), gpw((size_t)c->nw), gpd((size_t)c->ng);
+    std::vector<float4> ga((size_t)ngh);
+    if (ngh > 0) {
+        if (cudaMemcpy(gv.data(), c->B.g_vel, ngh * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ga.data(), c->B.g_aux, ngh * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HR_ECUDA;
+    }
+    if (c->nw > 0 &&
+        cudaMemcpy(gpw.data(), c->B.gw_pos, c->nw * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HR_ECUDA;
+    if (c->ng > 0 &&
+        cudaMemcpy(gpd.data(), c->B.gd_pos, c->ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HR_ECUDA;
+    for (long long k = 0; k < ngh; ++k) {
+        const long long dst = k < c->nw ? c->wall_id_of_sorted[k] : k;
+        const float2 pos = k < c->nw ? gpw[k] : gpd[k - c->nw];
+        if (xy) { xy[2 * dst] = pos.x; xy[2 * dst + 1] = pos.y; }
+        if (p) p[dst] = ga[k].y;
+        if (rho) rho[dst] = c->K.rho0 * (1.0f + ga[k].x);
+        if (vel) { vel[2 * dst] = gv[k].x; vel[2 * dst + 1] = gv[k].y; }
+    }
+    return st;
+}
+
+int hr_get_scalars(hr_case *c, double *out, int n)
+{
+    if (!c || !out) return HR_EINVAL;
+    const int st = device_status(c);
+    Scalars S;
+    if (cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    const double v[14] = {S.t, S.dt, (double)S.step, S.xc, S.yc, S.vproj, S.aproj, S.Fdx,
+                          S.Fdy, S.Fwall, S.Wb, S.impulse, S.diss, S.diss_rate};
+    for (int k = 0; k < n && k < 14; ++k) out[k] = v[k];
+    return st;
+}
+
+int hr_case_info(hr_case *c, int64_t *out, int n)
+{
+    if (!c || !out) return HR_EINVAL;
+    const int64_t v[6] = {c->nf, c->nw, c->ng, c->K.ncx, c->K.ncy, c->pass_blocks};
+    for (int k = 0; k < n && k < 6; ++k) out[k] = v[k];
+    return HR_OK;
+}
+
+int hr_debug_neighbors(hr_case *c, int64_t *offsets, int32_t *ids, int64_t cap, int64_t *n_pairs)
+{
+    if (!c || !offsets) return HR_EINVAL;
+    const long long npts = c->nf + c->nw + c->ng;
+    int *dcount = nullptr;
+    long long *doff = nullptr;
+    int *dids = nullptr;
+    if (cudaMalloc(&dcount, npts * 4) != cudaSuccess) return HR_ENOMEM;
+    const int blocks = (int)((npts + 255) / 256);
+    k_neighbors<<<blocks, 256, 0, c->stream>>>(c->K, c->B, dcount, nullptr, nullptr);
+    std::vector<int> cnt((size_t)npts);
+    std::vector<int> sid((size_t)c->nf);
+    int st = device_status(c);
+    if (cudaMemcpy(cnt.data(), dcount, npts * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(sid.data(), c->B.s_id, c->nf * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaFree(dcount);
+        return HR_ECUDA;
+    }
+    std::vector<long long> off((size_t)npts + 1, 0);
+    for (long long r = 0; r < npts; ++r) off[r + 1] = off[r] + cnt[r];
+    const long long total = off[npts];
+    if (n_pairs) *n_pairs = total;
+    // row index in global point order for each kernel row
+    std::vector<long long> grow((size_t)npts);
+    for (long long r = 0; r < c->nf; ++r) grow[r] = sid[r];
+    for (long long k = 0; k < c->nw; ++k) grow[c->nf + k] = c->nf + c->wall_id_of_sorted[k];
+    for (long long k = 0; k < c->ng; ++k) grow[c->nf + c->nw + k] = c->nf + c->nw + k;
+    std::vector<long long> goff((size_t)npts + 1, 0);
+    for (long long r = 0; r < npts; ++r) goff[grow[r] + 1] = cnt[r];
+    for (long long r = 0; r < npts; ++r) goff[r + 1] += goff[r];
+    for (long long r = 0; r <= npts; ++r) offsets[r] = goff[r];
+    if (!ids) {
+        cudaFree(dcount);
+        return st;
+    }
+    if (cap < total) {
+        cudaFree(dcount);
+        return HR_ERANGE;
+    }
+    if (cudaMalloc(&doff, (npts + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&dids, std::max<long long>(total, 1) * 4) != cudaSuccess) {
+        cudaFree(dcount);
+        cudaFree(doff);
+        return HR_ENOMEM;
+    }
+    cudaMemcpy(doff, off.data(), (npts + 1) * 8, cudaMemcpyHostToDevice);
+    k_neighbors<<<blocks, 256, 0, c->stream>>>(c->K, c->B, dcount, doff, dids);
+    st = device_status(c);
+    std::vector<int> raw((size_t)std::max<long long>(total, 1));
+    const cudaError_t e = cudaMemcpy(raw.data(), dids, total * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dcount);
+    cudaFree(doff);
+    cudaFree(dids);
+    if (e != cudaSuccess) return HR_ECUDA;
+    for (long long r = 0; r < npts; ++r) {
+        int32_t *dst = ids + goff[grow[r]];
+        std::memcpy(dst, raw.data() + off[r], (size_t)cnt[r] * 4);
+        std::sort(dst, dst + cnt[r]);
+    }
+    return st;
+}
+
+int hr_kernel_times(hr_case *c, float *ms, int n)
+{
+    if (!c || !ms) return HR_EINVAL;
+    if (!c->timing) return HR_EINVAL;
+    const int st = device_status(c);
+    for (int k = 0; k < n && k < kTimingEvents - 1; ++k)
+        if (cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]) != cudaSuccess) return HR_ECUDA;
+    return st;
+}
+
+// Checkpoint file: magic, counts, params, scalars, state in ID order, probes.
+int hr_save_state(hr_case *c, const char *path)
+{
+    if (!c || !path) return HR_EINVAL;
+    const int st = device_status(c);
+    if (st < 0) return st;
+    const size_t n = (size_t)c->nf;
+    // ID-order copies through the io buffer
+    std::vector<float2> pos(n), vel(n), X(n);
+    std::vector<float> d(n);
+    std::vector<float4> acc(n);
+    std::vector<int> sid(n);
+    Scalars S;
+    if (cudaMemcpy(sid.data(), c->B.s_id, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pos.data(), c->B.s_pos, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(vel.data(), c->B.st_vel, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(X.data(), c->B.st_X, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(d.data(), c->B.st_rho, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(acc.data(), c->B.st_acc, n * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HR_ECUDA;
+    std::vector<float2> pos2(n), vel2(n), X2(n);
+    std::vector<float> d2(n);
+    std::vector<float4> acc2(n);
+    for (size_t i = 0; i < n; ++i) {
+        const int id = sid[i];
+        pos2[id] = pos[i];
+        vel2[id] = vel[i];
+        X2[id] = X[i];
+        d2[id] = d[i];
+        acc2[id] = acc[i];
+    }
+    const long long hn = std::min<long long>(S.hist_n, c->K.probe_cap);
+    std::vector<float> ph((size_t)hn * std::max(c->K.n_probes, 1));
+    std::vector<double> pt((size_t)hn);
+    if (hn > 0 && c->K.n_probes > 0 &&
+        (cudaMemcpy(ph.data(), c->B.probe_hist, ph.size() * 4, cudaMemcpyDeviceToHost) !=
+             cudaSuccess ||
+         cudaMemcpy(pt.data(), c->B.probe_t, pt.size() * 8, cudaMemcpyDeviceToHost) !=
+             cudaSuccess))
+        return HR_ECUDA;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return HR_EIO;
+    const char magic[8] = {'H', 'R', 'A', 'M', 'C', 'K', '0', '1'};
+    const long long hdr[4] = {c->nf, c->nw, c->ng, hn};
+    bool ok = std::fwrite(magic, 8, 1, f) == 1 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              std::fwrite(&c->P, sizeof c->P, 1, f) == 1 && std::fwrite(&S, sizeof S, 1, f) == 1 &&
+              std::fwrite(pos2.data(), 8, n, f) == n && std::fwrite(vel2.data(), 8, n, f) == n &&
+              std::fwrite(d2.data(), 4, n, f) == n && std::fwrite(acc2.data(), 16, n, f) == n &&
+              std::fwrite(X2.data(), 8, n, f) == n &&
+              std::fwrite(&c->host_step, 8, 1, f) == 1;
+    if (ok && hn > 0 && c->K.n_probes > 0)
+        ok = std::fwrite(ph.data(), 4, ph.size(), f) == ph.size() &&
+             std::fwrite(pt.data(), 8, pt.size(), f) == pt.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? st : HR_EIO;
+}
+
+int hr_load_state(hr_case *c, const char *path)
+{
+    if (!c || !path) return HR_EINVAL;
+    device_status(c);
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return HR_EIO;
+    char magic[8];
+    long long hdr[4];
+    hr_params P;
+    Scalars S;
+    const size_t n = (size_t)c->nf;
+    bool ok = std::fread(magic, 8, 1, f) == 1 && std::memcmp(magic, "HRAMCK01", 8) == 0 &&
+              std::fread(hdr, sizeof hdr, 1, f) == 1 && std::fread(&P, sizeof P, 1, f) == 1 &&
+              std::fread(&S, sizeof S, 1, f) == 1;
+    ok = ok && hdr[0] == c->nf && hdr[1] == c->nw && hdr[2] == c->ng;
+    hr_params a = P, b = c->P;
+    a.flags = b.flags = 0;
+    a.diag_every = b.diag_every = 0;
+    ok = ok && std::memcmp(&a, &b, sizeof a) == 0;
+    std::vector<float2> pos(n), vel(n), X(n);
+    std::vector<float> d(n);
+    std::vector<float4> acc(n);
+    long long hstep = 0;
+    ok = ok && std::fread(pos.data(), 8, n, f) == n && std::fread(vel.data(), 8, n, f) == n &&
+         std::fread(d.data(), 4, n, f) == n && std::fread(acc.data(), 16, n, f) == n &&
+         std::fread(X.data(), 8, n, f) == n && std::fread(&hstep, 8, 1, f) == 1;
+    const long long hn = ok ? hdr[3] : 0;
+    std::vector<float> ph((size_t)hn * std::max(c->K.n_probes, 1));
+    std::vector<double> pt((size_t)hn);
+    if (ok && hn > 0 && c->K.n_probes > 0)
+        ok = std::fread(ph.data(), 4, ph.size(), f) == ph.size() &&
+             std::fread(pt.data(), 8, pt.size(), f) == pt.size();
+    std::fclose(f);
+    if (!ok) return HR_EIO;
+    std::vector<int> id(n);
+    std::iota(id.begin(), id.end(), 0);
+    CK(cudaMemcpy(c->B.s_pos, pos.data(), n * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.st_vel, vel.data(), n * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.st_rho, d.data(), n * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.st_acc, acc.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.st_X, X.data(), n * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4));
+    CK(cudaMemcpy(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice));
+    if (hn > 0 && c->K.n_probes > 0) {
+        CK(cudaMemcpy(c->B.probe_hist, ph.data(), ph.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->B.probe_t, pt.data(), pt.size() * 8, cudaMemcpyHostToDevice));
+    }
+    c->host_step = hstep;
+    c->sticky = 0;
+    return device_status(c);
+}
+
+void hr_destroy(hr_case *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (int k = 0; k < kTimingEvents; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+}
+
+const char *hr_status_str(int s)
+{
+    switch (s) {
+    case HR_OK: return "ok";
+    case HR_EINVAL: return "invalid argument";
+    case HR_ENOMEM: return "out of device memory or workspace too small";
+    case HR_ECUDA: return "CUDA error";
+    case HR_ENAN: return "NaN or Inf in the fluid state";
+    case HR_EDT: return "time step underflow";
+    case HR_ERANGE: return "buffer too small";
+    case HR_EIO: return "checkpoint file error";
+    default: break;
+    }
+    if (s > 0) return "warning (see HR_W* bits)";
+    return "unknown status";
+}
+
+}  // extern "C"

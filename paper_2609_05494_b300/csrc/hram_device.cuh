@@ -1,0 +1,848 @@
+// hram_device.cuh -- device data layout and kernels of the planar WCSPH
+// hydrodynamic-ram step on B300 (sm_103a).
+//
+// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is nine kernels:
+//   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key and
+//                   in-cell slot (atomic count)                  [T, first half]
+//   k_scan_tiles    \
+//   k_scan_mid       > exclusive scan of the cell counts; k_scan_mid also
+//   k_scan_apply    /  advances t and the projectile kinematics (FP64) and
+//                      places the disk ghosts
+//   k_slot           provisional scatter of old indices into cell order
+//   k_rank_scatter   stable rank by fluid ID inside the cell, SoA reorder,
+//                    Tait pressure of the predicted density
+//   k_ghost          Adami ghost extrapolation G (disk ring and wall layers)
+//   k_pass           fused interaction sums L + closing kick epilogue
+//   k_finalize       probes, FP64 accumulators, CFL gate           [T, gate]
+//
+// Densities are carried as the relative deviation d = rho/rho0 - 1 in FP32:
+// the Tait pressure B((1+d)^7 - 1) = B d (7 + 21 d + ...) then has no
+// cancellation and a pressure of 100 Pa is resolved (an FP32 rho near 1000
+// kg/m^3 resolves only 134 Pa).  Positions and velocities are FP32; time,
+// kinematics, and every global reduction are FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hr {
+
+constexpr int kMaxProbes = 16;
+constexpr int kPassThreads = 128;
+constexpr int kListCap = 24;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kFinalizeThreads = 512;
+
+// device status bits (warnings share the public HR_W* values)
+constexpr int ST_PENETRATION = 1;
+constexpr int ST_OUTSIDE = 2;
+constexpr int ST_PROBEFULL = 4;
+constexpr int ST_NAN = 256;
+constexpr int ST_DT = 512;
+
+enum GhostKind { KIND_SIDE = 1, KIND_END = 2, KIND_DISK = 3 };
+
+// Constants of a case, passed by value (kernel parameter bank).
+struct Consts {
+    // grid and box
+    float x0, y0, inv_dc;
+    int ncx, ncy, ncell;
+    float xlo, xhi, ylo, yhi;
+    float W2, Lx;
+    int side_walls, end_walls;
+    // kernel
+    float h, s2, half_inv_h, two_inv_h, Wc, Fc;
+    // fluid
+    float m, rho0, inv_rho0, B, c0, p_cav, alpha_h, eh2, nu4, eps_xsph, gx, gy;
+    float d_lo, d_hi, gamma, half_gm1, inv_rho0c02;
+    int gamma7;
+    // ghosts
+    int nf, nw, ng;
+    float m_wall, m_disk, R, disk_reach2, R2;
+    // CFL and kinematics (FP64)
+    double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k;
+    int dt_mode, motion;
+    // probes
+    int n_probes;
+    float probe_x[kMaxProbes], probe_y[kMaxProbes];
+    long long probe_cap;
+    int n_pass_blocks, n_ghost_blocks;
+};
+
+// Device-resident scalars of the case.
+struct Scalars {
+    double t, dt, dt_prev;
+    long long step;
+    double xc, yc, vproj, aproj;
+    double Fdx, Fdy, Fwall, diss_rate;
+    double Wb, impulse, diss;
+    double probe_imp[kMaxProbes];
+    long long hist_n;
+    int status;
+    int pad;
+};
+
+struct PassPartial {
+    double Fdx, Fdy, Fw, diss;
+    float vmax;
+    int npen;
+};
+
+// Device buffers of a case.  s_* are in the cell order of the current step,
+// st_* hold the end-of-step state in that same order, u_* are the drifted
+// particles before the sort (previous order).
+struct Bufs {
+    // sorted (k_rank_scatter)
+    float2 *s_pos;   // r^{n+1}
+    float2 *s_vel;   // v^{n+1/2}
+    float4 *s_aux;   // {d~, p~, p~/rho~^2, c~}   predicted density and its EOS
+    float2 *s_rd;    // {d^n, D^n}                 for the corrected density
+    int *s_id;
+    // end-of-step state (k_pass epilogue)
+    float2 *st_vel;  // v^{n+1}
+    float *st_rho;   // d^{n+1}
+    float4 *st_acc;  // {a_x, a_y, D^{n+1}, D^n}   D in units of d per second
+    float2 *st_X;    // XSPH sum X^{n+1}
+    // drifted, unsorted
+    float2 *u_pos, *u_vel;
+    float4 *u_rd;    // {d^n, d~, D^n, 0}
+    int *u_id, *u_key, *u_slot;
+    // cell list
+    int *cell_count; // ncell + 1 (last = frozen particles)
+    int *cell_start; // ncell + 2
+    int *tile_sum;
+    int *perm_tmp;
+    // wall ghosts (static, cell order) and disk ghosts
+    float2 *gw_pos;
+    float2 *gw_nrm;
+    int *gw_kind, *gw_id;
+    int *wall_start;   // ncell + 1
+    double2 *disk_off; // R (cos, sin) theta_k
+    float2 *gd_pos;
+    // ghost state: walls [0, nw), disk [nw, nw + ng)
+    float2 *g_vel;
+    float4 *g_aux;     // {d_g, p_g, p_g / rho_g^2, c_g}
+    float *ghost_vmax; // per ghost block
+    PassPartial *pass_part;
+    // probes
+    float *probe_hist;
+    double *probe_t;
+    // scalars
+    Scalars *S;
+};
+
+// ---------------------------------------------------------------- helpers
+
+// Neighbour predicate of the method: FP32, round-to-nearest, no contraction.
+__device__ __forceinline__ bool in_support(float xi, float yi, float xj, float yj, float s2)
+{
+    const float dx = __fsub_rn(xi, xj);
+    const float dy = __fsub_rn(yi, yj);
+    const float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return r2 < s2;
+}
+
+__device__ __forceinline__ int cell_of(const Consts &K, float x, float y)
+{
+    int cx = __float2int_rd(__fmul_rn(__fsub_rn(x, K.x0), K.inv_dc));
+    int cy = __float2int_rd(__fmul_rn(__fsub_rn(y, K.y0), K.inv_dc));
+    cx = min(max(cx, 1), K.ncx - 2);
+    cy = min(max(cy, 1), K.ncy - 2);
+    return cy * K.ncx + cx;
+}
+
+__device__ __forceinline__ bool outside_box(const Consts &K, float x, float y)
+{
+    return !(x >= K.xlo && x <= K.xhi && y >= K.ylo && y <= K.yhi);
+}
+
+// Tait pressure from the density deviation d, with the cavitation cutoff.
+// gamma = 7: (1+d)^7 - 1 = d (7 + 21 d + 35 d^2 + 35 d^3 + 21 d^4 + 7 d^5 + d^6).
+__device__ __forceinline__ float tait_p(const Consts &K, float d)
+{
+    float p;
+    if (K.gamma7) {
+        float poly = fmaf(d, 1.0f, 7.0f);
+        poly = fmaf(d, poly, 21.0f);
+        poly = fmaf(d, poly, 35.0f);
+        poly = fmaf(d, poly, 35.0f);
+        poly = fmaf(d, poly, 21.0f);
+        poly = fmaf(d, poly, 7.0f);
+        p = K.B * d * poly;
+    } else {
+        p = K.B * expm1f(K.gamma * log1pf(d));
+    }
+    return fmaxf(p, K.p_cav);
+}
+
+// c = c0 (rho/rho0)^((gamma-1)/2)
+__device__ __forceinline__ float sound_speed(const Consts &K, float d)
+{
+    if (K.gamma7) {
+        const float x = 1.0f + d;
+        return K.c0 * x * x * x;
+    }
+    return K.c0 * __powf(1.0f + d, K.half_gm1);
+}
+
+__device__ __forceinline__ float4 eos_record(const Consts &K, float d)
+{
+    const float p = tait_p(K, d);
+    const float rho = K.rho0 * (1.0f + d);
+    return make_float4(d, p, p / (rho * rho), sound_speed(K, d));
+}
+
+__device__ __forceinline__ float band(const Consts &K, float d)
+{
+    return fminf(fmaxf(d, K.d_lo), K.d_hi);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Projectile kinematics in closed form (FP64).  Section 2.6.3 ramp,
+// exponential decay with time constant tau (motion 0), the paper's quadratic
+// drag law after the ramp (motion 1, Section 2.7), constant acceleration
+// (motion 2).
+__device__ inline void kinematics(const Consts &K, double t, double *xo, double *vo, double *ao)
+{
+    const double v0 = K.v0, tr = K.t_ramp, tau = K.tau;
+    double x = K.x_c0, v, a;
+    if (K.motion == 2) {
+        v = K.a_const * t;
+        a = K.a_const;
+        x += 0.5 * K.a_const * t * t;
+    } else if (K.motion == 1) {
+        if (tr > 0.0 && t < tr) {
+            v = v0 * t / tr;
+            a = v0 / tr;
+            x += 0.5 * v0 * t * t / tr;
+        } else {
+            const double t1 = tr > 0.0 ? tr : 0.0;
+            const double u = 1.0 + K.drag_k * v0 * (t - t1);
+            v = v0 / u;
+            a = -K.drag_k * v * v;
+            x += 0.5 * v0 * t1 + log(u) / K.drag_k;
+        }
+    } else {
+        double f, df, e, de;
+        if (tr > 0.0 && t < tr) { f = t / tr; df = 1.0 / tr; }
+        else { f = 1.0; df = 0.0; }
+        if (tau > 0.0) { e = exp(-t / tau); de = -e / tau; }
+        else { e = 1.0; de = 0.0; }
+        v = v0 * f * e;
+        a = v0 * (df * e + f * de);
+        if (tau > 0.0) {
+            if (tr > 0.0) {
+                const double ta = t < tr ? t : tr;
+                x += (v0 / tr) * (tau * tau - tau * (ta + tau) * exp(-ta / tau));
+                if (t > tr) x += v0 * tau * (exp(-tr / tau) - exp(-t / tau));
+            } else {
+                x += v0 * tau * (1.0 - exp(-t / tau));
+            }
+        } else {
+            if (tr > 0.0) {
+                const double ta = t < tr ? t : tr;
+                x += 0.5 * v0 * ta * ta / tr;
+                if (t > tr) x += v0 * (t - tr);
+            } else {
+                x += v0 * t;
+            }
+        }
+    }
+    *xo = x;
+    *vo = v;
+    *ao = a;
+}
+
+// Candidate enumeration shared by every gather (ghost pass, interaction pass,
+// probes, debug neighbour lists): the 3x3 cell stencil of cell c is three
+// contiguous row ranges [start(row, cx-1), start(row, cx+2)) of the sorted
+// arrays.  f(j) is called for every candidate j.
+template <class F>
+__device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c, F &&f)
+{
+#pragma unroll 1
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int row = c + dy * K.ncx;
+        const int a = start[row - 1], b = start[row + 2];
+        for (int j = a; j < b; ++j) f(j);
+    }
+}
+
+// Disk ghosts are only candidates of fluid within R + 2h (with a margin) of
+// the disk centre; the ring is then scanned in full.
+__device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, float xc, float yc)
+{
+    const float dx = x - xc, dy = y - yc;
+    return dx * dx + dy * dy < K.disk_reach2;
+}
+
+// ----------------------------------------------------- a2: drift and key
+
+// Opening kick, XSPH drift, wall enforcement, predicted density and cell key.
+// prime = 1 evaluates the current state without advancing (dt = 0).
+__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    const double dtd = prime ? 0.0 : B.S->dt;
+    const double dtp = B.S->dt_prev;
+    const float dt = (float)dtd;
+    const float ratio = (!prime && dtp > 0.0) ? (float)(dtd / dtp) : 1.0f;
+    float2 r = B.s_pos[i];
+    const float2 v = B.st_vel[i];
+    const float d = B.st_rho[i];
+    const float4 a = B.st_acc[i];
+    const float2 X = B.st_X[i];
+    float2 vh;
+    float dp;
+    int key;
+    if (outside_box(K, r.x, r.y)) {
+        vh = v;
+        dp = d;
+        key = K.ncell;
+    } else {
+        vh.x = fmaf(0.5f * dt, a.x, v.x);
+        vh.y = fmaf(0.5f * dt, a.y, v.y);
+        r.x = fmaf(dt, fmaf(K.eps_xsph, X.x, vh.x), r.x);
+        r.y = fmaf(dt, fmaf(K.eps_xsph, X.y, vh.y), r.y);
+        if (K.side_walls) {
+            if (r.y > K.W2) { r.y = K.W2 - 1e-6f; vh.y = -vh.y; }
+            else if (r.y < -K.W2) { r.y = -K.W2 + 1e-6f; vh.y = -vh.y; }
+            if (K.end_walls) {
+                if (r.x > K.Lx) { r.x = K.Lx - 1e-6f; vh.x = -vh.x; }
+                else if (r.x < 0.0f) { r.x = 1e-6f; vh.x = -vh.x; }
+            }
+        }
+        // predicted density: D extrapolated linearly over the step
+        const float Dp = fmaf(ratio, a.z - a.w, a.z);
+        dp = band(K, fmaf(dt, Dp, d));
+        if (outside_box(K, r.x, r.y)) {
+            key = K.ncell;
+            atomicOr(&B.S->status, ST_OUTSIDE);
+        } else {
+            key = cell_of(K, r.x, r.y);
+        }
+    }
+    B.u_pos[i] = r;
+    B.u_vel[i] = vh;
+    B.u_rd[i] = make_float4(d, dp, a.z, 0.0f);
+    B.u_id[i] = B.s_id[i];
+    B.u_key[i] = key;
+    B.u_slot[i] = atomicAdd(&B.cell_count[key], 1);
+}
+
+// ---------------------------------------------------- a3: counting sort
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int s = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) smem_warp[lane] = s;
+    }
+    __syncthreads();
+    const int before = w > 0 ? smem_warp[w - 1] : 0;
+    *total = smem_warp[(blockDim.x >> 5) - 1];
+    return before + x - v;
+}
+
+// Tile sums of the cell counts (ncell + 1 entries).
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
+{
+    __shared__ int red[kScanThreads / 32];
+    const int n = K.ncell + 1;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s += (base + k < n) ? B.cell_count[base + k] : 0;
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) B.tile_sum[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the tile sums (one block), then the time advance and
+// the disk ghost ring at t^{n+1} (a1).
+__global__ void __launch_bounds__(kScanThreads) k_scan_mid(Consts K, Bufs B, int n_tiles, int prime)
+{
+    __shared__ int wsum[kScanThreads / 32];
+    __shared__ double kin[3];
+    int carry = 0;
+    for (int base = 0; base < n_tiles; base += kScanThreads) {
+        const int idx = base + threadIdx.x;
+        const int v = idx < n_tiles ? B.tile_sum[idx] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, wsum, &total);
+        if (idx < n_tiles) B.tile_sum[idx] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        Scalars *S = B.S;
+        if (!prime) S->t += S->dt;
+        double x, v, a;
+        kinematics(K, S->t, &x, &v, &a);
+        S->xc = x;
+        S->yc = K.y_c0;
+        S->vproj = v;
+        S->aproj = a;
+        kin[0] = x;
+        kin[1] = K.y_c0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K.ng; k += blockDim.x) {
+        const double2 o = B.disk_off[k];
+        B.gd_pos[k] = make_float2((float)(kin[0] + o.x), (float)(kin[1] + o.y));
+    }
+}
+
+// Cell starts: per-tile exclusive scan plus the tile offset; counts reset.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
+{
+    __shared__ int wsum[kScanThreads / 32];
+    const int n = K.ncell + 1;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, wsum, &total) + B.tile_sum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) {
+            B.cell_start[base + k] = ex;
+            B.cell_count[base + k] = 0;
+        }
+        ex += v[k];
+    }
+    if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
+}
+
+__global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    B.perm_tmp[B.cell_start[B.u_key[i]] + B.u_slot[i]] = i;
+}
+
+// Stable order inside a cell: rank by fluid ID among the cell's members.
+// Then the reorder into the SoA arrays of this step, with the Tait
+// pressure of the predicted density.
+__global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    const int key = B.u_key[i];
+    const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
+    const int id = B.u_id[i];
+    int rank = 0;
+    for (int k = cs; k < ce; ++k) rank += B.u_id[B.perm_tmp[k]] < id;
+    const int dst = cs + rank;
+    const float4 rd = B.u_rd[i];
+    B.s_pos[dst] = B.u_pos[i];
+    B.s_vel[dst] = B.u_vel[i];
+    B.s_aux[dst] = eos_record(K, rd.y);
+    B.s_rd[dst] = make_float2(rd.x, rd.z);
+    B.s_id[dst] = id;
+}
+
+// ------------------------------------------------------- a4: ghosts G
+
+// Adami extrapolation (eqs. adami-p, adami-v) for wall ghosts [0, nw) and
+// disk ghosts [nw, nw + ng), over fluid neighbours in the 3x3 cell stencil:
+//   p_g = max((S_p + (g - a_w) . S_rr) / S_W, p_cav),
+//   rho_g = rho0 (1 + p_g / (rho0 c0^2)),  v_g = 2 v_w - S_v / S_W.
+__global__ void __launch_bounds__(256) k_ghost(Consts K, Bufs B)
+{
+    __shared__ float red[8];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    float vabs = 0.0f;
+    if (g < K.nw + K.ng) {
+        const bool disk = g >= K.nw;
+        const float2 rg = disk ? B.gd_pos[g - K.nw] : B.gw_pos[g];
+        const float vwx = disk ? (float)B.S->vproj : 0.0f;
+        const float awx = disk ? (float)B.S->aproj : 0.0f;
+        float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f, Svx = 0.f, Svy = 0.f;
+        if (!outside_box(K, rg.x, rg.y)) {
+            const int c = cell_of(K, rg.x, rg.y);
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = __ldg(&B.s_pos[j]);
+                if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) return;
+                const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
+                const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
+                const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+                const float t2 = t * t;
+                const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+                const float4 aux = __ldg(&B.s_aux[j]);
+                const float2 vj = __ldg(&B.s_vel[j]);
+                const float rw = (1.0f + aux.x) * W;
+                SW += W;
+                Sp = fmaf(aux.y, W, Sp);
+                Srx = fmaf(rw, dx, Srx);
+                Sry = fmaf(rw, dy2, Sry);
+                Svx = fmaf(vj.x, W, Svx);
+                Svy = fmaf(vj.y, W, Svy);
+            });
+        }
+        float4 aux;
+        float2 vg;
+        if (SW > 0.0f) {
+            const float inv = 1.0f / SW;
+            const float bx = K.gx - awx, by = K.gy;
+            float pg = (Sp + K.rho0 * (bx * Srx + by * Sry)) * inv;
+            pg = fmaxf(pg, K.p_cav);
+            const float dg = pg * K.inv_rho0c02;
+            const float rho = K.rho0 * (1.0f + dg);
+            aux = make_float4(dg, pg, pg / (rho * rho), sound_speed(K, dg));
+            vg = make_float2(2.0f * vwx - Svx * inv, -Svy * inv);
+        } else {
+            aux = make_float4(0.0f, 0.0f, 0.0f, K.c0);
+            vg = make_float2(vwx, 0.0f);
+        }
+        B.g_aux[g] = aux;
+        B.g_vel[g] = vg;
+        if (!outside_box(K, rg.x, rg.y)) vabs = sqrtf(vg.x * vg.x + vg.y * vg.y);
+    }
+    vabs = warp_max(vabs);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vabs;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        v = warp_max(v);
+        if (threadIdx.x == 0) B.ghost_vmax[blockIdx.x] = v;
+    }
+}
+
+// --------------------------------------------- a5: fused interaction L
+
+struct Self {
+    float x, y, vx, vy, rho, P, c;
+};
+
+struct Acc {
+    float ax, ay, dr, Xx, Xy, avx, avy;
+};
+
+// One pair (i, j): continuity, momentum with artificial and laminar
+// viscosity (eqs. momentum, artificial-viscosity), XSPH when xsph.  Adds
+// m_j times the pair terms; returns the acceleration contribution of j on i.
+__device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float xj, float yj,
+                                             float vxj, float vyj, float rhoj, float Pj,
+                                             float cj, float mj, bool xsph, Acc &A)
+{
+    const float dx = I.x - xj, dy = I.y - yj;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+    const float t3 = t * t * t;
+    const float F = K.Fc * t3;                          // grad_i W = F r_ij
+    const float vx = I.vx - vxj, vy = I.vy - vyj;
+    const float vr = fmaf(vx, dx, vy * dy);
+    A.dr = fmaf(mj * F, vr, A.dr);                      // continuity
+    const float rs = I.rho + rhoj;
+    const float inv = __frcp_rn((r2 + K.eh2) * rs);     // 1 / ((r^2 + eta^2 h^2)(rho_i + rho_j))
+    const float Pi_ij = -K.alpha_h * (I.c + cj) * fminf(vr, 0.0f) * inv;  // -alpha cbar mu / rhobar
+    const float mF = mj * F;
+    const float S = -(I.P + Pj + Pi_ij) * mF;           // pressure + AV
+    const float lam = mj * K.nu4 * F * r2 * inv;        // laminar
+    const float fx = fmaf(S, dx, lam * vx);
+    const float fy = fmaf(S, dy, lam * vy);
+    A.ax += fx;
+    A.ay += fy;
+    const float av = -Pi_ij * mF;
+    A.avx = fmaf(av, dx, A.avx);
+    A.avy = fmaf(av, dy, A.avy);
+    if (xsph) {
+        const float W = K.Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f);
+        const float w = -2.0f * mj * W * inv * (r2 + K.eh2);  // -(m_j / rhobar) W
+        A.Xx = fmaf(w, vx, A.Xx);
+        A.Xy = fmaf(w, vy, A.Xy);
+    }
+    return make_float2(fx, fy);
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
+{
+    __shared__ int lst[kPassThreads / 32][kListCap][32];
+    __shared__ double red[kPassThreads / 32][4];
+    __shared__ float redv[kPassThreads / 32];
+    __shared__ int redn[kPassThreads / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double dtd = prime ? 0.0 : B.S->dt;
+    const float dt = (float)dtd;
+    double fdx = 0.0, fdy = 0.0, fw = 0.0, diss = 0.0;
+    float vmax = 0.0f;
+    int npen = 0;
+    if (i < K.nf) {
+        const float2 ri = B.s_pos[i];
+        const float2 vi = B.s_vel[i];
+        const float4 ai = B.s_aux[i];
+        const float2 rd = B.s_rd[i];
+        if (outside_box(K, ri.x, ri.y)) {
+            // frozen: keeps its state, takes part in nothing
+            B.st_vel[i] = vi;
+            B.st_rho[i] = rd.x;
+            B.st_acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            B.st_X[i] = make_float2(0.f, 0.f);
+        } else {
+            Self I{ri.x, ri.y, vi.x, vi.y, K.rho0 * (1.0f + ai.x), ai.z, ai.w};
+            Acc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int c = cell_of(K, ri.x, ri.y);
+            // fluid neighbours: three contiguous row ranges of the sorted arrays
+            int n = 0;
+            auto flush = [&](int cnt) {
+                for (int k = 0; k < cnt; ++k) {
+                    const int j = lst[w][k][lane];
+                    const float2 rj = __ldg(&B.s_pos[j]);
+                    const float2 vj = __ldg(&B.s_vel[j]);
+                    const float4 aj = __ldg(&B.s_aux[j]);
+                    pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, K.rho0 * (1.0f + aj.x), aj.z, aj.w,
+                               K.m, true, A);
+                }
+            };
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = __ldg(&B.s_pos[j]);
+                if (j != i && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) {
+                    lst[w][n][lane] = j;
+                    if (++n == kListCap) { flush(n); n = 0; }
+                }
+            });
+            flush(n);
+            // wall ghosts (static cell list)
+            if (K.nw > 0) {
+                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                    const float2 rg = __ldg(&B.gw_pos[k]);
+                    if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
+                    const float4 ag = B.g_aux[k];
+                    const float2 vg = B.g_vel[k];
+                    const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
+                                                K.rho0 * (1.0f + ag.x), ag.z, ag.w, K.m_wall,
+                                                false, A);
+                    if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
+                        const float2 e = __ldg(&B.gw_nrm[k]);
+                        fw -= (double)(K.m * (f.x * e.x + f.y * e.y));
+                    }
+                });
+            }
+            // disk ghosts (the ring, only near the disk)
+            if (K.ng > 0) {
+                const float xc = (float)B.S->xc, yc = (float)B.S->yc;
+                if (near_disk(K, ri.x, ri.y, xc, yc)) {
+                    for (int k = 0; k < K.ng; ++k) {
+                        const float2 rg = B.gd_pos[k];
+                        if (outside_box(K, rg.x, rg.y)) continue;
+                        if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
+                        const float4 ag = B.g_aux[K.nw + k];
+                        const float2 vg = B.g_vel[K.nw + k];
+                        const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
+                                                    K.rho0 * (1.0f + ag.x), ag.z, ag.w, K.m_disk,
+                                                    false, A);
+                        fdx += (double)(K.m * f.x);
+                        fdy += (double)(K.m * f.y);
+                    }
+                    const float ddx = ri.x - xc, ddy = ri.y - yc;
+                    npen = ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
+                }
+            }
+            // epilogue: corrected density, closing half kick (T)
+            const float ax = A.ax + K.gx, ay = A.ay + K.gy;
+            const float Dd = A.dr * K.inv_rho0;
+            const float dnew = band(K, fmaf(dt, Dd, rd.x));
+            const float2 vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
+            if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
+                atomicOr(&B.S->status, ST_NAN);
+            B.st_vel[i] = vnew;
+            B.st_rho[i] = dnew;
+            B.st_acc[i] = make_float4(ax, ay, Dd, prime ? Dd : rd.y);
+            B.st_X[i] = make_float2(A.Xx, A.Xy);
+            vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
+            diss = -(double)(K.m * (vi.x * A.avx + vi.y * A.avy));
+        }
+    }
+    // block partials (fixed order: deterministic)
+    fdx = warp_sum(fdx);
+    fdy = warp_sum(fdy);
+    fw = warp_sum(fw);
+    diss = warp_sum(diss);
+    vmax = warp_max(vmax);
+    npen = warp_sum(npen);
+    if (lane == 0) {
+        red[w][0] = fdx;
+        red[w][1] = fdy;
+        red[w][2] = fw;
+        red[w][3] = diss;
+        redv[w] = vmax;
+        redn[w] = npen;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PassPartial P{0.0, 0.0, 0.0, 0.0, 0.0f, 0};
+        for (int k = 0; k < kPassThreads / 32; ++k) {
+            P.Fdx += red[k][0];
+            P.Fdy += red[k][1];
+            P.Fw += red[k][2];
+            P.diss += red[k][3];
+            P.vmax = fmaxf(P.vmax, redv[k]);
+            P.npen += redn[k];
+        }
+        B.pass_part[blockIdx.x] = P;
+    }
+}
+
+// ----------------------------------- a6, a7: probes, accumulators, gate
+
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
+{
+    __shared__ double red[kFinalizeThreads / 32][4];
+    __shared__ float redv[kFinalizeThreads / 32];
+    __shared__ int redn[kFinalizeThreads / 32];
+    __shared__ float probe_p[kMaxProbes];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Scalars *S = B.S;
+    // a7: wall probes, one warp each, on the end-of-step state
+    if (!prime && w < K.n_probes) {
+        const float px = K.probe_x[w], py = K.probe_y[w];
+        float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
+        if (!outside_box(K, px, py)) {
+            const int c = cell_of(K, px, py);
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int row = c + dy * K.ncx;
+                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                for (int j = a + lane; j < b; j += 32) {
+                    const float2 rj = B.s_pos[j];
+                    if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
+                    const float dx = px - rj.x, dy2 = py - rj.y;
+                    const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
+                    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+                    const float t2 = t * t;
+                    const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+                    const float d = B.st_rho[j];
+                    const float rw = (1.0f + d) * W;
+                    SW += W;
+                    Sp = fmaf(tait_p(K, d), W, Sp);
+                    Srx = fmaf(rw, dx, Srx);
+                    Sry = fmaf(rw, dy2, Sry);
+                }
+            }
+        }
+        SW = warp_sum(SW);
+        Sp = warp_sum(Sp);
+        Srx = warp_sum(Srx);
+        Sry = warp_sum(Sry);
+        if (lane == 0) {
+            float p = 0.0f;
+            if (SW > 0.0f) p = fmaxf((Sp + K.rho0 * (K.gx * Srx + K.gy * Sry)) / SW, K.p_cav);
+            probe_p[w] = p;
+        }
+    }
+    // reductions of the pass and ghost partials (fixed order)
+    double fdx = 0.0, fdy = 0.0, fw = 0.0, diss = 0.0;
+    float vmax = 0.0f;
+    int npen = 0;
+    for (int b = threadIdx.x; b < K.n_pass_blocks; b += blockDim.x) {
+        const PassPartial P = B.pass_part[b];
+        fdx += P.Fdx;
+        fdy += P.Fdy;
+        fw += P.Fw;
+        diss += P.diss;
+        vmax = fmaxf(vmax, P.vmax);
+        npen += P.npen;
+    }
+    for (int b = threadIdx.x; b < K.n_ghost_blocks; b += blockDim.x)
+        vmax = fmaxf(vmax, B.ghost_vmax[b]);
+    fdx = warp_sum(fdx);
+    fdy = warp_sum(fdy);
+    fw = warp_sum(fw);
+    diss = warp_sum(diss);
+    vmax = warp_max(vmax);
+    npen = warp_sum(npen);
+    if (lane == 0) {
+        red[w][0] = fdx;
+        red[w][1] = fdy;
+        red[w][2] = fw;
+        red[w][3] = diss;
+        redv[w] = vmax;
+        redn[w] = npen;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kFinalizeThreads / 32; ++k) {
+            red[0][0] += red[k][0];
+            red[0][1] += red[k][1];
+            red[0][2] += red[k][2];
+            red[0][3] += red[k][3];
+            redv[0] = fmaxf(redv[0], redv[k]);
+            redn[0] += redn[k];
+        }
+        const double dt = S->dt;
+        S->Fdx = red[0][0];
+        S->Fdy = red[0][1];
+        S->Fwall = red[0][2];
+        S->diss_rate = red[0][3];
+        if (redn[0] > 0) S->status |= ST_PENETRATION;
+        if (!prime) {
+            S->Wb += dt * (red[0][0] * S->vproj);
+            S->impulse += dt * red[0][2];
+            S->diss += dt * red[0][3];
+            const long long k = S->step;
+            if (k < K.probe_cap) {
+                for (int q = 0; q < K.n_probes; ++q) {
+                    B.probe_hist[k * K.n_probes + q] = probe_p[q];
+                    S->probe_imp[q] += dt * (double)probe_p[q];
+                }
+                B.probe_t[k] = S->t;
+                S->hist_n = k + 1;
+            } else if (K.n_probes > 0) {
+                S->status |= ST_PROBEFULL;
+            }
+            S->step = k + 1;
+            S->dt_prev = dt;
+        }
+        double dtn;
+        if (K.dt_mode == 1) dtn = K.cfl_h / (K.c0d + K.v0);
+        else dtn = K.cfl_h / (K.c0d + (double)redv[0]);
+        if (!(dtn > 1e-14)) S->status |= ST_DT;
+        S->dt = dtn;
+        if (prime) S->dt_prev = dtn;
+    }
+}
+
+}  // namespace hr

@@ -1,0 +1,135 @@
+"""CUDA path against the FP64 oracle on identical seeded inputs.
+
+Gates: neighbour sets bit-exact; density and pressure after one step within
+1e-5 (density relative, pressure relative to max |p|); probe histories within
+1e-3 relative L2 over the 250-step window of the 150 x 150 mm, dx = 2 mm case.
+"""
+import numpy as np
+import pytest
+
+import casegen
+import oracle
+from helpers import as64, csr_equal, impact_case, perturbed, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2609_05494_b300 import Case  # noqa: E402
+
+
+def both(p, xy32, vel=None, rho=None, **kw):
+    g = Case(p, xy32, vel, rho, **kw)
+    o = oracle.OracleCase(p, as64(xy32), as64(vel), as64(rho))
+    return g, o
+
+
+# ------------------------------------------------------------ neighbours
+
+@pytest.mark.parametrize("kind", ["impact", "perturbed_positions", "closed_box"])
+def test_neighbour_sets_bit_exact(kind):
+    if kind == "impact":
+        p, xy = impact_case()
+    elif kind == "perturbed_positions":
+        p, xy = impact_case(jitter=0.3, Lx=0.05, W=0.04)
+    else:
+        p, xy = impact_case(Lx=0.03, W=0.02, dx=1e-3, end_walls=1, Ng=40, R_disk=3e-3,
+                            x_c0=0.012, v0=0.0)
+    g, o = both(p, xy)
+    off_g, ids_g = g.neighbours()
+    off_o, ids_o = o.neighbours()
+    assert off_g.shape == off_o.shape
+    assert csr_equal(off_g, ids_g, off_o, ids_o)
+    assert ids_g.size > 10 * xy.shape[0]
+
+
+def test_neighbour_sets_after_steps():
+    # same positions on both sides: the CUDA state after 30 steps is fed back
+    # into a fresh oracle case only through its float32 positions
+    p, xy = impact_case()
+    g = Case(p, xy)
+    g.run(30)
+    s = g.get_state()
+    g.set_state(s["xy"], s["vel"], s["rho"])
+    o = oracle.OracleCase(p, as64(s["xy"]), as64(s["vel"]), as64(s["rho"]))
+    off_g, ids_g = g.neighbours()
+    off_o, ids_o = o.neighbours()
+    assert csr_equal(off_g, ids_g, off_o, ids_o)
+
+
+# ------------------------------------------------------------- one step
+
+@pytest.mark.parametrize("state", ["rest_impact", "perturbed"])
+def test_one_step_density_pressure(state):
+    p, xy = impact_case()
+    vel = rho = None
+    if state == "perturbed":
+        vel, rho = perturbed(p, xy)
+    g, o = both(p, xy, vel, rho)
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] - fo["rho"]).max() / p["rho0"] <= 1e-5 * 1.0 + 0.0
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    pmax = np.abs(fo["p"]).max()
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * pmax
+    # positions and velocities too (float32 state against the double oracle)
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+    # time step from the CFL gate
+    assert abs(g.scalars()["dt"] / o.scalars()["dt"] - 1.0) <= 1e-6
+
+
+def test_ghost_state_after_one_step():
+    p, xy = impact_case()
+    vel, rho = perturbed(p, xy)
+    g, o = both(p, xy, vel, rho)
+    g.step()
+    o.step()
+    gg, go = g.ghosts(), o.ghosts()
+    assert np.array_equal(gg["xy"], go["xy"].astype(np.float32))
+    pmax = np.abs(go["p"]).max()
+    assert np.abs(gg["p"] - go["p"]).max() <= 1e-5 * pmax
+    assert np.abs(gg["rho"] / go["rho"] - 1.0).max() <= 1e-5
+    vmax = np.abs(go["vel"]).max()
+    assert np.abs(gg["vel"] - go["vel"]).max() <= 1e-5 * vmax
+
+
+# ------------------------------------------------------------ probe window
+
+def test_probe_history_parity_window():
+    p, xy = impact_case()
+    # the four wall probes plus interior probes that see the entry shock
+    p["probes"] = list(p["probes"]) + [(0.030, 0.0), (0.020, 0.030), (0.040, -0.030),
+                                       (0.060, 0.0)]
+    g, o = both(p, xy)
+    n = p["n_steps"]
+    g.run(n)
+    o.run(n)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    tg, to = g.probe_times(), o.probes()[1]
+    assert pg.shape == po.shape == (n, len(p["probes"]))
+    assert np.abs(tg / to - 1.0).max() <= 1e-5
+    for k in range(po.shape[1]):
+        peak = np.abs(po[:, k]).max()
+        if peak > 1e6:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
+        else:
+            # below 1 MPa the wall probes hold only the gravity settling
+            # signal; the float32 state resolves it to a few hundred Pa
+            assert np.abs(pg[:, k] - po[:, k]).max() <= 2e3, k
+
+
+def test_run_is_deterministic():
+    p, xy = impact_case()
+    a = Case(p, xy)
+    b = Case(p, xy)
+    a.run(40)
+    b.run(40)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k])
+    assert np.array_equal(a.probe_pressure(), b.probe_pressure())
