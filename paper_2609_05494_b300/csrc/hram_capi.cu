@@ -337,6 +337,11 @@ void make_consts(hr_case *c)
     K.ng = (int)c->ng;
     K.m_wall = (float)(P.rho0 * P.dx * P.dx);
     K.m_disk = P.Ng > 0 ? (float)(P.rho0 * P.dx * (2.0 * M_PI * P.R_disk / (double)P.Ng)) : 0.f;
+    K.wall_over_m = 1.0f;
+    K.disk_over_m = P.Ng > 0 ? (float)(P.dx * (2.0 * M_PI * P.R_disk / (double)P.Ng) /
+                                       (P.dx * P.dx))
+                             : 0.f;
+    K.m_over_rho0 = (float)(P.dx * P.dx);
     K.R = (float)P.R_disk;
     K.R2 = (float)(P.R_disk * P.R_disk);
     const double reach = P.R_disk + 1.02 * s;
@@ -361,7 +366,7 @@ void make_consts(hr_case *c)
     K.probe_cap = P.probe_capacity > 0 ? P.probe_capacity : (1LL << 16);
     c->drift_blocks = (int)((c->nf + 255) / 256);
     c->pass_blocks = (int)((c->nf + kPassThreads - 1) / kPassThreads);
-    c->ghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + 255) / 256);
+    c->ghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + kGhostWarps - 1) / kGhostWarps);
     c->n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
     c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
     K.n_pass_blocks = c->pass_blocks;
@@ -372,7 +377,7 @@ struct Offsets {
     size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_acc, st_X, u_pos, u_vel, u_rd,
         u_id, u_key, u_slot, cell_count, cell_start, tile_sum, perm_tmp, gw_pos, gw_nrm,
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
-        probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io;
+        probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w;
     size_t total;
 };
 
@@ -411,7 +416,10 @@ Offsets plan(const hr_case *c)
     o.g_vel = L.add(ng * 8);
     o.g_aux = L.add(ng * 16);
     o.ghost_vmax = L.add((size_t)c->ghost_blocks * 4);
-    o.pass_part = L.add((size_t)c->pass_blocks * sizeof(PassPartial));
+    o.pass_part = L.add((size_t)c->pass_blocks * 16);
+    o.part_w = L.add((size_t)c->pass_blocks * 16);
+    o.part_vmax = L.add((size_t)c->pass_blocks * 4);
+    o.part_npen = L.add((size_t)c->pass_blocks * 4);
     o.probe_hist = L.add((size_t)K.probe_cap * (size_t)std::max(K.n_probes, 1) * 4);
     o.probe_t = L.add((size_t)K.probe_cap * 8);
     o.S = L.add(sizeof(Scalars));
@@ -463,7 +471,10 @@ void bind(hr_case *c, const Offsets &o)
     B.g_vel = at<float2>(w, o.g_vel);
     B.g_aux = at<float4>(w, o.g_aux);
     B.ghost_vmax = at<float>(w, o.ghost_vmax);
-    B.pass_part = at<PassPartial>(w, o.pass_part);
+    B.part.f = at<double2>(w, o.pass_part);
+    B.part.w = at<double2>(w, o.part_w);
+    B.part.vmax = at<float>(w, o.part_vmax);
+    B.part.npen = at<int>(w, o.part_npen);
     B.probe_hist = at<float>(w, o.probe_hist);
     B.probe_t = at<double>(w, o.probe_t);
     B.S = at<Scalars>(w, o.S);
@@ -498,7 +509,7 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events)
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
     k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
-    k_ghost<<<c->ghost_blocks, 256, 0, s>>>(K, B);
+    k_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     k_pass<<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));

@@ -28,11 +28,11 @@ namespace hr {
 
 constexpr int kMaxProbes = 16;
 constexpr int kPassThreads = 128;
-constexpr int kListCap = 24;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kFinalizeThreads = 512;
+constexpr int kFinalizeThreads = 1024;
+constexpr int kGhostWarps = 8;
 
 // device status bits (warnings share the public HR_W* values)
 constexpr int ST_PENETRATION = 1;
@@ -59,7 +59,7 @@ struct Consts {
     int gamma7;
     // ghosts
     int nf, nw, ng;
-    float m_wall, m_disk, R, disk_reach2, R2;
+    float m_wall, m_disk, wall_over_m, disk_over_m, m_over_rho0, R, disk_reach2, R2;
     // CFL and kinematics (FP64)
     double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k;
     int dt_mode, motion;
@@ -83,10 +83,13 @@ struct Scalars {
     int pad;
 };
 
-struct PassPartial {
-    double Fdx, Fdy, Fw, diss;
-    float vmax;
-    int npen;
+// Per-block partials of the interaction pass, structure of arrays so the
+// finalize kernel streams them with wide independent loads.
+struct PassPartials {
+    double2 *f;      // {F_disk,x, F_disk,y}
+    double2 *w;      // {F_wall, dissipation rate}
+    float *vmax;
+    int *npen;
 };
 
 // Device buffers of a case.  s_* are in the cell order of the current step,
@@ -112,7 +115,7 @@ struct Bufs {
     int *cell_count; // ncell + 1 (last = frozen particles)
     int *cell_start; // ncell + 2
     int *tile_sum;
-    int *perm_tmp;
+    int *perm_tmp;   // fluid IDs in provisional cell order
     // wall ghosts (static, cell order) and disk ghosts
     float2 *gw_pos;
     float2 *gw_nrm;
@@ -124,7 +127,7 @@ struct Bufs {
     float2 *g_vel;
     float4 *g_aux;     // {d_g, p_g, p_g / rho_g^2, c_g}
     float *ghost_vmax; // per ghost block
-    PassPartial *pass_part;
+    PassPartials part;
     // probes
     float *probe_hist;
     double *probe_t;
@@ -331,6 +334,9 @@ __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
         // predicted density: D extrapolated linearly over the step
         const float Dp = fmaf(ratio, a.z - a.w, a.z);
         dp = band(K, fmaf(dt, Dp, d));
+        if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(vh.x) || !isfinite(vh.y) ||
+            !isfinite(dp))
+            atomicOr(&B.S->status, ST_NAN);
         if (outside_box(K, r.x, r.y)) {
             key = K.ncell;
             atomicOr(&B.S->status, ST_OUTSIDE);
@@ -459,7 +465,8 @@ __global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
-    B.perm_tmp[B.cell_start[B.u_key[i]] + B.u_slot[i]] = i;
+    const int dst = B.cell_start[B.u_key[i]] + B.u_slot[i];
+    B.perm_tmp[dst] = B.u_id[i];
 }
 
 // Stable order inside a cell: rank by fluid ID among the cell's members.
@@ -473,7 +480,8 @@ __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B)
     const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
     const int id = B.u_id[i];
     int rank = 0;
-    for (int k = cs; k < ce; ++k) rank += B.u_id[B.perm_tmp[k]] < id;
+#pragma unroll 4
+    for (int k = cs; k < ce; ++k) rank += __ldg(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
     const float4 rd = B.u_rd[i];
     B.s_pos[dst] = B.u_pos[i];
@@ -489,10 +497,13 @@ __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B)
 // disk ghosts [nw, nw + ng), over fluid neighbours in the 3x3 cell stencil:
 //   p_g = max((S_p + (g - a_w) . S_rr) / S_W, p_cav),
 //   rho_g = rho0 (1 + p_g / (rho0 c0^2)),  v_g = 2 v_w - S_v / S_W.
-__global__ void __launch_bounds__(256) k_ghost(Consts K, Bufs B)
+// One warp per ghost: the lanes split the stencil's candidates, then the six
+// Shepard sums are reduced across the warp.
+__global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
 {
-    __shared__ float red[8];
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float red[kGhostWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x * kGhostWarps + w;
     float vabs = 0.0f;
     if (g < K.nw + K.ng) {
         const bool disk = g >= K.nw;
@@ -500,27 +511,39 @@ __global__ void __launch_bounds__(256) k_ghost(Consts K, Bufs B)
         const float vwx = disk ? (float)B.S->vproj : 0.0f;
         const float awx = disk ? (float)B.S->aproj : 0.0f;
         float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f, Svx = 0.f, Svy = 0.f;
-        if (!outside_box(K, rg.x, rg.y)) {
+        const bool inside = !outside_box(K, rg.x, rg.y);
+        if (inside) {
             const int c = cell_of(K, rg.x, rg.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
-                const float2 rj = __ldg(&B.s_pos[j]);
-                if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) return;
-                const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
-                const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
-                const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
-                const float t2 = t * t;
-                const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
-                const float4 aux = __ldg(&B.s_aux[j]);
-                const float2 vj = __ldg(&B.s_vel[j]);
-                const float rw = (1.0f + aux.x) * W;
-                SW += W;
-                Sp = fmaf(aux.y, W, Sp);
-                Srx = fmaf(rw, dx, Srx);
-                Sry = fmaf(rw, dy2, Sry);
-                Svx = fmaf(vj.x, W, Svx);
-                Svy = fmaf(vj.y, W, Svy);
-            });
+#pragma unroll 1
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int row = c + dy * K.ncx;
+                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                for (int j = a + lane; j < b; j += 32) {
+                    const float2 rj = __ldg(&B.s_pos[j]);
+                    if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
+                    const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
+                    const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
+                    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+                    const float t2 = t * t;
+                    const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+                    const float4 aux = __ldg(&B.s_aux[j]);
+                    const float2 vj = __ldg(&B.s_vel[j]);
+                    const float rw = (1.0f + aux.x) * W;
+                    SW += W;
+                    Sp = fmaf(aux.y, W, Sp);
+                    Srx = fmaf(rw, dx, Srx);
+                    Sry = fmaf(rw, dy2, Sry);
+                    Svx = fmaf(vj.x, W, Svx);
+                    Svy = fmaf(vj.y, W, Svy);
+                }
+            }
         }
+        SW = warp_sum(SW);
+        Sp = warp_sum(Sp);
+        Srx = warp_sum(Srx);
+        Sry = warp_sum(Sry);
+        Svx = warp_sum(Svx);
+        Svy = warp_sum(Svy);
         float4 aux;
         float2 vg;
         if (SW > 0.0f) {
@@ -536,17 +559,18 @@ __global__ void __launch_bounds__(256) k_ghost(Consts K, Bufs B)
             aux = make_float4(0.0f, 0.0f, 0.0f, K.c0);
             vg = make_float2(vwx, 0.0f);
         }
-        B.g_aux[g] = aux;
-        B.g_vel[g] = vg;
-        if (!outside_box(K, rg.x, rg.y)) vabs = sqrtf(vg.x * vg.x + vg.y * vg.y);
+        if (lane == 0) {
+            B.g_aux[g] = aux;
+            B.g_vel[g] = vg;
+        }
+        if (inside) vabs = sqrtf(vg.x * vg.x + vg.y * vg.y);
     }
-    vabs = warp_max(vabs);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vabs;
+    if (lane == 0) red[w] = vabs;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
-        v = warp_max(v);
-        if (threadIdx.x == 0) B.ghost_vmax[blockIdx.x] = v;
+    if (threadIdx.x == 0) {
+        float v = 0.0f;
+        for (int k = 0; k < kGhostWarps; ++k) v = fmaxf(v, red[k]);
+        B.ghost_vmax[blockIdx.x] = v;
     }
 }
 
@@ -561,8 +585,10 @@ struct Acc {
 };
 
 // One pair (i, j): continuity, momentum with artificial and laminar
-// viscosity (eqs. momentum, artificial-viscosity), XSPH when xsph.  Adds
-// m_j times the pair terms; returns the acceleration contribution of j on i.
+// viscosity (eqs. momentum, artificial-viscosity) and, when xsph, the XSPH
+// sum (eq. xsph).  Adds mj times the pair terms (mj = 1 for fluid pairs: the
+// uniform fluid mass is applied once per particle) and returns the
+// acceleration contribution of j on i per unit mass mj.
 __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float xj, float yj,
                                              float vxj, float vyj, float rhoj, float Pj,
                                              float cj, float mj, bool xsph, Acc &A)
@@ -572,44 +598,47 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
     const float t3 = t * t * t;
-    const float F = K.Fc * t3;                          // grad_i W = F r_ij
+    const float F = mj * K.Fc * t3;                     // m_j grad_i W = F r_ij
     const float vx = I.vx - vxj, vy = I.vy - vyj;
     const float vr = fmaf(vx, dx, vy * dy);
-    A.dr = fmaf(mj * F, vr, A.dr);                      // continuity
-    const float rs = I.rho + rhoj;
-    const float inv = __frcp_rn((r2 + K.eh2) * rs);     // 1 / ((r^2 + eta^2 h^2)(rho_i + rho_j))
+    A.dr = fmaf(F, vr, A.dr);                           // continuity
+    const float e = r2 + K.eh2;
+    const float inv = __fdividef(1.0f, e * (I.rho + rhoj));  // 1/((r^2 + eta^2 h^2)(rho_i + rho_j))
     const float Pi_ij = -K.alpha_h * (I.c + cj) * fminf(vr, 0.0f) * inv;  // -alpha cbar mu / rhobar
-    const float mF = mj * F;
-    const float S = -(I.P + Pj + Pi_ij) * mF;           // pressure + AV
-    const float lam = mj * K.nu4 * F * r2 * inv;        // laminar
+    const float S = -(I.P + Pj + Pi_ij) * F;            // pressure + AV
+    const float lam = K.nu4 * F * r2 * inv;             // laminar
     const float fx = fmaf(S, dx, lam * vx);
     const float fy = fmaf(S, dy, lam * vy);
     A.ax += fx;
     A.ay += fy;
-    const float av = -Pi_ij * mF;
+    const float av = -Pi_ij * F;
     A.avx = fmaf(av, dx, A.avx);
     A.avy = fmaf(av, dy, A.avy);
     if (xsph) {
-        const float W = K.Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f);
-        const float w = -2.0f * mj * W * inv * (r2 + K.eh2);  // -(m_j / rhobar) W
-        A.Xx = fmaf(w, vx, A.Xx);
-        A.Xy = fmaf(w, vy, A.Xy);
+        const float W = mj * K.Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f);
+        const float wx = -2.0f * W * inv * e;           // -(m_j / rhobar) W
+        A.Xx = fmaf(wx, vx, A.Xx);
+        A.Xy = fmaf(wx, vy, A.Xy);
     }
     return make_float2(fx, fy);
 }
 
+// The fused interaction pass.  One thread per sorted fluid particle i.
+// Candidates are scanned per stencil row in chunks of 32: the float
+// predicate of each candidate sets one bit of a mask (loads unrolled, no
+// per-candidate branching), then the pair terms run over the set bits.
+// Ghost neighbours follow (static wall lists, then the disk ring).  The
+// epilogue applies the uniform fluid mass, the corrected density and the
+// closing half kick.  Block partials of the ghost forces, the dissipation
+// rate and max |v| are reduced in FP32 per warp and in FP64 per block.
 __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
 {
-    __shared__ int lst[kPassThreads / 32][kListCap][32];
-    __shared__ double red[kPassThreads / 32][4];
-    __shared__ float redv[kPassThreads / 32];
+    __shared__ float red[kPassThreads / 32][5];
     __shared__ int redn[kPassThreads / 32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const double dtd = prime ? 0.0 : B.S->dt;
-    const float dt = (float)dtd;
-    double fdx = 0.0, fdy = 0.0, fw = 0.0, diss = 0.0;
-    float vmax = 0.0f;
+    const float dt = prime ? 0.0f : (float)B.S->dt;
+    float fdx = 0.0f, fdy = 0.0f, fw = 0.0f, diss = 0.0f, vmax = 0.0f;
     int npen = 0;
     if (i < K.nf) {
         const float2 ri = B.s_pos[i];
@@ -623,29 +652,35 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
             B.st_acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             B.st_X[i] = make_float2(0.f, 0.f);
         } else {
-            Self I{ri.x, ri.y, vi.x, vi.y, K.rho0 * (1.0f + ai.x), ai.z, ai.w};
+            const Self I{ri.x, ri.y, vi.x, vi.y, fmaf(K.rho0, ai.x, K.rho0), ai.z, ai.w};
             Acc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int c = cell_of(K, ri.x, ri.y);
-            // fluid neighbours: three contiguous row ranges of the sorted arrays
-            int n = 0;
-            auto flush = [&](int cnt) {
-                for (int k = 0; k < cnt; ++k) {
-                    const int j = lst[w][k][lane];
-                    const float2 rj = __ldg(&B.s_pos[j]);
-                    const float2 vj = __ldg(&B.s_vel[j]);
-                    const float4 aj = __ldg(&B.s_aux[j]);
-                    pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, K.rho0 * (1.0f + aj.x), aj.z, aj.w,
-                               K.m, true, A);
+#pragma unroll 1
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int row = c + dy * K.ncx;
+                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+#pragma unroll 1
+                for (int base = a; base < b; base += 32) {
+                    const int cnt = min(32, b - base);
+                    const float2 *pp = B.s_pos + base;
+                    unsigned m = 0u;
+#pragma unroll 8
+                    for (int k = 0; k < cnt; ++k) {
+                        const float2 rj = __ldg(pp + k);
+                        m |= (unsigned)in_support(ri.x, ri.y, rj.x, rj.y, K.s2) << k;
+                    }
+                    if (i >= base && i < base + cnt) m &= ~(1u << (i - base));
+                    while (m) {
+                        const int j = base + __ffs(m) - 1;
+                        m &= m - 1u;
+                        const float2 rj = __ldg(&B.s_pos[j]);
+                        const float2 vj = __ldg(&B.s_vel[j]);
+                        const float4 aj = __ldg(&B.s_aux[j]);
+                        pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                                   aj.w, 1.0f, true, A);
+                    }
                 }
-            };
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
-                const float2 rj = __ldg(&B.s_pos[j]);
-                if (j != i && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) {
-                    lst[w][n][lane] = j;
-                    if (++n == kListCap) { flush(n); n = 0; }
-                }
-            });
-            flush(n);
+            }
             // wall ghosts (static cell list)
             if (K.nw > 0) {
                 for_fluid_candidates(K, B.wall_start, c, [&](int k) {
@@ -654,11 +689,11 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
                     const float4 ag = B.g_aux[k];
                     const float2 vg = B.g_vel[k];
                     const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                K.rho0 * (1.0f + ag.x), ag.z, ag.w, K.m_wall,
-                                                false, A);
+                                                fmaf(K.rho0, ag.x, K.rho0), ag.z, ag.w,
+                                                K.wall_over_m, false, A);
                     if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
                         const float2 e = __ldg(&B.gw_nrm[k]);
-                        fw -= (double)(K.m * (f.x * e.x + f.y * e.y));
+                        fw -= f.x * e.x + f.y * e.y;
                     }
                 });
             }
@@ -673,18 +708,18 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
                         const float4 ag = B.g_aux[K.nw + k];
                         const float2 vg = B.g_vel[K.nw + k];
                         const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                    K.rho0 * (1.0f + ag.x), ag.z, ag.w, K.m_disk,
-                                                    false, A);
-                        fdx += (double)(K.m * f.x);
-                        fdy += (double)(K.m * f.y);
+                                                    fmaf(K.rho0, ag.x, K.rho0), ag.z, ag.w,
+                                                    K.disk_over_m, false, A);
+                        fdx += f.x;
+                        fdy += f.y;
                     }
                     const float ddx = ri.x - xc, ddy = ri.y - yc;
                     npen = ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
                 }
             }
-            // epilogue: corrected density, closing half kick (T)
-            const float ax = A.ax + K.gx, ay = A.ay + K.gy;
-            const float Dd = A.dr * K.inv_rho0;
+            // epilogue: the fluid mass, corrected density, closing half kick (T)
+            const float ax = fmaf(K.m, A.ax, K.gx), ay = fmaf(K.m, A.ay, K.gy);
+            const float Dd = A.dr * K.m_over_rho0;
             const float dnew = band(K, fmaf(dt, Dd, rd.x));
             const float2 vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
             if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
@@ -692,12 +727,12 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
             B.st_vel[i] = vnew;
             B.st_rho[i] = dnew;
             B.st_acc[i] = make_float4(ax, ay, Dd, prime ? Dd : rd.y);
-            B.st_X[i] = make_float2(A.Xx, A.Xy);
+            B.st_X[i] = make_float2(K.m * A.Xx, K.m * A.Xy);
             vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
-            diss = -(double)(K.m * (vi.x * A.avx + vi.y * A.avy));
+            diss = -K.m * K.m * (vi.x * A.avx + vi.y * A.avy);
         }
     }
-    // block partials (fixed order: deterministic)
+    // block partials: FP32 within the warp, FP64 across warps (fixed order)
     fdx = warp_sum(fdx);
     fdy = warp_sum(fdy);
     fw = warp_sum(fw);
@@ -709,21 +744,27 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
         red[w][1] = fdy;
         red[w][2] = fw;
         red[w][3] = diss;
-        redv[w] = vmax;
+        red[w][4] = vmax;
         redn[w] = npen;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        PassPartial P{0.0, 0.0, 0.0, 0.0, 0.0f, 0};
+        const double m2 = (double)K.m * (double)K.m;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        float v = 0.0f;
+        int np = 0;
         for (int k = 0; k < kPassThreads / 32; ++k) {
-            P.Fdx += red[k][0];
-            P.Fdy += red[k][1];
-            P.Fw += red[k][2];
-            P.diss += red[k][3];
-            P.vmax = fmaxf(P.vmax, redv[k]);
-            P.npen += redn[k];
+            a0 += (double)red[k][0];
+            a1 += (double)red[k][1];
+            a2 += (double)red[k][2];
+            a3 += (double)red[k][3];
+            v = fmaxf(v, red[k][4]);
+            np += redn[k];
         }
-        B.pass_part[blockIdx.x] = P;
+        B.part.f[blockIdx.x] = make_double2(m2 * a0, m2 * a1);
+        B.part.w[blockIdx.x] = make_double2(m2 * a2, a3);
+        B.part.vmax[blockIdx.x] = v;
+        B.part.npen[blockIdx.x] = np;
     }
 }
 
@@ -735,8 +776,12 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
     __shared__ float redv[kFinalizeThreads / 32];
     __shared__ int redn[kFinalizeThreads / 32];
     __shared__ float probe_p[kMaxProbes];
+    __shared__ Scalars S;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Scalars *S = B.S;
+    // the device scalars, read once into shared memory
+    static_assert(sizeof(Scalars) % 8 == 0, "Scalars is copied as doubles");
+    for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
+        reinterpret_cast<double *>(&S)[k] = reinterpret_cast<const double *>(B.S)[k];
     // a7: wall probes, one warp each, on the end-of-step state
     if (!prime && w < K.n_probes) {
         const float px = K.probe_x[w], py = K.probe_y[w];
@@ -777,14 +822,16 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
     double fdx = 0.0, fdy = 0.0, fw = 0.0, diss = 0.0;
     float vmax = 0.0f;
     int npen = 0;
+#pragma unroll 4
     for (int b = threadIdx.x; b < K.n_pass_blocks; b += blockDim.x) {
-        const PassPartial P = B.pass_part[b];
-        fdx += P.Fdx;
-        fdy += P.Fdy;
-        fw += P.Fw;
-        diss += P.diss;
-        vmax = fmaxf(vmax, P.vmax);
-        npen += P.npen;
+        const double2 f = B.part.f[b];
+        const double2 q = B.part.w[b];
+        fdx += f.x;
+        fdy += f.y;
+        fw += q.x;
+        diss += q.y;
+        vmax = fmaxf(vmax, B.part.vmax[b]);
+        npen += B.part.npen[b];
     }
     for (int b = threadIdx.x; b < K.n_ghost_blocks; b += blockDim.x)
         vmax = fmaxf(vmax, B.ghost_vmax[b]);
@@ -812,37 +859,40 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
             redv[0] = fmaxf(redv[0], redv[k]);
             redn[0] += redn[k];
         }
-        const double dt = S->dt;
-        S->Fdx = red[0][0];
-        S->Fdy = red[0][1];
-        S->Fwall = red[0][2];
-        S->diss_rate = red[0][3];
-        if (redn[0] > 0) S->status |= ST_PENETRATION;
+        const double dt = S.dt;
+        S.Fdx = red[0][0];
+        S.Fdy = red[0][1];
+        S.Fwall = red[0][2];
+        S.diss_rate = red[0][3];
+        if (redn[0] > 0) S.status |= ST_PENETRATION;
         if (!prime) {
-            S->Wb += dt * (red[0][0] * S->vproj);
-            S->impulse += dt * red[0][2];
-            S->diss += dt * red[0][3];
-            const long long k = S->step;
+            S.Wb += dt * (red[0][0] * S.vproj);
+            S.impulse += dt * red[0][2];
+            S.diss += dt * red[0][3];
+            const long long k = S.step;
             if (k < K.probe_cap) {
                 for (int q = 0; q < K.n_probes; ++q) {
                     B.probe_hist[k * K.n_probes + q] = probe_p[q];
-                    S->probe_imp[q] += dt * (double)probe_p[q];
+                    S.probe_imp[q] += dt * (double)probe_p[q];
                 }
-                B.probe_t[k] = S->t;
-                S->hist_n = k + 1;
+                B.probe_t[k] = S.t;
+                S.hist_n = k + 1;
             } else if (K.n_probes > 0) {
-                S->status |= ST_PROBEFULL;
+                S.status |= ST_PROBEFULL;
             }
-            S->step = k + 1;
-            S->dt_prev = dt;
+            S.step = k + 1;
+            S.dt_prev = dt;
         }
         double dtn;
         if (K.dt_mode == 1) dtn = K.cfl_h / (K.c0d + K.v0);
         else dtn = K.cfl_h / (K.c0d + (double)redv[0]);
-        if (!(dtn > 1e-14)) S->status |= ST_DT;
-        S->dt = dtn;
-        if (prime) S->dt_prev = dtn;
+        if (!(dtn > 1e-14)) S.status |= ST_DT;
+        S.dt = dtn;
+        if (prime) S.dt_prev = dtn;
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
+        reinterpret_cast<double *>(B.S)[k] = reinterpret_cast<const double *>(&S)[k];
 }
 
 }  // namespace hr

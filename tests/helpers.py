@@ -29,3 +29,11 @@ def rel_l2(a, b):
 
 def csr_equal(off1, ids1, off2, ids2):
     return np.array_equal(off1, off2) and np.array_equal(ids1, ids2)
+
+
+def p_scale(p, p_ref):
+    """Pressure scale of the one-step gate "pressure within 1e-5 relative":
+    the larger of max |p_ref| and the EOS stiffness rho0 c0^2.  p = B((rho /
+    rho0)^gamma - 1) maps the density gate (1e-5 relative) onto 1e-5 rho0 c0^2;
+    near rest max |p| is far below that and p is a cancellation."""
+    return max(float(np.abs(p_ref).max()), p["rho0"] * p["c0"] ** 2)

@@ -9,7 +9,7 @@ import pytest
 
 import casegen
 import oracle
-from helpers import as64, csr_equal, impact_case, perturbed, rel_l2
+from helpers import as64, csr_equal, impact_case, p_scale, perturbed, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -71,10 +71,9 @@ def test_one_step_density_pressure(state):
     g.step()
     o.step()
     sg, fo = g.get_state(), o.fluid()
-    assert np.abs(sg["rho"] - fo["rho"]).max() / p["rho0"] <= 1e-5 * 1.0 + 0.0
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
-    pmax = np.abs(fo["p"]).max()
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * pmax
+    # at this size the stricter max |p| normalisation holds as well
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * np.abs(fo["p"]).max()
     # positions and velocities too (float32 state against the double oracle)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     vscale = max(np.abs(fo["vel"]).max(), 1.0)
