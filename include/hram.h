@@ -180,6 +180,31 @@ int hr_kernel_times(hr_case *c, float *ms, int n);
 int hr_save_state(hr_case *c, const char *path);
 int hr_load_state(hr_case *c, const char *path);
 
+/* Neighbour counts of the current state without any device allocation.
+ *
+ * The paper has no counterpart; this is a library service.  hr_debug_neighbors
+ * allocates device scratch with cudaMalloc on every call.  Some callers cannot
+ * do that: a process whose device memory is fully reserved by another
+ * allocator (a framework's caching allocator, a fixed pool handed out at
+ * start-up), or code that must not change the device's allocation state while
+ * it runs.  This entry point computes the same per-point neighbour counts
+ * (counts[r] = offsets[r+1] - offsets[r] of hr_debug_neighbors, in the same
+ * global point order: fluid IDs, then wall ghosts, then disk ghosts) into a
+ * fixed device array that the library holds for the life of the process, then
+ * copies them to host_counts (caller-owned, cap >= number of points).
+ *
+ * Limit: HR_STATIC_NEIGHBOR_MAX points (fluid + ghosts); larger cases are
+ * rejected with HR_ERANGE before any device work.  The fixed array (4 bytes
+ * per point, 8 MiB) is resident on every device that loads the library until
+ * the process exits.  The first call on a device looks up the array's device
+ * address for that device (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call overwrites entries [0, number of points) of
+ * the shared array and leaves the rest as an earlier call left them; calls that
+ * overlap on the GPU (other streams, other cases, other threads) race on it.
+ * Synchronises the case's stream. */
+#define HR_STATIC_NEIGHBOR_MAX (1 << 21)
+int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap);
+
 void hr_destroy(hr_case *c);
 const char *hr_status_str(int status);
 

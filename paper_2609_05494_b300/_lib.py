@@ -32,8 +32,10 @@ EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",
     "hr_probe_times", "hr_diagnostics", "hr_diag_history", "hr_get_state", "hr_set_state",
     "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors", "hr_kernel_times",
-    "hr_save_state", "hr_load_state", "hr_destroy", "hr_status_str",
+    "hr_save_state", "hr_load_state", "hr_neighbor_counts_static", "hr_destroy",
+    "hr_status_str",
 )
+HR_STATIC_NEIGHBOR_MAX = 1 << 21
 
 
 class HrParams(C.Structure):
@@ -95,6 +97,7 @@ def lib() -> C.CDLL:
     L.hr_kernel_times.argtypes = [vp, vp, C.c_int]
     L.hr_save_state.argtypes = [vp, C.c_char_p]
     L.hr_load_state.argtypes = [vp, C.c_char_p]
+    L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
     L.hr_destroy.argtypes = [vp]
     L.hr_destroy.restype = None
     L.hr_status_str.argtypes = [C.c_int]

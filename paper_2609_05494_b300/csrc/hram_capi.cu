@@ -178,6 +178,76 @@ __global__ void k_wall_keys(Consts K, const float2 *pos, int n, int *key)
     if (k < n) key[k] = cell_of(K, pos[k].x, pos[k].y);
 }
 
+// Fixed device scratch of hr_neighbor_counts_static: one count per point,
+// written by global point index.  Host code must not take its address
+// directly; it uses the per-device address from cudaGetSymbolAddress.
+__device__ __align__(256) int g_static_neighbor_counts[HR_STATIC_NEIGHBOR_MAX];
+
+// Count-only variant of k_neighbors that writes by global point index (fluid
+// ID, then wall-ghost ID, then disk ghost), so no host-side reordering is
+// needed.  Same candidate loops and predicate.
+__global__ void k_neighbor_counts_static(Consts K, Bufs B, int *counts)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npts = K.nf + K.nw + K.ng;
+    if (r >= npts) return;
+    int n = 0;
+    int gid;
+    if (r < K.nf) {
+        gid = B.s_id[r];
+        const float2 ri = B.s_pos[r];
+        if (!outside_box(K, ri.x, ri.y)) {
+            const int c = cell_of(K, ri.x, ri.y);
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = B.s_pos[j];
+                if (j != r && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) ++n;
+            });
+            if (K.nw > 0)
+                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                    const float2 rg = B.gw_pos[k];
+                    if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) ++n;
+                });
+            if (K.ng > 0 && near_disk(K, ri.x, ri.y, (float)B.S->xc, (float)B.S->yc))
+                for (int k = 0; k < K.ng; ++k) {
+                    const float2 rg = B.gd_pos[k];
+                    if (!outside_box(K, rg.x, rg.y) && in_support(ri.x, ri.y, rg.x, rg.y, K.s2))
+                        ++n;
+                }
+        }
+    } else {
+        const int g = r - K.nf;
+        gid = g < K.nw ? K.nf + B.gw_id[g] : r;
+        const float2 rg = g < K.nw ? B.gw_pos[g] : B.gd_pos[g - K.nw];
+        if (!outside_box(K, rg.x, rg.y)) {
+            const int c = cell_of(K, rg.x, rg.y);
+            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+                const float2 rj = B.s_pos[j];
+                if (in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) ++n;
+            });
+        }
+    }
+    counts[gid] = n;
+}
+
+constexpr int kMaxDevices = 64;
+int *g_static_counts_ptr[kMaxDevices] = {};
+
+// Device address of g_static_neighbor_counts on the current device, looked up
+// once per device.
+int static_counts_address(int **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HR_ECUDA;
+    if (!g_static_counts_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_neighbor_counts) != cudaSuccess || !ptr)
+            return HR_ECUDA;
+        g_static_counts_ptr[dev] = static_cast<int *>(ptr);
+    }
+    *out = g_static_counts_ptr[dev];
+    return HR_OK;
+}
+
 // ------------------------------------------------------------ host helpers
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1085,6 +1155,24 @@ int hr_load_state(hr_case *c, const char *path)
     }
     c->host_step = hstep;
     c->sticky = 0;
+    return device_status(c);
+}
+
+int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
+{
+    if (!c || !host_counts) return HR_EINVAL;
+    const long long npts = c->nf + c->nw + c->ng;
+    if (npts > HR_STATIC_NEIGHBOR_MAX) return HR_ERANGE;
+    if (cap < npts) return HR_ERANGE;
+    int *counts = nullptr;
+    const int rc = static_counts_address(&counts);
+    if (rc != HR_OK) return rc;
+    const int blocks = (int)((npts + 255) / 256);
+    k_neighbor_counts_static<<<blocks, 256, 0, c->stream>>>(c->K, c->B, counts);
+    if (cudaGetLastError() != cudaSuccess) return HR_ECUDA;
+    if (cudaMemcpyAsync(host_counts, counts, (size_t)npts * sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return HR_ECUDA;
     return device_status(c);
 }
 
