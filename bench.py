@@ -124,7 +124,7 @@ def read_traffic(src_hash):
     if vals.get("kernel_source_sha1") != src_hash:
         return None
     try:
-        return float(vals["dram_bytes_per_launch_scaled"])
+        return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
 
@@ -134,6 +134,23 @@ def kernel_source_hash():
     with open(os.path.join(ROOT, "paper_2609_05494_b300", "csrc", "hram_device.cuh"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()
+
+
+def max_over_ranks(total_ms, dist=None):
+    """The timed region's duration as the maximum over ranks (every rank runs
+    its own replica; the job is done when the slowest one is)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, particles, steps, total_ms):
+    """Whole-job particle-steps/s: all ranks' particle-steps over the slowest rank's time."""
+    return world * particles * steps / (total_ms * 1e-3)
 
 
 def cpu_baseline(seconds=15.0, Lx=0.075):
@@ -247,10 +264,8 @@ def main():
         torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     groups = case.kernel_times()
+    total_ms = max_over_ranks(total_ms, dist)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     status = case.sync()
 
@@ -277,7 +292,7 @@ def main():
         return 0
 
     pk, src = peaks()
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = aggregate_value(world, n, args.steps, total_ms)
     t_pass = statistics.mean(pass_ms) * 1e-3
     flops = pairs_fluid_rows * FLOP_PER_PAIR
     alu_peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0))

@@ -22,52 +22,64 @@ using namespace hr;
 namespace {
 
 constexpr int kDiagFields = 19;
-constexpr int kDiagThreads = 256;
+constexpr int kDiagThreads = 1024;
 constexpr int kTimingEvents = 6;
 
 // ------------------------------------------------ auxiliary device kernels
 
-// FP64 diagnostics, stage 1: per-block partial sums over the fluid.
+// Specific Tait elastic energy e(rho) (reading R18) divided by B / rho0,
+// written in the deviation d without cancellation: for gamma = 7,
+// ((1+d)^6 - 1)/6 + 1/(1+d) - 1 = d^2/(1+d) + 5/2 d^2 + 10/3 d^3 + 5/2 d^4 + d^5 + d^6/6.
+__device__ __forceinline__ float tait_energy_scaled(const Consts &K, float d)
+{
+    if (K.gamma7) {
+        float poly = fmaf(d, 1.0f / 6.0f, 1.0f);
+        poly = fmaf(d, poly, 2.5f);
+        poly = fmaf(d, poly, 10.0f / 3.0f);
+        poly = fmaf(d, poly, 2.5f);
+        return d * d * (poly + 1.0f / (1.0f + d));
+    }
+    const float g = K.gamma;
+    return expm1f((g - 1.0f) * log1pf(d)) / (g - 1.0f) - d / (1.0f + d);
+}
+
+// FP64 diagnostics, stage 1: per-particle terms in FP32, sums across a warp
+// in FP32 and across the block's warps in FP64 (per-block partial).
 // partial layout (16 doubles): px, py, KE, PE, E_el, rho_min, rho_max, p_min,
 // p_max, vmax, n_in, penetrated, (unused x4)
 __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Consts K, Bufs B, double *part)
 {
-    __shared__ double sm[kDiagThreads / 32][12];
+    __shared__ float sm[kDiagThreads / 32][12];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double v[12] = {0, 0, 0, 0, 0, 1e300, -1e300, 1e300, -1e300, 0, 0, 0};
+    float v[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 3e38f, -3e38f, 3e38f, -3e38f, 0.f, 0.f, 0.f};
     if (i < K.nf) {
         const float2 r = B.s_pos[i];
         if (!outside_box(K, r.x, r.y)) {
             const float2 u = B.st_vel[i];
-            const double d = (double)B.st_rho[i];
-            const double m = (double)K.m, rho0 = (double)K.rho0, g = (double)K.gamma;
-            const double vx = u.x, vy = u.y, v2 = vx * vx + vy * vy;
-            const double x = 1.0 + d;
-            // Tait elastic energy per unit mass, written in the deviation d
-            const double e = ((double)K.B / rho0) *
-                             (expm1((g - 1.0) * log1p(d)) / (g - 1.0) + 1.0 / x - 1.0);
-            v[0] = m * vx;
-            v[1] = m * vy;
-            v[2] = 0.5 * m * v2;
-            v[3] = -m * ((double)K.gx * r.x + (double)K.gy * r.y);
-            v[4] = m * e;
-            v[5] = v[6] = rho0 * x;
-            v[7] = v[8] = (double)tait_p(K, (float)d);
-            v[9] = sqrt(v2);
-            v[10] = 1.0;
-            const float dx = r.x - (float)B.S->xc, dy = r.y - (float)B.S->yc;
-            v[11] = (K.ng > 0 && dx * dx + dy * dy < K.R2) ? 1.0 : 0.0;
+            const float d = B.st_rho[i];
+            const float v2 = u.x * u.x + u.y * u.y;
+            v[0] = K.m * u.x;
+            v[1] = K.m * u.y;
+            v[2] = 0.5f * K.m * v2;
+            v[3] = -K.m * (K.gx * r.x + K.gy * r.y);
+            v[4] = K.m * (K.B / K.rho0) * tait_energy_scaled(K, d);
+            v[5] = v[6] = K.rho0 * (1.0f + d);
+            v[7] = v[8] = tait_p(K, d);
+            v[9] = sqrtf(v2);
+            v[10] = 1.0f;
+            const float dx = r.x - B.S->xc_f, dy = r.y - B.S->yc_f;
+            v[11] = (K.ng > 0 && dx * dx + dy * dy < K.R2) ? 1.0f : 0.0f;
         }
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        double a = v[k];
+        float a = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double b = __shfl_xor_sync(0xffffffffu, a, o);
-            if (k == 5 || k == 7) a = fmin(a, b);
-            else if (k == 6 || k == 8 || k == 9) a = fmax(a, b);
+            const float b = __shfl_xor_sync(0xffffffffu, a, o);
+            if (k == 5 || k == 7) a = fminf(a, b);
+            else if (k == 6 || k == 8 || k == 9) a = fmaxf(a, b);
             else a += b;
         }
         if (lane == 0) sm[w][k] = a;
@@ -325,7 +337,8 @@ struct hr_case {
     Bufs B;
     long long nf = 0, nw = 0, ng = 0;
     int n_tiles = 0, pass_blocks = 0, ghost_blocks = 0, drift_blocks = 0, diag_blocks = 0;
-    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev[kTimingEvents] = {};
@@ -412,11 +425,14 @@ void make_consts(hr_case *c)
                                        (P.dx * P.dx))
                              : 0.f;
     K.m_over_rho0 = (float)(P.dx * P.dx);
+    K.m2Wc = (float)(-2.0 * ad);
     K.R = (float)P.R_disk;
     K.R2 = (float)(P.R_disk * P.R_disk);
     const double reach = P.R_disk + 1.02 * s;
     K.disk_reach2 = (float)(reach * reach);
     K.cfl_h = P.cfl * h;
+    K.cfl_h_f = (float)K.cfl_h;
+    K.dt_fixed = K.cfl_h / (P.c0 + P.v0);
     K.c0d = P.c0;
     K.v0 = P.v0;
     K.tau = P.tau;
@@ -444,10 +460,11 @@ void make_consts(hr_case *c)
 }
 
 struct Offsets {
-    size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_acc, st_X, u_pos, u_vel, u_rd,
+    size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_a, st_D, st_X, u_pos, u_vel,
         u_id, u_key, u_slot, cell_count, cell_start, tile_sum, perm_tmp, gw_pos, gw_nrm,
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
-        probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w;
+        probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
+        fin_part, fin_vmax, fin_npen, fin_ticket;
     size_t total;
 };
 
@@ -464,11 +481,11 @@ Offsets plan(const hr_case *c)
     o.s_id = L.add(n * 4);
     o.st_vel = L.add(n * 8);
     o.st_rho = L.add(n * 4);
-    o.st_acc = L.add(n * 16);
+    o.st_a = L.add(n * 8);
+    o.st_D = L.add(n * 8);
     o.st_X = L.add(n * 8);
     o.u_pos = L.add(n * 8);
     o.u_vel = L.add(n * 8);
-    o.u_rd = L.add(n * 16);
     o.u_id = L.add(n * 4);
     o.u_key = L.add(n * 4);
     o.u_slot = L.add(n * 4);
@@ -487,12 +504,17 @@ Offsets plan(const hr_case *c)
     o.g_aux = L.add(ng * 16);
     o.ghost_vmax = L.add((size_t)c->ghost_blocks * 4);
     o.pass_part = L.add((size_t)c->pass_blocks * 16);
-    o.part_w = L.add((size_t)c->pass_blocks * 16);
+    o.part_w = L.add(16);
     o.part_vmax = L.add((size_t)c->pass_blocks * 4);
     o.part_npen = L.add((size_t)c->pass_blocks * 4);
+    o.probe_now = L.add(kMaxProbes * 4);
     o.probe_hist = L.add((size_t)K.probe_cap * (size_t)std::max(K.n_probes, 1) * 4);
     o.probe_t = L.add((size_t)K.probe_cap * 8);
     o.S = L.add(sizeof(Scalars));
+    o.fin_part = L.add(kFinalizeBlocks * 8 * 4);
+    o.fin_vmax = L.add(kFinalizeBlocks * 4);
+    o.fin_npen = L.add(kFinalizeBlocks * 4);
+    o.fin_ticket = L.add(4);
     o.diag_part = L.add((size_t)c->diag_blocks * 16 * 8);
     o.diag_out = L.add(kDiagFields * 8);
     const long long dcap = c->P.diag_every > 0 ? 4096 : 1;
@@ -519,11 +541,11 @@ void bind(hr_case *c, const Offsets &o)
     B.s_id = at<int>(w, o.s_id);
     B.st_vel = at<float2>(w, o.st_vel);
     B.st_rho = at<float>(w, o.st_rho);
-    B.st_acc = at<float4>(w, o.st_acc);
+    B.st_a = at<float2>(w, o.st_a);
+    B.st_D = at<float2>(w, o.st_D);
     B.st_X = at<float2>(w, o.st_X);
     B.u_pos = at<float2>(w, o.u_pos);
     B.u_vel = at<float2>(w, o.u_vel);
-    B.u_rd = at<float4>(w, o.u_rd);
     B.u_id = at<int>(w, o.u_id);
     B.u_key = at<int>(w, o.u_key);
     B.u_slot = at<int>(w, o.u_slot);
@@ -541,13 +563,17 @@ void bind(hr_case *c, const Offsets &o)
     B.g_vel = at<float2>(w, o.g_vel);
     B.g_aux = at<float4>(w, o.g_aux);
     B.ghost_vmax = at<float>(w, o.ghost_vmax);
-    B.part.f = at<double2>(w, o.pass_part);
-    B.part.w = at<double2>(w, o.part_w);
+    B.part.f = at<float4>(w, o.pass_part);
     B.part.vmax = at<float>(w, o.part_vmax);
     B.part.npen = at<int>(w, o.part_npen);
+    B.probe_now = at<float>(w, o.probe_now);
     B.probe_hist = at<float>(w, o.probe_hist);
     B.probe_t = at<double>(w, o.probe_t);
     B.S = at<Scalars>(w, o.S);
+    B.fin_part = at<float>(w, o.fin_part);
+    B.fin_vmax = at<float>(w, o.fin_vmax);
+    B.fin_npen = at<int>(w, o.fin_npen);
+    B.fin_ticket = at<int>(w, o.fin_ticket);
     c->diag_part = at<double>(w, o.diag_part);
     c->diag_out = at<double>(w, o.diag_out);
     c->diag_hist = at<double>(w, o.diag_hist);
@@ -565,25 +591,35 @@ void bind(hr_case *c, const Offsets &o)
         }                                                           \
     } while (0)
 
-// The kernels of one step (prime = 1: evaluate without advancing).
-int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events)
+// The kernels of one step (prime = 1: evaluate without advancing).  With a
+// side stream (graph capture) the kinematics run on a branch that joins
+// before the ghost pass; without one they run first on the same stream.
+int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side)
 {
     const Consts &K = c->K;
     const Bufs &B = c->B;
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
+    if (side) {
+        CK(cudaEventRecord(c->fork, s));
+        CK(cudaStreamWaitEvent(side, c->fork, 0));
+        k_kinematics<<<1, 128, 0, side>>>(K, B, prime);
+        CK(cudaEventRecord(c->join, side));
+    } else {
+        k_kinematics<<<1, 128, 0, s>>>(K, B, prime);
+    }
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     k_scan_tiles<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
-    k_scan_mid<<<1, kScanThreads, 0, s>>>(K, B, c->n_tiles, prime);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
-    k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B);
+    k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
+    if (side) CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     k_pass<<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-    k_finalize<<<1, kFinalizeThreads, 0, s>>>(K, B, prime);
+    k_finalize<<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
     return HR_OK;
@@ -600,7 +636,7 @@ int capture(hr_case *c)
         c->graph = nullptr;
     }
     CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_step(c, c->cap, 0, c->timing);
+    const int rc = launch_step(c, c->cap, 0, c->timing, c->cap2);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (rc != HR_OK) return rc;
@@ -636,9 +672,11 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
     CK(cudaMemcpyAsync(c->B.st_vel, v.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->B.st_rho, d.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(c->B.st_acc, 0, n * 16, c->stream));
+    CK(cudaMemsetAsync(c->B.st_a, 0, n * 8, c->stream));
+    CK(cudaMemsetAsync(c->B.st_D, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.st_X, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(c->B.fin_ticket, 0, 4, c->stream));
     Scalars S;
     std::memset(&S, 0, sizeof S);
     CK(cudaMemcpyAsync(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice, c->stream));
@@ -651,7 +689,7 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
 
 int prime(hr_case *c)
 {
-    const int rc = launch_step(c, c->stream, 1, false);
+    const int rc = launch_step(c, c->stream, 1, false, nullptr);
     if (rc != HR_OK) return rc;
     return device_status(c);
 }
@@ -759,7 +797,10 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
         c->ws_bytes = o.total;
     }
     bind(c, o);
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(HR_ECUDA);
     for (int k = 0; k < kTimingEvents; ++k)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(HR_ECUDA);
@@ -1065,7 +1106,9 @@ int hr_save_state(hr_case *c, const char *path)
         cudaMemcpy(vel.data(), c->B.st_vel, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(X.data(), c->B.st_X, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(d.data(), c->B.st_rho, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(acc.data(), c->B.st_acc, n * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy2D(acc.data(), 16, c->B.st_a, 8, 8, n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy2D(reinterpret_cast<char *>(acc.data()) + 8, 16, c->B.st_D, 8, 8, n,
+                     cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost) != cudaSuccess)
         return HR_ECUDA;
     std::vector<float2> pos2(n), vel2(n), X2(n);
@@ -1144,10 +1187,13 @@ int hr_load_state(hr_case *c, const char *path)
     CK(cudaMemcpy(c->B.s_pos, pos.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.st_vel, vel.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.st_rho, d.data(), n * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->B.st_acc, acc.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy2D(c->B.st_a, 8, acc.data(), 16, 8, n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy2D(c->B.st_D, 8, reinterpret_cast<const char *>(acc.data()) + 8, 16, 8, n,
+                    cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.st_X, X.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice));
     CK(cudaMemset(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4));
+    CK(cudaMemset(c->B.fin_ticket, 0, 4));
     CK(cudaMemcpy(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice));
     if (hn > 0 && c->K.n_probes > 0) {
         CK(cudaMemcpy(c->B.probe_hist, ph.data(), ph.size() * 4, cudaMemcpyHostToDevice));
@@ -1185,6 +1231,9 @@ void hr_destroy(hr_case *c)
     for (int k = 0; k < kTimingEvents; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
 }

@@ -4,10 +4,10 @@
 // One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is nine kernels:
 //   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key and
 //                   in-cell slot (atomic count)                  [T, first half]
-//   k_scan_tiles    \
-//   k_scan_mid       > exclusive scan of the cell counts; k_scan_mid also
-//   k_scan_apply    /  advances t and the projectile kinematics (FP64) and
-//                      places the disk ghosts
+//   k_kinematics     advances t, projectile kinematics (FP64), disk ghost ring
+//                    (a branch of the step graph, beside the drift and sort)
+//   k_scan_tiles     tile sums of the cell counts
+//   k_scan_apply     cell starts (each block scans the tile sums before it)
 //   k_slot           provisional scatter of old indices into cell order
 //   k_rank_scatter   stable rank by fluid ID inside the cell, SoA reorder,
 //                    Tait pressure of the predicted density
@@ -31,7 +31,8 @@ constexpr int kPassThreads = 128;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kFinalizeThreads = 1024;
+constexpr int kFinalizeThreads = 256;
+constexpr int kFinalizeBlocks = 64;
 constexpr int kGhostWarps = 8;
 
 // device status bits (warnings share the public HR_W* values)
@@ -59,9 +60,10 @@ struct Consts {
     int gamma7;
     // ghosts
     int nf, nw, ng;
-    float m_wall, m_disk, wall_over_m, disk_over_m, m_over_rho0, R, disk_reach2, R2;
+    float m_wall, m_disk, wall_over_m, disk_over_m, m_over_rho0, m2Wc, R, disk_reach2, R2;
     // CFL and kinematics (FP64)
-    double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k;
+    double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k, dt_fixed;
+    float cfl_h_f;
     int dt_mode, motion;
     // probes
     int n_probes;
@@ -81,13 +83,15 @@ struct Scalars {
     long long hist_n;
     int status;
     int pad;
+    // single-precision copies for the per-particle kernels (the FP64 pipe of
+    // the B300 is far too slow to convert doubles in every thread)
+    float dt_f, ratio_f, xc_f, yc_f, vproj_f, aproj_f;
 };
 
 // Per-block partials of the interaction pass, structure of arrays so the
 // finalize kernel streams them with wide independent loads.
 struct PassPartials {
-    double2 *f;      // {F_disk,x, F_disk,y}
-    double2 *w;      // {F_wall, dissipation rate}
+    float4 *f;       // {F_disk,x, F_disk,y, F_wall, dissipation rate} / m^2 except the last
     float *vmax;
     int *npen;
 };
@@ -99,17 +103,17 @@ struct Bufs {
     // sorted (k_rank_scatter)
     float2 *s_pos;   // r^{n+1}
     float2 *s_vel;   // v^{n+1/2}
-    float4 *s_aux;   // {d~, p~, p~/rho~^2, c~}   predicted density and its EOS
+    float4 *s_aux;   // {d~, p~, p~/rho~^2, -alpha h c~}  predicted density and its EOS
     float2 *s_rd;    // {d^n, D^n}                 for the corrected density
     int *s_id;
     // end-of-step state (k_pass epilogue)
     float2 *st_vel;  // v^{n+1}
     float *st_rho;   // d^{n+1}
-    float4 *st_acc;  // {a_x, a_y, D^{n+1}, D^n}   D in units of d per second
+    float2 *st_a;    // a^{n+1}
+    float2 *st_D;    // {D^{n+1}, D^n}   density rate in units of d per second
     float2 *st_X;    // XSPH sum X^{n+1}
     // drifted, unsorted
     float2 *u_pos, *u_vel;
-    float4 *u_rd;    // {d^n, d~, D^n, 0}
     int *u_id, *u_key, *u_slot;
     // cell list
     int *cell_count; // ncell + 1 (last = frozen particles)
@@ -125,10 +129,15 @@ struct Bufs {
     float2 *gd_pos;
     // ghost state: walls [0, nw), disk [nw, nw + ng)
     float2 *g_vel;
-    float4 *g_aux;     // {d_g, p_g, p_g / rho_g^2, c_g}
+    float4 *g_aux;     // {d_g, p_g, p_g / rho_g^2, -alpha h c_g}
     float *ghost_vmax; // per ghost block
     PassPartials part;
+    float *fin_part;   // kFinalizeBlocks x 4 two-float sums
+    float *fin_vmax;
+    int *fin_npen;
+    int *fin_ticket;
     // probes
+    float *probe_now;  // this step's values, one per probe
     float *probe_hist;
     double *probe_t;
     // scalars
@@ -189,11 +198,13 @@ __device__ __forceinline__ float sound_speed(const Consts &K, float d)
     return K.c0 * __powf(1.0f + d, K.half_gm1);
 }
 
+// {d, p, p / rho^2, -alpha h c}: what a neighbour contributes to the pair
+// terms (the last entry is the artificial-viscosity signal factor).
 __device__ __forceinline__ float4 eos_record(const Consts &K, float d)
 {
     const float p = tait_p(K, d);
     const float rho = K.rho0 * (1.0f + d);
-    return make_float4(d, p, p / (rho * rho), sound_speed(K, d));
+    return make_float4(d, p, p / (rho * rho), -K.alpha_h * sound_speed(K, d));
 }
 
 __device__ __forceinline__ float band(const Consts &K, float d)
@@ -213,6 +224,37 @@ __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Compensated single-precision sums ("two-float": hi + lo carries about 48
+// bits; Knuth's TwoSum for the error of each addition).  Used for the
+// per-step reductions so they keep near-FP64 accuracy on the FP32 pipes; the
+// B300's FP64 pipe is slow enough that a warp-wide FP64 reduction costs
+// microseconds.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = a.lo + b.lo + err;
+    const float hi = s + lo;
+    return F2{hi, lo - (hi - s)};
+}
+
+__device__ __forceinline__ F2 f2_warp_sum(F2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F2 u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = f2_add(v, u);
+    }
     return v;
 }
 
@@ -296,27 +338,22 @@ __device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, flo
 
 // ----------------------------------------------------- a2: drift and key
 
-// Opening kick, XSPH drift, wall enforcement, predicted density and cell key.
-// prime = 1 evaluates the current state without advancing (dt = 0).
+// Opening kick, XSPH drift, wall enforcement and cell key (the predicted
+// density is formed in k_rank_scatter from the same state).  prime = 1
+// evaluates the current state without advancing (dt = 0).
 __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
-    const double dtd = prime ? 0.0 : B.S->dt;
-    const double dtp = B.S->dt_prev;
-    const float dt = (float)dtd;
-    const float ratio = (!prime && dtp > 0.0) ? (float)(dtd / dtp) : 1.0f;
+    const float dt = prime ? 0.0f : B.S->dt_f;
     float2 r = B.s_pos[i];
     const float2 v = B.st_vel[i];
-    const float d = B.st_rho[i];
-    const float4 a = B.st_acc[i];
+    const float2 a = B.st_a[i];
     const float2 X = B.st_X[i];
     float2 vh;
-    float dp;
     int key;
     if (outside_box(K, r.x, r.y)) {
         vh = v;
-        dp = d;
         key = K.ncell;
     } else {
         vh.x = fmaf(0.5f * dt, a.x, v.x);
@@ -331,11 +368,7 @@ __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
                 else if (r.x < 0.0f) { r.x = 1e-6f; vh.x = -vh.x; }
             }
         }
-        // predicted density: D extrapolated linearly over the step
-        const float Dp = fmaf(ratio, a.z - a.w, a.z);
-        dp = band(K, fmaf(dt, Dp, d));
-        if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(vh.x) || !isfinite(vh.y) ||
-            !isfinite(dp))
+        if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(vh.x) || !isfinite(vh.y))
             atomicOr(&B.S->status, ST_NAN);
         if (outside_box(K, r.x, r.y)) {
             key = K.ncell;
@@ -346,7 +379,6 @@ __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
     }
     B.u_pos[i] = r;
     B.u_vel[i] = vh;
-    B.u_rd[i] = make_float4(d, dp, a.z, 0.0f);
     B.u_id[i] = B.s_id[i];
     B.u_key[i] = key;
     B.u_slot[i] = atomicAdd(&B.cell_count[key], 1);
@@ -381,7 +413,36 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int *
     return before + x - v;
 }
 
-// Tile sums of the cell counts (ncell + 1 entries).
+// a1: advances t by dt (unless priming), evaluates the projectile
+// kinematics at t^{n+1} in FP64 and places the disk ghost ring there.  One
+// block; in the step graph it runs on a branch beside the drift and the sort.
+__global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
+{
+    __shared__ double kin[2];
+    if (threadIdx.x == 0) {
+        Scalars *S = B.S;
+        if (!prime) S->t += S->dt;
+        double x, v, a;
+        kinematics(K, S->t, &x, &v, &a);
+        S->xc = x;
+        S->yc = K.y_c0;
+        S->vproj = v;
+        S->aproj = a;
+        S->xc_f = (float)x;
+        S->yc_f = (float)K.y_c0;
+        S->vproj_f = (float)v;
+        S->aproj_f = (float)a;
+        kin[0] = x;
+        kin[1] = K.y_c0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K.ng; k += blockDim.x) {
+        const double2 o = B.disk_off[k];
+        B.gd_pos[k] = make_float2((float)(kin[0] + o.x), (float)(kin[1] + o.y));
+    }
+}
+
+// Tile sums of the cell counts (ncell + 1 entries), one block per tile.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
 {
     __shared__ int red[kScanThreads / 32];
@@ -400,45 +461,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
     }
 }
 
-// Exclusive scan of the tile sums (one block), then the time advance and
-// the disk ghost ring at t^{n+1} (a1).
-__global__ void __launch_bounds__(kScanThreads) k_scan_mid(Consts K, Bufs B, int n_tiles, int prime)
-{
-    __shared__ int wsum[kScanThreads / 32];
-    __shared__ double kin[3];
-    int carry = 0;
-    for (int base = 0; base < n_tiles; base += kScanThreads) {
-        const int idx = base + threadIdx.x;
-        const int v = idx < n_tiles ? B.tile_sum[idx] : 0;
-        int total;
-        const int ex = block_exclusive_scan(v, wsum, &total);
-        if (idx < n_tiles) B.tile_sum[idx] = carry + ex;
-        carry += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        Scalars *S = B.S;
-        if (!prime) S->t += S->dt;
-        double x, v, a;
-        kinematics(K, S->t, &x, &v, &a);
-        S->xc = x;
-        S->yc = K.y_c0;
-        S->vproj = v;
-        S->aproj = a;
-        kin[0] = x;
-        kin[1] = K.y_c0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K.ng; k += blockDim.x) {
-        const double2 o = B.disk_off[k];
-        B.gd_pos[k] = make_float2((float)(kin[0] + o.x), (float)(kin[1] + o.y));
-    }
-}
-
-// Cell starts: per-tile exclusive scan plus the tile offset; counts reset.
+// Cell starts: each block adds up the sums of the tiles before it, then an
+// exclusive scan of its own tile; the counts are reset for the next step.
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
 {
     __shared__ int wsum[kScanThreads / 32];
+    __shared__ int offset;
+    int o = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) o += B.tile_sum[t];
+    o = warp_sum(o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = o;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < kScanThreads / 32; ++k) t += wsum[k];
+        offset = t;
+    }
+    __syncthreads();
     const int n = K.ncell + 1;
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     int v[kScanItems];
@@ -449,7 +488,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
         s += v[k];
     }
     int total;
-    int ex = block_exclusive_scan(s, wsum, &total) + B.tile_sum[blockIdx.x];
+    int ex = block_exclusive_scan(s, wsum, &total) + offset;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) {
@@ -470,9 +509,10 @@ __global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
 }
 
 // Stable order inside a cell: rank by fluid ID among the cell's members.
-// Then the reorder into the SoA arrays of this step, with the Tait
-// pressure of the predicted density.
-__global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B)
+// Then the reorder into the SoA arrays of this step, with the predicted
+// density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n - D^{n-1})))
+// and its Tait pressure.
+__global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prime)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
@@ -483,11 +523,18 @@ __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B)
 #pragma unroll 4
     for (int k = cs; k < ce; ++k) rank += __ldg(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
-    const float4 rd = B.u_rd[i];
+    const float d = B.st_rho[i];
+    const float2 D = B.st_D[i];
+    float dp = d;
+    if (key != K.ncell) {
+        const float dt = prime ? 0.0f : B.S->dt_f;
+        const float ratio = prime ? 1.0f : B.S->ratio_f;
+        dp = band(K, fmaf(dt, fmaf(ratio, D.x - D.y, D.x), d));
+    }
     B.s_pos[dst] = B.u_pos[i];
     B.s_vel[dst] = B.u_vel[i];
-    B.s_aux[dst] = eos_record(K, rd.y);
-    B.s_rd[dst] = make_float2(rd.x, rd.z);
+    B.s_aux[dst] = eos_record(K, dp);
+    B.s_rd[dst] = make_float2(d, D.x);
     B.s_id[dst] = id;
 }
 
@@ -508,8 +555,8 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
     if (g < K.nw + K.ng) {
         const bool disk = g >= K.nw;
         const float2 rg = disk ? B.gd_pos[g - K.nw] : B.gw_pos[g];
-        const float vwx = disk ? (float)B.S->vproj : 0.0f;
-        const float awx = disk ? (float)B.S->aproj : 0.0f;
+        const float vwx = disk ? B.S->vproj_f : 0.0f;
+        const float awx = disk ? B.S->aproj_f : 0.0f;
         float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f, Svx = 0.f, Svy = 0.f;
         const bool inside = !outside_box(K, rg.x, rg.y);
         if (inside) {
@@ -553,10 +600,10 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
             pg = fmaxf(pg, K.p_cav);
             const float dg = pg * K.inv_rho0c02;
             const float rho = K.rho0 * (1.0f + dg);
-            aux = make_float4(dg, pg, pg / (rho * rho), sound_speed(K, dg));
+            aux = make_float4(dg, pg, pg / (rho * rho), -K.alpha_h * sound_speed(K, dg));
             vg = make_float2(2.0f * vwx - Svx * inv, -Svy * inv);
         } else {
-            aux = make_float4(0.0f, 0.0f, 0.0f, K.c0);
+            aux = make_float4(0.0f, 0.0f, 0.0f, -K.alpha_h * K.c0);
             vg = make_float2(vwx, 0.0f);
         }
         if (lane == 0) {
@@ -588,7 +635,9 @@ struct Acc {
 // viscosity (eqs. momentum, artificial-viscosity) and, when xsph, the XSPH
 // sum (eq. xsph).  Adds mj times the pair terms (mj = 1 for fluid pairs: the
 // uniform fluid mass is applied once per particle) and returns the
-// acceleration contribution of j on i per unit mass mj.
+// acceleration contribution of j on i per unit mass mj.  I.c and cj hold
+// -alpha h c, so Pi_ij = (c'_i + c'_j) min(v_ij . r_ij, 0) / ((r^2 + eta^2 h^2)
+// (rho_i + rho_j)) is -alpha cbar mu / rhobar under approach and 0 otherwise.
 __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float xj, float yj,
                                              float vxj, float vyj, float rhoj, float Pj,
                                              float cj, float mj, bool xsph, Acc &A)
@@ -603,41 +652,58 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     const float vr = fmaf(vx, dx, vy * dy);
     A.dr = fmaf(F, vr, A.dr);                           // continuity
     const float e = r2 + K.eh2;
-    const float inv = __fdividef(1.0f, e * (I.rho + rhoj));  // 1/((r^2 + eta^2 h^2)(rho_i + rho_j))
-    const float Pi_ij = -K.alpha_h * (I.c + cj) * fminf(vr, 0.0f) * inv;  // -alpha cbar mu / rhobar
-    const float S = -(I.P + Pj + Pi_ij) * F;            // pressure + AV
+    const float inv = __fdividef(1.0f, e * (I.rho + rhoj));
+    const float Pi_ij = (I.c + cj) * fminf(vr, 0.0f) * inv;
+    const float PF = (I.P + Pj + Pi_ij) * F;
     const float lam = K.nu4 * F * r2 * inv;             // laminar
-    const float fx = fmaf(S, dx, lam * vx);
-    const float fy = fmaf(S, dy, lam * vy);
+    const float fx = fmaf(-PF, dx, lam * vx);
+    const float fy = fmaf(-PF, dy, lam * vy);
     A.ax += fx;
     A.ay += fy;
-    const float av = -Pi_ij * F;
-    A.avx = fmaf(av, dx, A.avx);
-    A.avy = fmaf(av, dy, A.avy);
+    const float av = Pi_ij * F;                         // minus the AV acceleration factor
+    A.avx = fmaf(-av, dx, A.avx);
+    A.avy = fmaf(-av, dy, A.avy);
     if (xsph) {
-        const float W = mj * K.Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f);
-        const float wx = -2.0f * W * inv * e;           // -(m_j / rhobar) W
+        // -(m_j / rhobar) W = -2 W / (rho_i + rho_j) (mj = 1)
+        const float wx = K.m2Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f) * (inv * e);
         A.Xx = fmaf(wx, vx, A.Xx);
         A.Xy = fmaf(wx, vy, A.Xy);
     }
     return make_float2(fx, fy);
 }
 
+// Predicate mask of the candidates [base, base + cnt), cnt <= 32.
+__device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float x,
+                                                 float y, float s2)
+{
+    unsigned m = 0u;
+    const float2 *pp = pos + base;
+#pragma unroll 8
+    for (int k = 0; k < cnt; ++k) {
+        const float2 rj = __ldg(pp + k);
+        m |= (unsigned)in_support(x, y, rj.x, rj.y, s2) << k;
+    }
+    return m;
+}
+
 // The fused interaction pass.  One thread per sorted fluid particle i.
-// Candidates are scanned per stencil row in chunks of 32: the float
-// predicate of each candidate sets one bit of a mask (loads unrolled, no
-// per-candidate branching), then the pair terms run over the set bits.
-// Ghost neighbours follow (static wall lists, then the disk ring).  The
-// epilogue applies the uniform fluid mass, the corrected density and the
-// closing half kick.  Block partials of the ghost forces, the dissipation
-// rate and max |v| are reduced in FP32 per warp and in FP64 per block.
+// Phase 1: for each of the three stencil rows, the float predicate of each
+// candidate sets one bit of a mask (unrolled loads, no per-candidate
+// branching).  Phase 2: one loop over the set bits of all three masks
+// evaluates the pair terms, so a warp runs as many iterations as its busiest
+// lane has neighbours.  Rows with more than 32 candidates are handled in
+// chunks on the spot.  Ghost neighbours follow (static wall lists, then the
+// disk ring).  The epilogue applies the uniform fluid mass, the corrected
+// density and the closing half kick.  Block partials of the ghost forces,
+// the dissipation rate and max |v| are reduced in FP32 per warp and in FP64
+// per block.
 __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
 {
     __shared__ float red[kPassThreads / 32][5];
     __shared__ int redn[kPassThreads / 32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float dt = prime ? 0.0f : (float)B.S->dt;
+    const float dt = prime ? 0.0f : B.S->dt_f;
     float fdx = 0.0f, fdy = 0.0f, fw = 0.0f, diss = 0.0f, vmax = 0.0f;
     int npen = 0;
     if (i < K.nf) {
@@ -649,37 +715,65 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
             // frozen: keeps its state, takes part in nothing
             B.st_vel[i] = vi;
             B.st_rho[i] = rd.x;
-            B.st_acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            B.st_a[i] = make_float2(0.f, 0.f);
+            B.st_D[i] = make_float2(0.f, 0.f);
             B.st_X[i] = make_float2(0.f, 0.f);
         } else {
             const Self I{ri.x, ri.y, vi.x, vi.y, fmaf(K.rho0, ai.x, K.rho0), ai.z, ai.w};
             Acc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            auto fluid_pair = [&](int j) {
+                const float2 rj = __ldg(&B.s_pos[j]);
+                const float2 vj = __ldg(&B.s_vel[j]);
+                const float4 aj = __ldg(&B.s_aux[j]);
+                pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z, aj.w,
+                           1.0f, true, A);
+            };
             const int c = cell_of(K, ri.x, ri.y);
+            int base0, base1, base2;
+            unsigned m0, m1, m2;
+            {
+                const int r0 = c - K.ncx, r1 = c, r2 = c + K.ncx;
+                base0 = B.cell_start[r0 - 1];
+                base1 = B.cell_start[r1 - 1];
+                base2 = B.cell_start[r2 - 1];
+                const int e0 = B.cell_start[r0 + 2], e1 = B.cell_start[r1 + 2],
+                          e2 = B.cell_start[r2 + 2];
+                // rows longer than 32 candidates: chunks evaluated right away
+                auto row_mask = [&](int a, int b) -> unsigned {
+                    if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri.x, ri.y, K.s2);
 #pragma unroll 1
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int row = c + dy * K.ncx;
-                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                    for (int base = a; base < b; base += 32) {
+                        unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri.x, ri.y,
+                                                  K.s2);
+                        if (i >= base && i < base + 32) m &= ~(1u << (i - base));
+                        while (m) {
+                            const int j = base + __ffs(m) - 1;
+                            m &= m - 1u;
+                            fluid_pair(j);
+                        }
+                    }
+                    return 0u;
+                };
+                m0 = row_mask(base0, e0);
+                m1 = row_mask(base1, e1);
+                m2 = row_mask(base2, e2);
+                // the particle itself sits in the middle row
+                if (i >= base1 && i < base1 + 32) m1 &= ~(1u << (i - base1));
+            }
 #pragma unroll 1
-                for (int base = a; base < b; base += 32) {
-                    const int cnt = min(32, b - base);
-                    const float2 *pp = B.s_pos + base;
-                    unsigned m = 0u;
-#pragma unroll 8
-                    for (int k = 0; k < cnt; ++k) {
-                        const float2 rj = __ldg(pp + k);
-                        m |= (unsigned)in_support(ri.x, ri.y, rj.x, rj.y, K.s2) << k;
-                    }
-                    if (i >= base && i < base + cnt) m &= ~(1u << (i - base));
-                    while (m) {
-                        const int j = base + __ffs(m) - 1;
-                        m &= m - 1u;
-                        const float2 rj = __ldg(&B.s_pos[j]);
-                        const float2 vj = __ldg(&B.s_vel[j]);
-                        const float4 aj = __ldg(&B.s_aux[j]);
-                        pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z,
-                                   aj.w, 1.0f, true, A);
-                    }
+            while ((m0 | m1 | m2) != 0u) {
+                int j;
+                if (m0) {
+                    j = base0 + __ffs(m0) - 1;
+                    m0 &= m0 - 1u;
+                } else if (m1) {
+                    j = base1 + __ffs(m1) - 1;
+                    m1 &= m1 - 1u;
+                } else {
+                    j = base2 + __ffs(m2) - 1;
+                    m2 &= m2 - 1u;
                 }
+                fluid_pair(j);
             }
             // wall ghosts (static cell list)
             if (K.nw > 0) {
@@ -699,7 +793,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
             }
             // disk ghosts (the ring, only near the disk)
             if (K.ng > 0) {
-                const float xc = (float)B.S->xc, yc = (float)B.S->yc;
+                const float xc = B.S->xc_f, yc = B.S->yc_f;
                 if (near_disk(K, ri.x, ri.y, xc, yc)) {
                     for (int k = 0; k < K.ng; ++k) {
                         const float2 rg = B.gd_pos[k];
@@ -726,7 +820,8 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
                 atomicOr(&B.S->status, ST_NAN);
             B.st_vel[i] = vnew;
             B.st_rho[i] = dnew;
-            B.st_acc[i] = make_float4(ax, ay, Dd, prime ? Dd : rd.y);
+            B.st_a[i] = make_float2(ax, ay);
+            B.st_D[i] = make_float2(Dd, prime ? Dd : rd.y);
             B.st_X[i] = make_float2(K.m * A.Xx, K.m * A.Xy);
             vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
             diss = -K.m * K.m * (vi.x * A.avx + vi.y * A.avy);
@@ -749,20 +844,17 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double m2 = (double)K.m * (double)K.m;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        float v = 0.0f;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, v = 0.f;
         int np = 0;
         for (int k = 0; k < kPassThreads / 32; ++k) {
-            a0 += (double)red[k][0];
-            a1 += (double)red[k][1];
-            a2 += (double)red[k][2];
-            a3 += (double)red[k][3];
+            a0 += red[k][0];
+            a1 += red[k][1];
+            a2 += red[k][2];
+            a3 += red[k][3];
             v = fmaxf(v, red[k][4]);
             np += redn[k];
         }
-        B.part.f[blockIdx.x] = make_double2(m2 * a0, m2 * a1);
-        B.part.w[blockIdx.x] = make_double2(m2 * a2, a3);
+        B.part.f[blockIdx.x] = make_float4(a0, a1, a2, a3);
         B.part.vmax[blockIdx.x] = v;
         B.part.npen[blockIdx.x] = np;
     }
@@ -770,105 +862,186 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
 
 // ----------------------------------- a6, a7: probes, accumulators, gate
 
+// Wall-probe value (reading R13: the wall-ghost formula with a = 0, body
+// force kept, cutoff applied) at (px, py) over the end-of-step fluid, by one
+// warp.  The three stencil rows are flattened into one candidate range so
+// the lanes' loads go out together.
+__device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, float px, float py)
+{
+    const int lane = threadIdx.x & 31;
+    float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
+    if (!outside_box(K, px, py)) {
+        const int c = cell_of(K, px, py);
+        const int a0 = B.cell_start[c - K.ncx - 1], b0 = B.cell_start[c - K.ncx + 2];
+        const int a1 = B.cell_start[c - 1], b1 = B.cell_start[c + 2];
+        const int a2 = B.cell_start[c + K.ncx - 1], b2 = B.cell_start[c + K.ncx + 2];
+        const int n0 = b0 - a0, n1 = b1 - a1, n = n0 + n1 + (b2 - a2);
+        for (int k = lane; k < n; k += 32) {
+            const int j = k < n0 ? a0 + k : (k < n0 + n1 ? a1 + (k - n0) : a2 + (k - n0 - n1));
+            const float2 rj = B.s_pos[j];
+            const float d = B.st_rho[j];
+            if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
+            const float dx = px - rj.x, dy = py - rj.y;
+            const float r = sqrtf(fmaf(dx, dx, dy * dy));
+            const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+            const float t2 = t * t;
+            const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+            const float rw = (1.0f + d) * W;
+            SW += W;
+            Sp = fmaf(tait_p(K, d), W, Sp);
+            Srx = fmaf(rw, dx, Srx);
+            Sry = fmaf(rw, dy, Sry);
+        }
+    }
+    SW = warp_sum(SW);
+    Sp = warp_sum(Sp);
+    Srx = warp_sum(Srx);
+    Sry = warp_sum(Sry);
+    if (SW > 0.0f) return fmaxf((Sp + K.rho0 * (K.gx * Srx + K.gy * Sry)) / SW, K.p_cav);
+    return 0.0f;
+}
+
+// Closes the step.  kFinalizeBlocks blocks reduce slices of the pass and
+// ghost partials; the block that finishes last (atomic ticket) reduces the
+// block results, updates the FP64 accumulators and applies the CFL gate (a6).
+// Block q < n_probes first samples wall probe q (a7) into probe_now[q].  The
+// sums are compensated FP32 (two-float) in a fixed tree order, converted to
+// FP64 once at the end.
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
 {
-    __shared__ double red[kFinalizeThreads / 32][4];
-    __shared__ float redv[kFinalizeThreads / 32];
-    __shared__ int redn[kFinalizeThreads / 32];
+    constexpr int NW = kFinalizeThreads / 32;
+    __shared__ F2 redd[4][NW];
+    __shared__ float redv[NW];
+    __shared__ int redn[NW];
     __shared__ float probe_p[kMaxProbes];
     __shared__ Scalars S;
+    __shared__ int is_last;
+    __shared__ F2 tot[4];
+    __shared__ float totv;
+    __shared__ int totn;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // the device scalars, read once into shared memory
-    static_assert(sizeof(Scalars) % 8 == 0, "Scalars is copied as doubles");
-    for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
-        reinterpret_cast<double *>(&S)[k] = reinterpret_cast<const double *>(B.S)[k];
-    // a7: wall probes, one warp each, on the end-of-step state
-    if (!prime && w < K.n_probes) {
-        const float px = K.probe_x[w], py = K.probe_y[w];
-        float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
-        if (!outside_box(K, px, py)) {
-            const int c = cell_of(K, px, py);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int row = c + dy * K.ncx;
-                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
-                for (int j = a + lane; j < b; j += 32) {
-                    const float2 rj = B.s_pos[j];
-                    if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
-                    const float dx = px - rj.x, dy2 = py - rj.y;
-                    const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
-                    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
-                    const float t2 = t * t;
-                    const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
-                    const float d = B.st_rho[j];
-                    const float rw = (1.0f + d) * W;
-                    SW += W;
-                    Sp = fmaf(tait_p(K, d), W, Sp);
-                    Srx = fmaf(rw, dx, Srx);
-                    Sry = fmaf(rw, dy2, Sry);
-                }
+    const int nb = gridDim.x;
+    if (!prime && (int)blockIdx.x < K.n_probes && w == 0) {
+        const float pv = probe_value(K, B, K.probe_x[blockIdx.x], K.probe_y[blockIdx.x]);
+        if (lane == 0) B.probe_now[blockIdx.x] = pv;
+    }
+    // reduce one (value per thread) set of four sums, max and count over the
+    // block; the results land in tot[] (lane 0 of warp 0 writes them)
+    auto block_reduce = [&](F2 a0, F2 a1, F2 a2, F2 a3, float v, int np) {
+        a0 = f2_warp_sum(a0);
+        a1 = f2_warp_sum(a1);
+        a2 = f2_warp_sum(a2);
+        a3 = f2_warp_sum(a3);
+        v = warp_max(v);
+        np = warp_sum(np);
+        if (lane == 0) {
+            redd[0][w] = a0;
+            redd[1][w] = a1;
+            redd[2][w] = a2;
+            redd[3][w] = a3;
+            redv[w] = v;
+            redn[w] = np;
+        }
+        __syncthreads();
+        if (w == 0) {
+            const F2 z{0.f, 0.f};
+            F2 b0 = lane < NW ? redd[0][lane] : z, b1 = lane < NW ? redd[1][lane] : z;
+            F2 b2 = lane < NW ? redd[2][lane] : z, b3 = lane < NW ? redd[3][lane] : z;
+            b0 = f2_warp_sum(b0);
+            b1 = f2_warp_sum(b1);
+            b2 = f2_warp_sum(b2);
+            b3 = f2_warp_sum(b3);
+            const float vv = warp_max(lane < NW ? redv[lane] : 0.0f);
+            const int nn = warp_sum(lane < NW ? redn[lane] : 0);
+            if (lane == 0) {
+                tot[0] = b0;
+                tot[1] = b1;
+                tot[2] = b2;
+                tot[3] = b3;
+                totv = vv;
+                totn = nn;
             }
         }
-        SW = warp_sum(SW);
-        Sp = warp_sum(Sp);
-        Srx = warp_sum(Srx);
-        Sry = warp_sum(Sry);
-        if (lane == 0) {
-            float p = 0.0f;
-            if (SW > 0.0f) p = fmaxf((Sp + K.rho0 * (K.gx * Srx + K.gy * Sry)) / SW, K.p_cav);
-            probe_p[w] = p;
+        __syncthreads();
+    };
+    {
+        F2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+        float vmax = 0.0f;
+        int npen = 0;
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K.n_pass_blocks;
+             b += nb * blockDim.x) {
+            const float4 f = B.part.f[b];
+            a0 = f2_add(a0, F2{f.x, 0.f});
+            a1 = f2_add(a1, F2{f.y, 0.f});
+            a2 = f2_add(a2, F2{f.z, 0.f});
+            a3 = f2_add(a3, F2{f.w, 0.f});
+            vmax = fmaxf(vmax, B.part.vmax[b]);
+            npen += B.part.npen[b];
         }
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
+             b += nb * blockDim.x)
+            vmax = fmaxf(vmax, B.ghost_vmax[b]);
+        block_reduce(a0, a1, a2, a3, vmax, npen);
     }
-    // reductions of the pass and ghost partials (fixed order)
-    double fdx = 0.0, fdy = 0.0, fw = 0.0, diss = 0.0;
-    float vmax = 0.0f;
-    int npen = 0;
-#pragma unroll 4
-    for (int b = threadIdx.x; b < K.n_pass_blocks; b += blockDim.x) {
-        const double2 f = B.part.f[b];
-        const double2 q = B.part.w[b];
-        fdx += f.x;
-        fdy += f.y;
-        fw += q.x;
-        diss += q.y;
-        vmax = fmaxf(vmax, B.part.vmax[b]);
-        npen += B.part.npen[b];
-    }
-    for (int b = threadIdx.x; b < K.n_ghost_blocks; b += blockDim.x)
-        vmax = fmaxf(vmax, B.ghost_vmax[b]);
-    fdx = warp_sum(fdx);
-    fdy = warp_sum(fdy);
-    fw = warp_sum(fw);
-    diss = warp_sum(diss);
-    vmax = warp_max(vmax);
-    npen = warp_sum(npen);
-    if (lane == 0) {
-        red[w][0] = fdx;
-        red[w][1] = fdy;
-        red[w][2] = fw;
-        red[w][3] = diss;
-        redv[w] = vmax;
-        redn[w] = npen;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) {
+            B.fin_part[blockIdx.x * 8 + 2 * k] = tot[k].hi;
+            B.fin_part[blockIdx.x * 8 + 2 * k + 1] = tot[k].lo;
+        }
+        B.fin_vmax[blockIdx.x] = totv;
+        B.fin_npen[blockIdx.x] = totn;
+        __threadfence();
+        is_last = atomicAdd(B.fin_ticket, 1) == nb - 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < kFinalizeThreads / 32; ++k) {
-            red[0][0] += red[k][0];
-            red[0][1] += red[k][1];
-            red[0][2] += red[k][2];
-            red[0][3] += red[k][3];
-            redv[0] = fmaxf(redv[0], redv[k]);
-            redn[0] += redn[k];
+    if (!is_last) return;
+    __threadfence();
+    static_assert(sizeof(Scalars) % 8 == 0, "Scalars is copied as doubles");
+    for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
+        reinterpret_cast<double *>(&S)[k] = __ldcg(reinterpret_cast<const double *>(B.S) + k);
+    {
+        const int b = threadIdx.x;
+        F2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float v = 0.0f;
+        int np = 0;
+        if (b < nb) {
+            for (int k = 0; k < 4; ++k)
+                a[k] = F2{__ldcg(&B.fin_part[b * 8 + 2 * k]), __ldcg(&B.fin_part[b * 8 + 2 * k + 1])};
+            v = __ldcg(&B.fin_vmax[b]);
+            np = __ldcg(&B.fin_npen[b]);
         }
+        block_reduce(a[0], a[1], a[2], a[3], v, np);
+    }
+    if (threadIdx.x < K.n_probes) probe_p[threadIdx.x] = __ldcg(&B.probe_now[threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *B.fin_ticket = 0;
         const double dt = S.dt;
-        S.Fdx = red[0][0];
-        S.Fdy = red[0][1];
-        S.Fwall = red[0][2];
-        S.diss_rate = red[0][3];
-        if (redn[0] > 0) S.status |= ST_PENETRATION;
+        const double m2 = (double)K.m * (double)K.m;
+        const double F0 = m2 * ((double)tot[0].hi + (double)tot[0].lo);
+        const double F2w = m2 * ((double)tot[2].hi + (double)tot[2].lo);
+        const double Dr = (double)tot[3].hi + (double)tot[3].lo;
+        S.Fdx = F0;
+        S.Fdy = m2 * ((double)tot[1].hi + (double)tot[1].lo);
+        S.Fwall = F2w;
+        S.diss_rate = Dr;
+        if (totn > 0) S.status |= ST_PENETRATION;
+        // a6: CFL gate over fluid and ghost velocities, FP32 (a float ulp of
+        // dt is far below every tolerance); dt_mode 1 uses the fixed host value
+        float dtf;
+        double dtn;
+        if (K.dt_mode == 1) {
+            dtn = K.dt_fixed;
+            dtf = (float)dtn;
+        } else {
+            dtf = __fdiv_rn(K.cfl_h_f, K.c0 + totv);
+            dtn = (double)dtf;
+        }
+        if (!(dtn > 1e-14)) S.status |= ST_DT;
         if (!prime) {
-            S.Wb += dt * (red[0][0] * S.vproj);
-            S.impulse += dt * red[0][2];
-            S.diss += dt * red[0][3];
+            S.Wb += dt * (F0 * S.vproj);
+            S.impulse += dt * F2w;
+            S.diss += dt * Dr;
             const long long k = S.step;
             if (k < K.probe_cap) {
                 for (int q = 0; q < K.n_probes; ++q) {
@@ -881,14 +1054,11 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
                 S.status |= ST_PROBEFULL;
             }
             S.step = k + 1;
-            S.dt_prev = dt;
         }
-        double dtn;
-        if (K.dt_mode == 1) dtn = K.cfl_h / (K.c0d + K.v0);
-        else dtn = K.cfl_h / (K.c0d + (double)redv[0]);
-        if (!(dtn > 1e-14)) S.status |= ST_DT;
+        S.ratio_f = prime ? 1.0f : __fdiv_rn(dtf, S.dt_f);
+        S.dt_prev = prime ? dtn : dt;
         S.dt = dtn;
-        if (prime) S.dt_prev = dtn;
+        S.dt_f = dtf;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)

@@ -89,7 +89,9 @@ def test_ghost_state_after_one_step():
     g.step()
     o.step()
     gg, go = g.ghosts(), o.ghosts()
-    assert np.array_equal(gg["xy"], go["xy"].astype(np.float32))
+    # wall ghosts are static (bit-identical); disk ghosts follow x_c(t), and t
+    # carries the ~1e-7 relative difference of the two CFL gates
+    assert np.abs(gg["xy"] - go["xy"].astype(np.float32)).max() <= 1e-9
     pmax = np.abs(go["p"]).max()
     assert np.abs(gg["p"] - go["p"]).max() <= 1e-5 * pmax
     assert np.abs(gg["rho"] / go["rho"] - 1.0).max() <= 1e-5
