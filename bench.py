@@ -153,6 +153,53 @@ def aggregate_value(world, particles, steps, total_ms):
     return world * particles * steps / (total_ms * 1e-3)
 
 
+def shard(items, rank, world):
+    """Cases of an independent sweep split across ranks (no collective needed)."""
+    return list(items)[rank::world]
+
+
+def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3):
+    """The batched coefficient sweep: n_cases cases from casegen.sweep_draws
+    (alpha, c0, cutoff, v0, width; dx = 1 mm), each run to t_end, first one
+    after another (each its own graph replays), then all together in one
+    batch.  Wall-clock time of each, max over ranks for N > 1."""
+    import torch
+    from paper_2609_05494_b300 import Batch, Case
+    specs = []
+    for p in shard(casegen.sweep_draws(casegen.DEFAULT_SEED, n_cases), rank, world):
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                                   disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
+        specs.append((p, xy.astype(np.float32)))
+    serial = [Case(p, xy, stream=stream) for p, xy in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps_serial = 0
+    for c in serial:
+        c.run(0, t_end)
+        steps_serial += int(c.scalars()["step"])
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    batched = [Case(p, xy, stream=stream) for p, xy in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Batch(batched, t_end, stream=stream) as b:
+        b.run()
+        n_batched_steps = b.steps
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    same = all(np.array_equal(a.probe_pressure(), g.probe_pressure()) for a, g in
+               zip(serial[:4], batched[:4]))
+    particles = sum(xy.shape[0] for _, xy in specs)
+    t_serial = max_over_ranks(t_serial * 1e3, dist) * 1e-3
+    t_batch = max_over_ranks(t_batch * 1e3, dist) * 1e-3
+    for c in serial + batched:
+        c.close()
+    return {"cases": n_cases, "cases_per_rank": len(specs), "t_end_s": t_end,
+            "particles": particles, "serial_s": t_serial, "batched_s": t_batch,
+            "speedup": t_serial / t_batch, "case_steps": steps_serial,
+            "batched_launch_steps": n_batched_steps, "batched_equals_serial": bool(same)}
+
+
 def cpu_baseline(seconds=15.0, Lx=0.075):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the
     workload: the first Lx of the channel at the same spacing, from t = 0."""
@@ -212,6 +259,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--dx", type=float, default=DX)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -285,8 +333,9 @@ def main():
     h2d = h_xy.nbytes + h_v.nbytes + h_r.nbytes
     d2h = probes.nbytes + sum(v.nbytes for v in final.values())
 
+    case.close()
+    sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
     if rank != 0:
-        case.close()
         if dist:
             dist.destroy_process_group()
         return 0
@@ -324,11 +373,11 @@ def main():
                          "step_frac": ALG_BYTES_PER_PARTICLE * value / world / 1e9 / pk["hbm_gbs"],
                          "peak_source": src, "bytes_per_particle": ALG_BYTES_PER_PARTICLE},
         "kernel_groups_ms": groups,
+        "batched_sweep": sweep,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
-    case.close()
     if dist:
         dist.destroy_process_group()
     return 0

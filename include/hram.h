@@ -180,6 +180,36 @@ int hr_kernel_times(hr_case *c, float *ms, int n);
 int hr_save_state(hr_case *c, const char *path);
 int hr_load_state(hr_case *c, const char *path);
 
+/* Batched runs: many cases advanced together, one launch per kernel per
+ * step for all of them (the coefficient sweep of the sensitivity study,
+ * Section 4.5: artificial viscosity, sound speed, cutoff, impact speed and
+ * channel width varied per case).  Each case keeps its own cell grid, time
+ * step, kinematics, probes and diagnostics; a case whose time reaches t_end
+ * stops advancing while the others go on.  The cases stay owned by the
+ * caller and must outlive the batch; they must all live on the current
+ * device.  Read results with the per-case calls after hr_batch_run. */
+typedef struct hr_batch hr_batch;
+
+/* Groups n_cases existing cases into a batch that runs each one up to
+ * simulated time t_end (> 0), captures the batched step graph.  cuda_stream:
+ * the stream the batch runs on.  Allocates a small device block for the
+ * case tables. */
+int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, void *cuda_stream,
+                    hr_batch **out);
+
+/* One batched step (graph replay), asynchronous. */
+int hr_batch_step(hr_batch *b);
+
+/* Steps until every case has reached t_end (or max_steps batched steps when
+ * max_steps > 0); synchronises and returns the worst case status.
+ * *steps_done = batched steps launched. */
+int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done);
+
+/* Number of cases that have reached t_end (synchronises). */
+int hr_batch_done(hr_batch *b, int *n_done);
+
+void hr_batch_destroy(hr_batch *b);
+
 /* Neighbour counts of the current state without any device allocation.
  *
  * The paper has no counterpart; this is a library service.  hr_debug_neighbors

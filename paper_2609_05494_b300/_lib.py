@@ -32,7 +32,8 @@ EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",
     "hr_probe_times", "hr_diagnostics", "hr_diag_history", "hr_get_state", "hr_set_state",
     "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors", "hr_kernel_times",
-    "hr_save_state", "hr_load_state", "hr_neighbor_counts_static", "hr_destroy",
+    "hr_save_state", "hr_load_state", "hr_neighbor_counts_static", "hr_batch_create",
+    "hr_batch_step", "hr_batch_run", "hr_batch_done", "hr_batch_destroy", "hr_destroy",
     "hr_status_str",
 )
 HR_STATIC_NEIGHBOR_MAX = 1 << 21
@@ -98,12 +99,18 @@ def lib() -> C.CDLL:
     L.hr_save_state.argtypes = [vp, C.c_char_p]
     L.hr_load_state.argtypes = [vp, C.c_char_p]
     L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
+    L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, vp, P(vp)]
+    L.hr_batch_step.argtypes = [vp]
+    L.hr_batch_run.argtypes = [vp, i64, P(i64)]
+    L.hr_batch_done.argtypes = [vp, P(C.c_int)]
+    L.hr_batch_destroy.argtypes = [vp]
+    L.hr_batch_destroy.restype = None
     L.hr_destroy.argtypes = [vp]
     L.hr_destroy.restype = None
     L.hr_status_str.argtypes = [C.c_int]
     L.hr_status_str.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("hr_destroy", "hr_status_str"):
+        if name not in ("hr_destroy", "hr_status_str", "hr_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

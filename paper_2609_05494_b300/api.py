@@ -222,3 +222,52 @@ class Case:
 
     def load(self, path: str) -> None:
         check(lib().hr_load_state(self._h, str(path).encode()), "hr_load_state")
+
+
+class Batch:
+    """Several cases advanced together up to simulated time t_end: one launch
+    per kernel per step covers every case (each keeps its own grid, dt,
+    probes and diagnostics).  The cases stay usable on their own."""
+
+    def __init__(self, cases, t_end: float, stream=None):
+        L = lib()
+        self.cases = list(cases)
+        arr = (C.c_void_p * len(self.cases))(*[c._h for c in self.cases])
+        h = C.c_void_p()
+        check(L.hr_batch_create(arr, len(self.cases), float(t_end),
+                                _stream_handle(stream) if stream is not None else
+                                self.cases[0]._stream, C.byref(h)), "hr_batch_create")
+        self._h = h
+        self.steps = 0
+
+    def step(self) -> None:
+        check(lib().hr_batch_step(self._h), "hr_batch_step")
+
+    def run(self, max_steps: int = 0) -> int:
+        n = C.c_int64(0)
+        st = check(lib().hr_batch_run(self._h, int(max_steps), C.byref(n)), "hr_batch_run")
+        self.steps += n.value
+        return st
+
+    def n_done(self) -> int:
+        n = C.c_int(0)
+        check(lib().hr_batch_done(self._h, C.byref(n)), "hr_batch_done")
+        return n.value
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h:
+            lib().hr_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

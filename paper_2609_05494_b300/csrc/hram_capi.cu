@@ -356,6 +356,21 @@ struct hr_case {
     int sticky = 0;
 };
 
+struct hr_batch {
+    std::vector<hr_case *> cases;
+    cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *mem = nullptr;
+    Consts *dK = nullptr;
+    Bufs *dB = nullptr;
+    int *d_count = nullptr;
+    BatchBlock *map[9] = {};
+    int nblocks[9] = {};
+    long long steps = 0;
+};
+
 namespace {
 
 // Derived constants (FP64 on the host, then rounded once).
@@ -1220,6 +1235,196 @@ int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
                         c->stream) != cudaSuccess)
         return HR_ECUDA;
     return device_status(c);
+}
+
+// ------------------------------------------------------------ batches
+
+namespace {
+
+enum BatchKernel { BK_KIN, BK_DRIFT, BK_TILES, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN };
+
+__global__ void k_batch_count_done(const Bufs *Bs, int n, int *out)
+{
+    int d = 0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) d += __ldcg(&Bs[c].S->done);
+    d = warp_sum(d);
+    __shared__ int red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        *out = t;
+    }
+}
+
+int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
+{
+    const Consts *K = b->dK;
+    const Bufs *B = b->dB;
+    CK(cudaEventRecord(b->fork, s));
+    CK(cudaStreamWaitEvent(side, b->fork, 0));
+    kb_kinematics<<<b->nblocks[BK_KIN], 128, 0, side>>>(K, B, b->map[BK_KIN]);
+    CK(cudaEventRecord(b->join, side));
+    kb_drift_key<<<b->nblocks[BK_DRIFT], 256, 0, s>>>(K, B, b->map[BK_DRIFT]);
+    kb_scan_tiles<<<b->nblocks[BK_TILES], kScanThreads, 0, s>>>(K, B, b->map[BK_TILES]);
+    kb_scan_apply<<<b->nblocks[BK_APPLY], kScanThreads, 0, s>>>(K, B, b->map[BK_APPLY]);
+    kb_slot<<<b->nblocks[BK_SLOT], 256, 0, s>>>(K, B, b->map[BK_SLOT]);
+    kb_rank_scatter<<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
+    CK(cudaStreamWaitEvent(s, b->join, 0));
+    kb_ghost<<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
+    kb_pass<<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+    kb_finalize<<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
+    CK(cudaGetLastError());
+    return HR_OK;
+}
+
+}  // namespace
+
+int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, void *cuda_stream,
+                    hr_batch **out)
+{
+    if (!out || !cases || n_cases <= 0) return HR_EINVAL;
+    *out = nullptr;
+    hr_batch *b = new hr_batch();
+    auto fail = [&](int code) {
+        hr_batch_destroy(b);
+        return code;
+    };
+    for (int k = 0; k < n_cases; ++k) {
+        if (!cases[k] || cases[k]->sticky < 0) return fail(HR_EINVAL);
+        b->cases.push_back(cases[k]);
+    }
+    b->stream = (cudaStream_t)cuda_stream;
+    // per-kernel block maps: (case, local block, blocks of that case)
+    std::vector<BatchBlock> maps[9];
+    for (int k = 0; k < n_cases; ++k) {
+        const hr_case *c = cases[k];
+        const int fin = std::max(4, c->K.n_probes);
+        const int nb[9] = {1, c->drift_blocks, c->n_tiles, c->n_tiles, c->drift_blocks,
+                           c->drift_blocks, c->ghost_blocks, c->pass_blocks, fin};
+        for (int q = 0; q < 9; ++q)
+            for (int j = 0; j < nb[q]; ++j) maps[q].push_back(BatchBlock{k, j, nb[q], 0});
+    }
+    size_t bytes = align256(sizeof(Consts) * n_cases) + align256(sizeof(Bufs) * n_cases) + 256;
+    size_t off[9];
+    for (int q = 0; q < 9; ++q) {
+        off[q] = bytes;
+        bytes += align256(maps[q].size() * sizeof(BatchBlock));
+    }
+    if (cudaMalloc(&b->mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b->mem = nullptr;
+        return fail(HR_ENOMEM);
+    }
+    b->dK = at<Consts>(b->mem, 0);
+    b->dB = at<Bufs>(b->mem, align256(sizeof(Consts) * n_cases));
+    b->d_count = at<int>(b->mem, align256(sizeof(Consts) * n_cases) + align256(sizeof(Bufs) * n_cases));
+    std::vector<Consts> hk(n_cases);
+    std::vector<Bufs> hb(n_cases);
+    for (int k = 0; k < n_cases; ++k) {
+        hk[k] = cases[k]->K;
+        hb[k] = cases[k]->B;
+    }
+    if (cudaMemcpy(b->dK, hk.data(), sizeof(Consts) * n_cases, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->dB, hb.data(), sizeof(Bufs) * n_cases, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(HR_ECUDA);
+    for (int q = 0; q < 9; ++q) {
+        b->map[q] = at<BatchBlock>(b->mem, off[q]);
+        b->nblocks[q] = (int)maps[q].size();
+        if (cudaMemcpy(b->map[q], maps[q].data(), maps[q].size() * sizeof(BatchBlock),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(HR_ECUDA);
+    }
+    // every case stops at t_end
+    for (int k = 0; k < n_cases; ++k) {
+        hr_case *c = cases[k];
+        if (device_status(c) < 0) return fail(c->sticky);
+        Scalars S;
+        if (cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(HR_ECUDA);
+        S.t_end = t_end;
+        S.done = (t_end > 0.0 && S.t >= t_end) ? 1 : 0;
+        if (cudaMemcpy(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(HR_ECUDA);
+    }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HR_ECUDA);
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(HR_ECUDA);
+    const int rc = batch_launch(b, b->cap, b->cap2);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (rc != HR_OK || e != cudaSuccess) return fail(HR_ECUDA);
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(HR_ECUDA);
+    *out = b;
+    return HR_OK;
+}
+
+int hr_batch_step(hr_batch *b)
+{
+    if (!b || !b->exec) return HR_EINVAL;
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return HR_ECUDA;
+    b->steps++;
+    return HR_OK;
+}
+
+int hr_batch_done(hr_batch *b, int *n_done)
+{
+    if (!b || !n_done) return HR_EINVAL;
+    k_batch_count_done<<<1, 256, 0, b->stream>>>(b->dB, (int)b->cases.size(), b->d_count);
+    if (cudaMemcpyAsync(n_done, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return HR_ECUDA;
+    return HR_OK;
+}
+
+int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done)
+{
+    if (!b) return HR_EINVAL;
+    const int n = (int)b->cases.size();
+    int64_t done_steps = 0;
+    int rc = HR_OK;
+    for (;;) {
+        int nd = 0;
+        if ((rc = hr_batch_done(b, &nd)) != HR_OK) break;
+        if (nd >= n || (max_steps > 0 && done_steps >= max_steps)) break;
+        int64_t k = 64;
+        if (max_steps > 0) k = std::min<int64_t>(k, max_steps - done_steps);
+        for (int64_t q = 0; q < k; ++q)
+            if ((rc = hr_batch_step(b)) != HR_OK) break;
+        if (rc != HR_OK) break;
+        done_steps += k;
+    }
+    if (steps_done) *steps_done = done_steps;
+    if (rc != HR_OK) return rc;
+    int worst = HR_OK;
+    for (hr_case *c : b->cases) {
+        const int st = device_status(c);
+        if (st < 0) return st;
+        worst |= st;
+    }
+    return worst;
+}
+
+void hr_batch_destroy(hr_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap2) cudaStreamDestroy(b->cap2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
 }
 
 void hr_destroy(hr_case *c)

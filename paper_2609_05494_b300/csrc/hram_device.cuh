@@ -82,7 +82,8 @@ struct Scalars {
     double probe_imp[kMaxProbes];
     long long hist_n;
     int status;
-    int pad;
+    int done;          // 1 once t >= t_end (batched runs)
+    double t_end;      // stop time of a batched run (<= 0: none)
     // single-precision copies for the per-particle kernels (the FP64 pipe of
     // the B300 is far too slow to convert doubles in every thread)
     float dt_f, ratio_f, xc_f, yc_f, vproj_f, aproj_f;
@@ -341,9 +342,9 @@ __device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, flo
 // Opening kick, XSPH drift, wall enforcement and cell key (the predicted
 // density is formed in k_rank_scatter from the same state).  prime = 1
 // evaluates the current state without advancing (dt = 0).
-__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
+__device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
     const float dt = prime ? 0.0f : B.S->dt_f;
     float2 r = B.s_pos[i];
@@ -416,7 +417,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int *
 // a1: advances t by dt (unless priming), evaluates the projectile
 // kinematics at t^{n+1} in FP64 and places the disk ghost ring there.  One
 // block; in the step graph it runs on a branch beside the drift and the sort.
-__global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
+__device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     __shared__ double kin[2];
     if (threadIdx.x == 0) {
@@ -443,11 +444,11 @@ __global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
 }
 
 // Tile sums of the cell counts (ncell + 1 entries), one block per tile.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
+__device__ __forceinline__ void b_scan_tiles(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int red[kScanThreads / 32];
     const int n = K.ncell + 1;
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const int base = bx * kScanTile + threadIdx.x * kScanItems;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) s += (base + k < n) ? B.cell_count[base + k] : 0;
@@ -457,18 +458,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
     if (threadIdx.x < 32) {
         int t = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
         t = warp_sum(t);
-        if (threadIdx.x == 0) B.tile_sum[blockIdx.x] = t;
+        if (threadIdx.x == 0) B.tile_sum[bx] = t;
     }
 }
 
 // Cell starts: each block adds up the sums of the tiles before it, then an
 // exclusive scan of its own tile; the counts are reset for the next step.
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
+__device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int wsum[kScanThreads / 32];
     __shared__ int offset;
     int o = 0;
-    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) o += B.tile_sum[t];
+    for (int t = threadIdx.x; t < (int)bx; t += blockDim.x) o += B.tile_sum[t];
     o = warp_sum(o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = o;
     __syncthreads();
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
     }
     __syncthreads();
     const int n = K.ncell + 1;
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const int base = bx * kScanTile + threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
@@ -500,9 +501,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
 }
 
-__global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
+__device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
     const int dst = B.cell_start[B.u_key[i]] + B.u_slot[i];
     B.perm_tmp[dst] = B.u_id[i];
@@ -512,9 +513,9 @@ __global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
 // Then the reorder into the SoA arrays of this step, with the predicted
 // density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n - D^{n-1})))
 // and its Tait pressure.
-__global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prime)
+__device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
     const int key = B.u_key[i];
     const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
@@ -546,11 +547,11 @@ __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prim
 //   rho_g = rho0 (1 + p_g / (rho0 c0^2)),  v_g = 2 v_w - S_v / S_W.
 // One warp per ghost: the lanes split the stencil's candidates, then the six
 // Shepard sums are reduced across the warp.
-__global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
+__device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ float red[kGhostWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = blockIdx.x * kGhostWarps + w;
+    const int g = bx * kGhostWarps + w;
     float vabs = 0.0f;
     if (g < K.nw + K.ng) {
         const bool disk = g >= K.nw;
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
     if (threadIdx.x == 0) {
         float v = 0.0f;
         for (int k = 0; k < kGhostWarps; ++k) v = fmaxf(v, red[k]);
-        B.ghost_vmax[blockIdx.x] = v;
+        B.ghost_vmax[bx] = v;
     }
 }
 
@@ -697,11 +698,11 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
 // density and the closing half kick.  Block partials of the ghost forces,
 // the dissipation rate and max |v| are reduced in FP32 per warp and in FP64
 // per block.
-__global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
+__device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     __shared__ float red[kPassThreads / 32][5];
     __shared__ int redn[kPassThreads / 32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float dt = prime ? 0.0f : B.S->dt_f;
     float fdx = 0.0f, fdy = 0.0f, fw = 0.0f, diss = 0.0f, vmax = 0.0f;
@@ -854,9 +855,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int pri
             v = fmaxf(v, red[k][4]);
             np += redn[k];
         }
-        B.part.f[blockIdx.x] = make_float4(a0, a1, a2, a3);
-        B.part.vmax[blockIdx.x] = v;
-        B.part.npen[blockIdx.x] = np;
+        B.part.f[bx] = make_float4(a0, a1, a2, a3);
+        B.part.vmax[bx] = v;
+        B.part.npen[bx] = np;
     }
 }
 
@@ -907,7 +908,7 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 // Block q < n_probes first samples wall probe q (a7) into probe_now[q].  The
 // sums are compensated FP32 (two-float) in a fixed tree order, converted to
 // FP64 once at the end.
-__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
+__device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     constexpr int NW = kFinalizeThreads / 32;
     __shared__ F2 redd[4][NW];
@@ -920,10 +921,10 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
     __shared__ float totv;
     __shared__ int totn;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nb = gridDim.x;
-    if (!prime && (int)blockIdx.x < K.n_probes && w == 0) {
-        const float pv = probe_value(K, B, K.probe_x[blockIdx.x], K.probe_y[blockIdx.x]);
-        if (lane == 0) B.probe_now[blockIdx.x] = pv;
+    const int nb = nbx;
+    if (!prime && (int)bx < K.n_probes && w == 0) {
+        const float pv = probe_value(K, B, K.probe_x[bx], K.probe_y[bx]);
+        if (lane == 0) B.probe_now[bx] = pv;
     }
     // reduce one (value per thread) set of four sums, max and count over the
     // block; the results land in tot[] (lane 0 of warp 0 writes them)
@@ -968,7 +969,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
         F2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
         float vmax = 0.0f;
         int npen = 0;
-        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K.n_pass_blocks;
+        for (int b = bx * blockDim.x + threadIdx.x; b < K.n_pass_blocks;
              b += nb * blockDim.x) {
             const float4 f = B.part.f[b];
             a0 = f2_add(a0, F2{f.x, 0.f});
@@ -978,18 +979,18 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
             vmax = fmaxf(vmax, B.part.vmax[b]);
             npen += B.part.npen[b];
         }
-        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
+        for (int b = bx * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
              b += nb * blockDim.x)
             vmax = fmaxf(vmax, B.ghost_vmax[b]);
         block_reduce(a0, a1, a2, a3, vmax, npen);
     }
     if (threadIdx.x == 0) {
         for (int k = 0; k < 4; ++k) {
-            B.fin_part[blockIdx.x * 8 + 2 * k] = tot[k].hi;
-            B.fin_part[blockIdx.x * 8 + 2 * k + 1] = tot[k].lo;
+            B.fin_part[bx * 8 + 2 * k] = tot[k].hi;
+            B.fin_part[bx * 8 + 2 * k + 1] = tot[k].lo;
         }
-        B.fin_vmax[blockIdx.x] = totv;
-        B.fin_npen[blockIdx.x] = totn;
+        B.fin_vmax[bx] = totv;
+        B.fin_npen[bx] = totn;
         __threadfence();
         is_last = atomicAdd(B.fin_ticket, 1) == nb - 1;
     }
@@ -1056,6 +1057,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
             S.step = k + 1;
         }
         S.ratio_f = prime ? 1.0f : __fdiv_rn(dtf, S.dt_f);
+        S.done = (S.t_end > 0.0 && S.t >= S.t_end) ? 1 : 0;
         S.dt_prev = prime ? dtn : dt;
         S.dt = dtn;
         S.dt_f = dtf;
@@ -1063,6 +1065,159 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B,
     __syncthreads();
     for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
         reinterpret_cast<double *>(B.S)[k] = reinterpret_cast<const double *>(&S)[k];
+}
+
+
+// ------------------------------------------------ kernels (one case)
+
+__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
+{
+    b_drift_key(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+__global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
+{
+    b_kinematics(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
+{
+    b_scan_tiles(K, B, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
+{
+    b_scan_apply(K, B, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
+{
+    b_slot(K, B, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prime)
+{
+    b_rank_scatter(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+__global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
+{
+    b_ghost(K, B, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
+{
+    b_pass(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
+{
+    b_finalize(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+// --------------------------------------------- kernels (a batch of cases)
+
+// Block b of a batched launch works for case map[b].x as its local block
+// map[b].y of map[b].w; the case's constants and buffers are copied to
+// shared memory first.  Cases whose run is done (t >= t_end) skip the step.
+struct BatchBlock {
+    int c, local, nlocal, pad;
+};
+
+__device__ __forceinline__ bool batch_enter(const Consts *Ks, const Bufs *Bs, const BatchBlock *map,
+                                            Consts &K, Bufs &B, BatchBlock &m)
+{
+    m = map[blockIdx.x];
+    static_assert(sizeof(Consts) % 4 == 0 && sizeof(Bufs) % 8 == 0, "copied as words");
+    const int *ks = reinterpret_cast<const int *>(Ks + m.c);
+    for (int k = threadIdx.x; k < (int)(sizeof(Consts) / 4); k += blockDim.x)
+        reinterpret_cast<int *>(&K)[k] = ks[k];
+    const unsigned long long *bs = reinterpret_cast<const unsigned long long *>(Bs + m.c);
+    for (int k = threadIdx.x; k < (int)(sizeof(Bufs) / 8); k += blockDim.x)
+        reinterpret_cast<unsigned long long *>(&B)[k] = bs[k];
+    __syncthreads();
+    return !__ldcg(&B.S->done);
+}
+
+__global__ void __launch_bounds__(256) kb_drift_key(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_drift_key(K, B, m.local, m.nlocal, 0);
+}
+
+__global__ void __launch_bounds__(128) kb_kinematics(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_kinematics(K, B, m.local, m.nlocal, 0);
+}
+
+__global__ void __launch_bounds__(kScanThreads) kb_scan_tiles(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_scan_tiles(K, B, m.local, m.nlocal);
+}
+
+__global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_scan_apply(K, B, m.local, m.nlocal);
+}
+
+__global__ void __launch_bounds__(256) kb_slot(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_slot(K, B, m.local, m.nlocal);
+}
+
+__global__ void __launch_bounds__(256) kb_rank_scatter(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_rank_scatter(K, B, m.local, m.nlocal, 0);
+}
+
+__global__ void __launch_bounds__(kGhostWarps * 32) kb_ghost(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_ghost(K, B, m.local, m.nlocal);
+}
+
+__global__ void __launch_bounds__(kPassThreads) kb_pass(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_pass(K, B, m.local, m.nlocal, 0);
+}
+
+__global__ void __launch_bounds__(kFinalizeThreads) kb_finalize(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_finalize(K, B, m.local, m.nlocal, 0);
 }
 
 }  // namespace hr

@@ -1,0 +1,78 @@
+"""Batched runs (the coefficient sweep): every case advanced inside a batch
+ends bit-for-bit where it ends when run alone, and a batched case matches
+the FP64 oracle on its probe window."""
+import numpy as np
+import pytest
+
+import casegen
+import oracle
+from helpers import as64, impact_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2609_05494_b300 import Batch, Case  # noqa: E402
+
+
+def sweep_cases(n, dx=2e-3):
+    out = []
+    for p in casegen.sweep_draws(casegen.DEFAULT_SEED, n):
+        p = dict(p)
+        p["dx"] = dx          # coarse copies of the sweep cases keep the test short
+        p, xy = impact_case(p)
+        out.append((p, xy))
+    return out
+
+
+def test_batch_equals_cases_run_alone():
+    t_end = 12e-6
+    specs = sweep_cases(6)
+    alone, batched = [], []
+    for p, xy in specs:
+        a = Case(p, xy)
+        a.run(0, t_end)
+        alone.append(a)
+        batched.append(Case(p, xy))
+    with Batch(batched, t_end) as b:
+        b.run()
+        assert b.n_done() == len(batched)
+    for a, g in zip(alone, batched):
+        sa, sg = a.get_state(), g.get_state()
+        for k in sa:
+            assert np.array_equal(sa[k], sg[k]), k
+        assert np.array_equal(a.probe_pressure(), g.probe_pressure())
+        assert a.scalars()["step"] == g.scalars()["step"]
+        assert g.scalars()["t"] >= t_end
+
+
+def test_batched_case_matches_oracle():
+    (p, xy), = sweep_cases(1)
+    g = Case(p, xy)
+    other = [Case(q, x) for q, x in sweep_cases(3)[1:]]
+    with Batch([g] + other, 10e-6) as b:
+        b.run()
+    n = int(g.scalars()["step"])
+    o = oracle.OracleCase(p, as64(xy))
+    o.run(n)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    for k in range(po.shape[1]):
+        if np.abs(po[:, k]).max() > 1e6:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3
+    fo, sg = o.fluid(), g.get_state()
+    assert np.abs(sg["rho"] / fo["rho"] - 1).max() <= 1e-4
+
+
+def test_batch_stops_each_case_at_its_end_time():
+    specs = sweep_cases(4)
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 8e-6) as b:
+        b.run(max_steps=3)
+        assert b.n_done() == 0
+        b.run()
+        assert b.n_done() == 4
+    for c in cs:
+        t = c.probe_times()
+        assert t[-1] >= 8e-6 > t[-2]
