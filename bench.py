@@ -164,12 +164,16 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     after another (each its own graph replays), then all together in one
     batch.  Wall-clock time of each, max over ranks for N > 1."""
     import torch
-    from paper_2609_05494_b300 import Batch, Case
+    from paper_2609_05494_b300 import Batch, Case, autotune
     specs = []
     for p in shard(casegen.sweep_draws(casegen.DEFAULT_SEED, n_cases), rank, world):
         xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
                                    disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
         specs.append((p, xy.astype(np.float32)))
+    # per-case cell grids and the batch's block schedule, picked by timing
+    t0 = time.perf_counter()
+    specs, schedule, tune_report = autotune.tune_sweep(specs, stream=stream)
+    t_tune = time.perf_counter() - t0
     serial = [Case(p, xy, stream=stream) for p, xy in specs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -182,7 +186,7 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     batched = [Case(p, xy, stream=stream) for p, xy in specs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with Batch(batched, t_end, stream=stream) as b:
+    with Batch(batched, t_end, stream=stream, schedule=schedule) as b:
         b.run()
         n_batched_steps = b.steps
     torch.cuda.synchronize()
@@ -197,7 +201,8 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     return {"cases": n_cases, "cases_per_rank": len(specs), "t_end_s": t_end,
             "particles": particles, "serial_s": t_serial, "batched_s": t_batch,
             "speedup": t_serial / t_batch, "case_steps": steps_serial,
-            "batched_launch_steps": n_batched_steps, "batched_equals_serial": bool(same)}
+            "batched_launch_steps": n_batched_steps, "batched_equals_serial": bool(same),
+            "autotune": tune_report, "autotune_s": t_tune}
 
 
 def cpu_baseline(seconds=15.0, Lx=0.075):

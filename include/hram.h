@@ -191,11 +191,13 @@ int hr_load_state(hr_case *c, const char *path);
 typedef struct hr_batch hr_batch;
 
 /* Groups n_cases existing cases into a batch that runs each one up to
- * simulated time t_end (> 0), captures the batched step graph.  cuda_stream:
- * the stream the batch runs on.  Allocates a small device block for the
- * case tables. */
-int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, void *cuda_stream,
-                    hr_batch **out);
+ * simulated time t_end (> 0), captures the batched step graph.  schedule
+ * orders the blocks of each batched launch: 0 case after case, 1 round robin
+ * over the cases, 2 case after case from the largest down (results do not
+ * depend on it; the autotuner picks the fastest).  cuda_stream: the stream
+ * the batch runs on.  Allocates a small device block for the case tables. */
+int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedule,
+                    void *cuda_stream, hr_batch **out);
 
 /* One batched step (graph replay), asynchronous. */
 int hr_batch_step(hr_batch *b);

@@ -99,7 +99,7 @@ def lib() -> C.CDLL:
     L.hr_save_state.argtypes = [vp, C.c_char_p]
     L.hr_load_state.argtypes = [vp, C.c_char_p]
     L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
-    L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, vp, P(vp)]
+    L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, C.c_int, vp, P(vp)]
     L.hr_batch_step.argtypes = [vp]
     L.hr_batch_run.argtypes = [vp, i64, P(i64)]
     L.hr_batch_done.argtypes = [vp, P(C.c_int)]

@@ -229,12 +229,15 @@ class Batch:
     per kernel per step covers every case (each keeps its own grid, dt,
     probes and diagnostics).  The cases stay usable on their own."""
 
-    def __init__(self, cases, t_end: float, stream=None):
+    SCHEDULES = ("case-major", "round-robin", "largest-first")
+
+    def __init__(self, cases, t_end: float, stream=None, schedule: int = 0):
         L = lib()
         self.cases = list(cases)
+        self.schedule = int(schedule)
         arr = (C.c_void_p * len(self.cases))(*[c._h for c in self.cases])
         h = C.c_void_p()
-        check(L.hr_batch_create(arr, len(self.cases), float(t_end),
+        check(L.hr_batch_create(arr, len(self.cases), float(t_end), self.schedule,
                                 _stream_handle(stream) if stream is not None else
                                 self.cases[0]._stream, C.byref(h)), "hr_batch_create")
         self._h = h

@@ -1281,10 +1281,10 @@ int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
 
 }  // namespace
 
-int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, void *cuda_stream,
-                    hr_batch **out)
+int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedule,
+                    void *cuda_stream, hr_batch **out)
 {
-    if (!out || !cases || n_cases <= 0) return HR_EINVAL;
+    if (!out || !cases || n_cases <= 0 || schedule < 0 || schedule > 2) return HR_EINVAL;
     *out = nullptr;
     hr_batch *b = new hr_batch();
     auto fail = [&](int code) {
@@ -1296,15 +1296,34 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, void *cuda
         b->cases.push_back(cases[k]);
     }
     b->stream = (cudaStream_t)cuda_stream;
-    // per-kernel block maps: (case, local block, blocks of that case)
+    // per-kernel block maps: (case, local block, blocks of that case), in the
+    // order of the schedule: 0 case after case, 1 round robin over the cases,
+    // 2 case after case from the largest case down
     std::vector<BatchBlock> maps[9];
-    for (int k = 0; k < n_cases; ++k) {
+    std::vector<int> order(n_cases);
+    std::iota(order.begin(), order.end(), 0);
+    if (schedule == 2)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int c) { return cases[a]->nf > cases[c]->nf; });
+    auto nblk = [&](int k, int q) {
         const hr_case *c = cases[k];
         const int fin = std::max(4, c->K.n_probes);
         const int nb[9] = {1, c->drift_blocks, c->n_tiles, c->n_tiles, c->drift_blocks,
                            c->drift_blocks, c->ghost_blocks, c->pass_blocks, fin};
-        for (int q = 0; q < 9; ++q)
-            for (int j = 0; j < nb[q]; ++j) maps[q].push_back(BatchBlock{k, j, nb[q], 0});
+        return nb[q];
+    };
+    for (int q = 0; q < 9; ++q) {
+        if (schedule == 1) {
+            int most = 0;
+            for (int k = 0; k < n_cases; ++k) most = std::max(most, nblk(k, q));
+            for (int j = 0; j < most; ++j)
+                for (int k = 0; k < n_cases; ++k)
+                    if (j < nblk(k, q)) maps[q].push_back(BatchBlock{k, j, nblk(k, q), 0});
+        } else {
+            for (int k : order)
+                for (int j = 0; j < nblk(k, q); ++j)
+                    maps[q].push_back(BatchBlock{k, j, nblk(k, q), 0});
+        }
     }
     size_t bytes = align256(sizeof(Consts) * n_cases) + align256(sizeof(Bufs) * n_cases) + 256;
     size_t off[9];

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover - CPU machine
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_2609_05494_b300 import Batch, Case  # noqa: E402
+from paper_2609_05494_b300 import Batch, Case, autotune  # noqa: E402
 
 
 def sweep_cases(n, dx=2e-3):
@@ -76,3 +76,35 @@ def test_batch_stops_each_case_at_its_end_time():
     for c in cs:
         t = c.probe_times()
         assert t[-1] >= 8e-6 > t[-2]
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+def test_schedules_give_identical_results(schedule):
+    specs = sweep_cases(5)
+    ref = [Case(p, xy) for p, xy in specs]
+    with Batch(ref, 6e-6, schedule=0) as b:
+        b.run()
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 6e-6, schedule=schedule) as b:
+        b.run()
+    for a, g in zip(ref, cs):
+        assert np.array_equal(a.get_state()["rho"], g.get_state()["rho"])
+
+
+def test_autotuned_sweep_runs_and_matches_alone():
+    specs = sweep_cases(4)
+    tuned, schedule, report = autotune.tune_sweep(specs, classes=2)
+    assert 0 <= schedule < len(Batch.SCHEDULES)
+    assert all(q["cell_factor"] in autotune.CELL_FACTORS for q, _ in tuned)
+    assert report["schedule"] == Batch.SCHEDULES[schedule]
+    alone = []
+    for p, xy in tuned:
+        a = Case(p, xy)
+        a.run(0, 6e-6)
+        alone.append(a)
+    cs = [Case(p, xy) for p, xy in tuned]
+    with Batch(cs, 6e-6, schedule=schedule) as b:
+        b.run()
+    for a, g in zip(alone, cs):
+        assert np.array_equal(a.probe_pressure(), g.probe_pressure())
+        assert np.array_equal(a.get_state()["xy"], g.get_state()["xy"])
