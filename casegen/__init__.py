@@ -117,7 +117,8 @@ def base_params() -> dict:
     paper's alpha is 0.03; the workloads use 0.02), XSPH epsilon 0.02, water
     dynamic viscosity 8.9e-4 Pa s, gravity (0, -9.81) m/s^2, CFL 0.2, h = 1.3 dx,
     3 ghost layers per side wall, a 5 mm disk entering at the mid-height of the
-    x = 0 face with a 5 us ramp and exponential deceleration tau = 200 us.
+    x = 0 face with a 5 us ramp and exponential deceleration tau = 200 us;
+    disk density 7850 kg/m^3 (steel) for the two-way coupled motion.
     """
     return dict(
         dx=2e-3, h_over_dx=1.3, Lx=0.150, W=0.150,
@@ -127,7 +128,7 @@ def base_params() -> dict:
         rho0=1000.0, c0=1480.0, gamma=7.0, p_cav=-1e5, alpha=0.02, eta2=0.01,
         eps_xsph=0.02, mu_lam=8.9e-4, gx=0.0, gy=-9.81, cfl=0.2, dt_mode=0,
         rho_lo=0.5, rho_hi=1.5, box_pad=-1.0, cell_factor=1.001,
-        seed=DEFAULT_SEED, jitter=0.01,
+        seed=DEFAULT_SEED, jitter=0.01, disk_density=7850.0,
         probes=[],
     )
 

@@ -65,7 +65,9 @@ extern "C" {
  *  Ng              disk ghost count (Section 2.6.1); 0 = no disk
  *  motion          0 ramp x exponential decay, 1 ramp + quadratic drag
  *                  (Section 2.7, drag_M, drag_Cd, drag_R), 2 constant
- *                  acceleration a_const from rest
+ *                  acceleration a_const from rest, 3 ramp then two-way
+ *                  coupling: M' dv/dt = -(force of the disk ghosts on the
+ *                  fluid), M' = disk_density pi R^2 per unit depth
  *  rho0, c0, gamma Tait equation of state; p_cav cavitation cutoff
  *  alpha, eta2     artificial viscosity (eq. artificial-viscosity)
  *  eps_xsph        XSPH blending (eq. xsph); mu_lam dynamic viscosity
@@ -90,6 +92,7 @@ typedef struct hr_params {
     double probe_xy[2 * HR_MAX_PROBES];
     int64_t probe_capacity;
     int32_t diag_every, flags;
+    double disk_density;
 } hr_params;
 
 /* FP64 diagnostics (Section 2.10 and eq. energy-audit of Section 4.7). */

@@ -51,6 +51,7 @@ class OracleParams(C.Structure):
         ("rho_lo", C.c_double), ("rho_hi", C.c_double), ("box_pad", C.c_double),
         ("probe_xy", C.c_double * (2 * N_PROBE_MAX)),
         ("mutation", C.c_int32), ("brute", C.c_int32),
+        ("disk_density", C.c_double),
     ]
 
 

@@ -57,6 +57,7 @@ typedef struct {
     double rho_lo, rho_hi, box_pad;
     double probe_xy[32];
     int32_t mutation, brute;
+    double disk_density;
 } orc_params;
 
 enum { KIND_FLUID = 0, KIND_SIDE = 1, KIND_END = 2, KIND_DISK = 3 };
@@ -202,10 +203,12 @@ static double tait_energy(const orc_case *c, double rho)
  *  motion 1: the paper's ramp followed by its quadratic drag law,
  *           M dv/dt = -1/2 Cd rho_f pi R^2 v^2, solved in closed form.
  *  motion 2: constant acceleration from rest (verification case).
+ *  motion 3: the ramp (no decay); afterwards the disk is driven by the fluid
+ *           force (two-way coupling, advanced in orc_step, not here).
  * Returns centre x, velocity and acceleration, all in closed form. */
 void orc_kinematics(const orc_params *P, double t, double *xo, double *vo, double *ao)
 {
-    double v0 = P->v0, tr = P->t_ramp, tau = P->tau, x = P->x_c0, v, a;
+    double v0 = P->v0, tr = P->t_ramp, tau = P->motion == 3 ? 0.0 : P->tau, x = P->x_c0, v, a;
     if (P->motion == 2) {
         v = P->a_const * t;
         a = P->a_const;
@@ -424,6 +427,26 @@ static void build_neighbours(orc_case *c)
 static void kinematics_now(orc_case *c)
 {
     orc_kinematics(&c->P, c->t, &c->xc, &c->vproj, &c->aproj);
+    c->yc = c->P.y_c0;
+}
+
+/* Two-way coupling (motion 3; the extension the paper names in its
+ * Conclusions): after the ramp the disk is no longer prescribed but obeys
+ * M' dv/dt = -F, F the force of the disk ghosts on the fluid from the last
+ * interaction sums, M' = rho_disk pi R^2 its mass per unit depth.  Advanced
+ * with the step's dt by symplectic Euler in FP64:
+ *   a = -F_x / M',  v += dt a,  x += dt v.
+ * During the ramp (t <= t_ramp) the ramp's closed form is used. */
+static void kinematics_advance(orc_case *c, double dt)
+{
+    if (c->P.motion != 3 || (c->P.t_ramp > 0.0 && c->t <= c->P.t_ramp)) {
+        kinematics_now(c);
+        return;
+    }
+    double M = c->P.disk_density * M_PI * c->P.R_disk * c->P.R_disk;
+    c->aproj = -c->Fdx / M;
+    c->vproj += dt * c->aproj;
+    c->xc += dt * c->vproj;
     c->yc = c->P.y_c0;
 }
 
@@ -796,7 +819,7 @@ void orc_step(orc_case *c)
     }
     /* (3) time and projectile kinematics at t^{n+1} */
     c->t += dt;
-    kinematics_now(c);
+    kinematics_advance(c, dt);
     place_disk(c);
     /* (4) predicted density and its pressure, then the ghosts */
     for (int64_t i = 0; i < c->nf; ++i) {

@@ -57,6 +57,7 @@ class HrParams(C.Structure):
         ("probe_xy", C.c_double * (2 * MAX_PROBES)),
         ("probe_capacity", C.c_int64),
         ("diag_every", C.c_int32), ("flags", C.c_int32),
+        ("disk_density", C.c_double),
     ]
 
 

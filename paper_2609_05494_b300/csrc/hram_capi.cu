@@ -320,7 +320,8 @@ int validate(const hr_params *P, long long nf)
     if (P->n_probes < 0 || P->n_probes > HR_MAX_PROBES) return HR_EINVAL;
     if (!(P->rho0 > 0) || !(P->c0 > 0) || !(P->gamma > 1) || !(P->cfl > 0)) return HR_EINVAL;
     if (!(P->rho_lo > 0) || !(P->rho_hi > P->rho_lo)) return HR_EINVAL;
-    if (P->motion < 0 || P->motion > 2 || P->dt_mode < 0 || P->dt_mode > 1) return HR_EINVAL;
+    if (P->motion < 0 || P->motion > 3 || P->dt_mode < 0 || P->dt_mode > 1) return HR_EINVAL;
+    if (P->motion == 3 && !(P->disk_density > 0)) return HR_EINVAL;
     if (P->motion == 1 && !(P->drag_M > 0)) return HR_EINVAL;
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
     if (P->cell_factor < 1.0) return HR_EINVAL;
@@ -448,6 +449,7 @@ void make_consts(hr_case *c)
     K.cfl_h = P.cfl * h;
     K.cfl_h_f = (float)K.cfl_h;
     K.dt_fixed = K.cfl_h / (P.c0 + P.v0);
+    K.disk_mass = P.disk_density * M_PI * P.R_disk * P.R_disk;
     K.c0d = P.c0;
     K.v0 = P.v0;
     K.tau = P.tau;

@@ -62,7 +62,7 @@ struct Consts {
     int nf, nw, ng;
     float m_wall, m_disk, wall_over_m, disk_over_m, m_over_rho0, m2Wc, R, disk_reach2, R2;
     // CFL and kinematics (FP64)
-    double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k, dt_fixed;
+    double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k, dt_fixed, disk_mass;
     float cfl_h_f;
     int dt_mode, motion;
     // probes
@@ -262,10 +262,11 @@ __device__ __forceinline__ F2 f2_warp_sum(F2 v)
 // Projectile kinematics in closed form (FP64).  Section 2.6.3 ramp,
 // exponential decay with time constant tau (motion 0), the paper's quadratic
 // drag law after the ramp (motion 1, Section 2.7), constant acceleration
-// (motion 2).
+// (motion 2).  Motion 3 uses the ramp here; after it the disk is advanced
+// by the fluid force in b_kinematics (two-way coupling).
 __device__ inline void kinematics(const Consts &K, double t, double *xo, double *vo, double *ao)
 {
-    const double v0 = K.v0, tr = K.t_ramp, tau = K.tau;
+    const double v0 = K.v0, tr = K.t_ramp, tau = K.motion == 3 ? 0.0 : K.tau;
     double x = K.x_c0, v, a;
     if (K.motion == 2) {
         v = K.a_const * t;
@@ -422,9 +423,19 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
     __shared__ double kin[2];
     if (threadIdx.x == 0) {
         Scalars *S = B.S;
-        if (!prime) S->t += S->dt;
+        const double dt = prime ? 0.0 : S->dt;
+        S->t += dt;
         double x, v, a;
-        kinematics(K, S->t, &x, &v, &a);
+        if (K.motion == 3 && !prime && !(K.t_ramp > 0.0 && S->t <= K.t_ramp)) {
+            // two-way coupling (the extension named in the paper's
+            // Conclusions): M' dv/dt = -F_x, F the disk ghosts' force on the
+            // fluid from the last interaction pass; symplectic Euler in FP64
+            a = -S->Fdx / K.disk_mass;
+            v = S->vproj + dt * a;
+            x = S->xc + dt * v;
+        } else {
+            kinematics(K, S->t, &x, &v, &a);
+        }
         S->xc = x;
         S->yc = K.y_c0;
         S->vproj = v;

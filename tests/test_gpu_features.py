@@ -195,3 +195,16 @@ def test_full_size_one_step_against_oracle():
     assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     assert g.scalars()["dt"] == pytest.approx(o.scalars()["dt"], rel=1e-6)
+
+
+def test_two_way_coupling_matches_oracle():
+    p, xy = impact_case(motion=3, t_ramp=2e-6, v0=300.0)
+    g, o = both(p, xy)
+    g.run(80)
+    o.run(80)
+    sg, so = g.scalars(), o.scalars()
+    assert sg["vproj"] < 300.0
+    for k in ("xc", "vproj"):
+        assert sg[k] == pytest.approx(so[k], rel=1e-5), k
+    assert sg["aproj"] == pytest.approx(so["aproj"], rel=1e-3)
+    assert np.abs(g.get_state()["rho"] / o.fluid()["rho"] - 1).max() <= 1e-4

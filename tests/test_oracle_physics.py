@@ -223,3 +223,20 @@ def test_mass_and_count_conserved_in_impact():
     assert d1["n_in"] == d0["n_in"] == xy.shape[0]
     assert np.isfinite([d1[k] for k in ("KE", "E_el", "p_max", "W_boundary")]).all()
     assert d1["rho_min"] >= 0.5 * p["rho0"] and d1["rho_max"] <= 1.5 * p["rho0"]
+
+
+def test_two_way_coupling_energy_balance():
+    """Two-way coupled disk (the extension the paper's Conclusions name): the
+    disk's kinetic energy lost equals the boundary work it does on the fluid
+    (eq. energy-audit's W_boundary) up to the O(dt) lag of the force."""
+    p = params(Lx=0.06, W=0.04, dx=1e-3, motion=3, t_ramp=0.0, v0=100.0, x_c0=0.012,
+               y_c0=0.0, R_disk=5e-3, gx=0.0, gy=0.0, disk_density=7850.0)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 4, disk=(0.012, 0.0, 5e-3))
+    c = oracle.OracleCase(p, xy)
+    M = p["disk_density"] * math.pi * p["R_disk"] ** 2
+    v_start = c.scalars()["vproj"]
+    c.run(300)
+    s = c.scalars()
+    dKE = 0.5 * M * (s["vproj"] ** 2 - v_start ** 2)
+    assert s["vproj"] < v_start                      # the fluid brakes the disk
+    assert abs(dKE + s["W_boundary"]) <= 0.02 * abs(s["W_boundary"])
