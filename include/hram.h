@@ -54,6 +54,9 @@ extern "C" {
 
 /* flags */
 #define HR_FLAG_TIMING 1  /* record CUDA events around the step's kernels */
+#define HR_FLAG_TANGENT 2 /* carry tangent-linear derivatives along the run
+                            (see hr_tangent_outputs); needs dt_mode 1 and
+                            motion 0-2 */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)
@@ -214,6 +217,28 @@ int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done);
 int hr_batch_done(hr_batch *b, int *n_done);
 
 void hr_batch_destroy(hr_batch *b);
+
+/* Tangent-linear (forward-mode) derivatives of two outputs of the run, for
+ * a case created with HR_FLAG_TANGENT (dt_mode 1, motion 0-2).  The parameters
+ * are theta = (alpha, c0, tau): the artificial-viscosity coefficient
+ * (eq. artificial-viscosity, Section 2.2), the reference sound speed of the
+ * Tait equation of state (which also sets the fixed step dt = C h / (c0 + v0))
+ * and the decay time of motion 0, v = v0 min(t / t_ramp, 1) exp(-t / tau)
+ * (eq. velocity-ramp times the exponential decay; motions 1 and 2 do not
+ * depend on tau, so their tau-derivatives are zero).  The derivatives are those of
+ * the discrete run itself: every step's kernels are differentiated with the
+ * step's own neighbour sets and clamp decisions, from a state uploaded by
+ * hr_init_case / hr_set_state that is taken as independent of theta.
+ *   out[0]      peak probe-0 pressure P = max_n p_0(t^n) over the recorded
+ *               history [Pa]
+ *   out[1..3]   dP / d ln alpha, dP / d ln c0, dP / d ln tau  (theta_k dP/dtheta_k)
+ *   out[4]      wall impulse J = sum_n dt^n F_wall^{n+1} [N s / m]
+ *   out[5..7]   dJ / d ln alpha, dJ / d ln c0, dJ / d ln tau
+ *   out[8]      history row of the peak (-1: no probe sample yet)
+ * n >= 9 doubles; synchronises the case's stream.  HR_EINVAL if the case was
+ * not created with HR_FLAG_TANGENT.  Batched runs do not take tangent cases,
+ * and hr_load_state refuses them (a loaded state has no derivatives). */
+int hr_tangent_outputs(hr_case *c, double *out, int n);
 
 /* Neighbour counts of the current state without any device allocation.
  *

@@ -27,12 +27,14 @@ HR_WPENETRATION = 1
 HR_WOUTSIDE = 2
 HR_WPROBEFULL = 4
 HR_FLAG_TIMING = 1
+HR_FLAG_TANGENT = 2
 
 EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",
     "hr_probe_times", "hr_diagnostics", "hr_diag_history", "hr_get_state", "hr_set_state",
     "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors", "hr_kernel_times",
-    "hr_save_state", "hr_load_state", "hr_neighbor_counts_static", "hr_batch_create",
+    "hr_save_state", "hr_load_state", "hr_tangent_outputs", "hr_neighbor_counts_static",
+    "hr_batch_create",
     "hr_batch_step", "hr_batch_run", "hr_batch_done", "hr_batch_destroy", "hr_destroy",
     "hr_status_str",
 )
@@ -99,6 +101,7 @@ def lib() -> C.CDLL:
     L.hr_kernel_times.argtypes = [vp, vp, C.c_int]
     L.hr_save_state.argtypes = [vp, C.c_char_p]
     L.hr_load_state.argtypes = [vp, C.c_char_p]
+    L.hr_tangent_outputs.argtypes = [vp, vp, C.c_int]
     L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
     L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, C.c_int, vp, P(vp)]
     L.hr_batch_step.argtypes = [vp]

@@ -17,6 +17,7 @@ DIAG_FIELDS = tuple(n for n, _ in HrDiag._fields_)
 SCALAR_FIELDS = ("t", "dt", "step", "xc", "yc", "vproj", "aproj", "Fdisk_x", "Fdisk_y",
                  "Fwall", "W_boundary", "wall_impulse", "dissipation", "diss_rate")
 KERNEL_GROUPS = ("drift", "sort", "ghost", "pass", "finalize")
+TANGENT_PARAMS = ("alpha", "c0", "tau")
 
 
 def make_params(d: dict, flags: int = 0, probe_capacity: int = 1 << 16,
@@ -73,7 +74,8 @@ class Case:
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
-                 probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True):
+                 probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
+                 tangent: bool = False):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -81,8 +83,8 @@ class Case:
             raise ValueError("xy must be (N, 2)")
         self.n = n
         self.params = dict(params)
-        self._p = make_params(params, _lib.HR_FLAG_TIMING if timing else 0, probe_capacity,
-                              diag_every)
+        flags = (_lib.HR_FLAG_TIMING if timing else 0) | (_lib.HR_FLAG_TANGENT if tangent else 0)
+        self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)
         check(L.hr_workspace_bytes(C.byref(self._p), n, C.byref(nbytes)), "hr_workspace_bytes")
@@ -216,6 +218,15 @@ class Case:
         ms = np.zeros(len(KERNEL_GROUPS), dtype=np.float32)
         check(lib().hr_kernel_times(self._h, _ptr(ms), len(KERNEL_GROUPS)), "hr_kernel_times")
         return dict(zip(KERNEL_GROUPS, ms.tolist()))
+
+    def tangent_outputs(self) -> dict:
+        """Peak probe-0 pressure and wall impulse with their derivatives along
+        ln alpha, ln c0, ln tau (a case made with tangent=True)."""
+        v = np.empty(9)
+        self.last_status = check(lib().hr_tangent_outputs(self._h, _ptr(v), 9),
+                                 "hr_tangent_outputs")
+        return dict(peak=float(v[0]), dpeak=v[1:4].copy(), impulse=float(v[4]),
+                    dimpulse=v[5:8].copy(), peak_row=int(v[8]))
 
     def save(self, path: str) -> None:
         check(lib().hr_save_state(self._h, str(path).encode()), "hr_save_state")

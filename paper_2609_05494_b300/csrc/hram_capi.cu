@@ -7,6 +7,7 @@
 // kernels with dt = 0), and captures one step as a CUDA graph on a private
 // stream; hr_step replays that graph on the caller's stream.
 #include "hram_device.cuh"
+#include "hram_tangent.cuh"
 #include "hram.h"
 
 #include <cmath>
@@ -325,6 +326,8 @@ int validate(const hr_params *P, long long nf)
     if (P->motion == 1 && !(P->drag_M > 0)) return HR_EINVAL;
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
     if (P->cell_factor < 1.0) return HR_EINVAL;
+    // tangent mode: fixed time step (smooth in c0) and a prescribed motion
+    if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
     return HR_OK;
 }
 
@@ -355,6 +358,12 @@ struct hr_case {
     float *io = nullptr;  // nf x 6 floats for state transfers
     long long host_step = 0;
     int sticky = 0;
+    // tangent mode (HR_FLAG_TANGENT)
+    bool tangent = false;
+    TBufs T{};
+    int tpass_blocks = 0;
+    void *t_base = nullptr;
+    size_t t_bytes = 0;
 };
 
 struct hr_batch {
@@ -420,6 +429,7 @@ void make_consts(hr_case *c)
     K.c0 = (float)P.c0;
     K.p_cav = (float)std::max(P.p_cav, -1e30);
     K.alpha_h = (float)(P.alpha * h);
+    K.alpha_f = (float)P.alpha;
     K.eh2 = (float)(P.eta2 * h * h);
     K.nu4 = (float)(4.0 * P.mu_lam / P.rho0);
     K.eps_xsph = (float)P.eps_xsph;
@@ -472,6 +482,7 @@ void make_consts(hr_case *c)
     c->ghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + kGhostWarps - 1) / kGhostWarps);
     c->n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
     c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
+    c->tpass_blocks = (int)((c->nf + kTPassThreads - 1) / kTPassThreads);
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
 }
@@ -482,6 +493,9 @@ struct Offsets {
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
         probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
         fin_part, fin_vmax, fin_npen, fin_ticket;
+    // tangent arrays (zero-sized unless HR_FLAG_TANGENT)
+    size_t t_begin, t_s_pos, t_s_vel, t_s_aux, t_s_rd, t_st_vel, t_st_rho, t_st_a, t_st_D, t_st_X,
+        t_u_pos, t_u_vel, t_g_vel, t_g_aux, t_perm, t_part, t_sc, t_end;
     size_t total;
 };
 
@@ -537,6 +551,27 @@ Offsets plan(const hr_case *c)
     const long long dcap = c->P.diag_every > 0 ? 4096 : 1;
     o.diag_hist = L.add((size_t)dcap * kDiagFields * 8);
     o.io = L.add(n * 6 * 4);
+    const size_t tn = (c->P.flags & HR_FLAG_TANGENT) ? n * kDir : 0;
+    const size_t tg = (c->P.flags & HR_FLAG_TANGENT) ? ng * kDir : 0;
+    const bool tm = (c->P.flags & HR_FLAG_TANGENT) != 0;
+    o.t_begin = L.total;
+    o.t_s_pos = L.add(tn * 8);
+    o.t_s_vel = L.add(tn * 8);
+    o.t_s_aux = L.add(tn * 16);
+    o.t_s_rd = L.add(tn * 8);
+    o.t_st_vel = L.add(tn * 8);
+    o.t_st_rho = L.add(tn * 4);
+    o.t_st_a = L.add(tn * 8);
+    o.t_st_D = L.add(tn * 8);
+    o.t_st_X = L.add(tn * 8);
+    o.t_u_pos = L.add(tn * 8);
+    o.t_u_vel = L.add(tn * 8);
+    o.t_g_vel = L.add(tg * 8);
+    o.t_g_aux = L.add(tg * 16);
+    o.t_perm = L.add(tm ? n * 4 : 0);
+    o.t_part = L.add(tm ? (size_t)c->tpass_blocks * kDir * 4 : 0);
+    o.t_sc = L.add(tm ? TSC_N * 8 : 0);
+    o.t_end = L.total;
     o.total = L.total;
     return o;
 }
@@ -596,6 +631,32 @@ void bind(hr_case *c, const Offsets &o)
     c->diag_hist = at<double>(w, o.diag_hist);
     c->diag_cap = c->P.diag_every > 0 ? 4096 : 1;
     c->io = at<float>(w, o.io);
+    c->tangent = (c->P.flags & HR_FLAG_TANGENT) != 0;
+    B.perm_dst = nullptr;
+    if (c->tangent) {
+        TBufs &T = c->T;
+        T.n = (int)c->nf;
+        T.ngh = (int)(c->nw + c->ng);
+        T.s_pos = at<float2>(w, o.t_s_pos);
+        T.s_vel = at<float2>(w, o.t_s_vel);
+        T.s_aux = at<float4>(w, o.t_s_aux);
+        T.s_rd = at<float2>(w, o.t_s_rd);
+        T.st_vel = at<float2>(w, o.t_st_vel);
+        T.st_rho = at<float>(w, o.t_st_rho);
+        T.st_a = at<float2>(w, o.t_st_a);
+        T.st_D = at<float2>(w, o.t_st_D);
+        T.st_X = at<float2>(w, o.t_st_X);
+        T.u_pos = at<float2>(w, o.t_u_pos);
+        T.u_vel = at<float2>(w, o.t_u_vel);
+        T.g_vel = at<float2>(w, o.t_g_vel);
+        T.g_aux = at<float4>(w, o.t_g_aux);
+        T.perm_dst = at<int>(w, o.t_perm);
+        T.part = at<float>(w, o.t_part);
+        T.sc = at<double>(w, o.t_sc);
+        B.perm_dst = T.perm_dst;
+        c->t_base = at<char>(w, o.t_begin);
+        c->t_bytes = o.t_end - o.t_begin;
+    }
 }
 
 #define CK(call)                                                    \
@@ -620,23 +681,30 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
         CK(cudaEventRecord(c->fork, s));
         CK(cudaStreamWaitEvent(side, c->fork, 0));
         k_kinematics<<<1, 128, 0, side>>>(K, B, prime);
+        if (c->tangent) kt_kinematics<<<1, 32, 0, side>>>(K, B, c->T, prime);
         CK(cudaEventRecord(c->join, side));
     } else {
         k_kinematics<<<1, 128, 0, s>>>(K, B, prime);
+        if (c->tangent) kt_kinematics<<<1, 32, 0, s>>>(K, B, c->T, prime);
     }
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     k_scan_tiles<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
     k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    if (c->tangent) kt_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
     if (side) CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+    if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     k_pass<<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
     k_finalize<<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    if (c->tangent) kt_finalize<<<1, 256, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
     return HR_OK;
@@ -697,6 +765,16 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
     Scalars S;
     std::memset(&S, 0, sizeof S);
     CK(cudaMemcpyAsync(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice, c->stream));
+    if (c->tangent) {
+        // the uploaded state does not depend on the parameters; dt = C h /
+        // (c0 + v0) has d dt / d ln c0 = -dt c0 / (c0 + v0)
+        CK(cudaMemsetAsync(c->t_base, 0, c->t_bytes, c->stream));
+        std::vector<double> sc(TSC_N, 0.0);
+        sc[TSC_DT + 1] = -c->K.dt_fixed * c->P.c0 / (c->P.c0 + c->P.v0);
+        sc[TSC_PEAK] = -HUGE_VAL;
+        sc[TSC_PSTEP] = -1.0;
+        CK(cudaMemcpyAsync(c->T.sc, sc.data(), TSC_N * 8, cudaMemcpyHostToDevice, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     c->host_step = 0;
     c->diag_rec = 0;
@@ -1167,7 +1245,7 @@ int hr_save_state(hr_case *c, const char *path)
 
 int hr_load_state(hr_case *c, const char *path)
 {
-    if (!c || !path) return HR_EINVAL;
+    if (!c || !path || c->tangent) return HR_EINVAL;
     device_status(c);
     FILE *f = std::fopen(path, "rb");
     if (!f) return HR_EIO;
@@ -1219,6 +1297,25 @@ int hr_load_state(hr_case *c, const char *path)
     c->host_step = hstep;
     c->sticky = 0;
     return device_status(c);
+}
+
+int hr_tangent_outputs(hr_case *c, double *out, int n)
+{
+    if (!c || !out || n < 9) return HR_EINVAL;
+    if (!c->tangent) return HR_EINVAL;
+    const int st = device_status(c);
+    if (st < 0) return st;
+    double sc[TSC_N];
+    Scalars S;
+    CK(cudaMemcpy(sc, c->T.sc, sizeof sc, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost));
+    const bool any = sc[TSC_PSTEP] >= 0.0;
+    out[0] = any ? sc[TSC_PEAK] : 0.0;
+    for (int k = 0; k < kDir; ++k) out[1 + k] = any ? sc[TSC_DPEAK + k] : 0.0;
+    out[4] = S.impulse;
+    for (int k = 0; k < kDir; ++k) out[5 + k] = sc[TSC_IMP + k];
+    out[8] = any ? sc[TSC_PSTEP] : -1.0;
+    return st;
 }
 
 int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
@@ -1294,7 +1391,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
         return code;
     };
     for (int k = 0; k < n_cases; ++k) {
-        if (!cases[k] || cases[k]->sticky < 0) return fail(HR_EINVAL);
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent) return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }
     b->stream = (cudaStream_t)cuda_stream;

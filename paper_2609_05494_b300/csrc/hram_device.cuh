@@ -55,7 +55,7 @@ struct Consts {
     // kernel
     float h, s2, half_inv_h, two_inv_h, Wc, Fc;
     // fluid
-    float m, rho0, inv_rho0, B, c0, p_cav, alpha_h, eh2, nu4, eps_xsph, gx, gy;
+    float m, rho0, inv_rho0, B, c0, p_cav, alpha_h, alpha_f, eh2, nu4, eps_xsph, gx, gy;
     float d_lo, d_hi, gamma, half_gm1, inv_rho0c02;
     int gamma7;
     // ghosts
@@ -121,6 +121,7 @@ struct Bufs {
     int *cell_start; // ncell + 2
     int *tile_sum;
     int *perm_tmp;   // fluid IDs in provisional cell order
+    int *perm_dst;   // previous slot -> slot of this step (tangent mode only, else null)
     // wall ghosts (static, cell order) and disk ghosts
     float2 *gw_pos;
     float2 *gw_nrm;
@@ -548,6 +549,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     B.s_aux[dst] = eos_record(K, dp);
     B.s_rd[dst] = make_float2(d, D.x);
     B.s_id[dst] = id;
+    if (B.perm_dst) B.perm_dst[i] = dst;
 }
 
 // ------------------------------------------------------- a4: ghosts G
