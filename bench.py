@@ -205,6 +205,55 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
             "autotune": tune_report, "autotune_s": t_tune}
 
 
+def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
+    """Cost of the tangent-linear mode (derivatives of the peak probe pressure
+    and the wall impulse along alpha, c0, tau): the 22,500-particle fixed-dt
+    workload run for its 400 steps with and without HR_FLAG_TANGENT, and a few
+    steps of the 1.125M-particle workload (fixed dt) both ways.  CUDA events on
+    the case's stream around hr_run."""
+    import torch
+    from paper_2609_05494_b300 import Case
+
+    def timed(p, xy, steps, tangent):
+        with torch.cuda.stream(stream):
+            c = Case(p, xy, stream=stream, tangent=tangent, probe_capacity=steps + 8)
+        c.run(3)
+        c.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.run(steps)
+        b.record(stream)
+        c.sync()
+        ms = a.elapsed_time(b)
+        out = c.tangent_outputs() if tangent else None
+        c.close()
+        return ms, out
+
+    p = casegen.config_adjoint()
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+    steps = int(p["n_steps"])
+    f_ms, _ = timed(p, xy, steps, False)
+    t_ms, out = timed(p, xy, steps, True)
+    res = {"workload": "150 x 150 mm, dx = 1 mm, %d particles, %d steps, fixed dt"
+                       % (xy.shape[0], steps),
+           "forward_ms_per_step": f_ms / steps, "tangent_ms_per_step": t_ms / steps,
+           "tangent_over_forward": t_ms / f_ms,
+           "gradients_per_s": 1e3 / t_ms,
+           "peak_Pa": out["peak"], "dpeak_dln": out["dpeak"].tolist(),
+           "impulse": out["impulse"], "dimpulse_dln": out["dimpulse"].tolist()}
+    if big_xy is not None:
+        q = dict(big_p)
+        q["dt_mode"] = 1
+        f_ms, _ = timed(q, big_xy, big_steps, False)
+        t_ms, _ = timed(q, big_xy, big_steps, True)
+        res["large"] = {"particles": int(big_xy.shape[0]), "steps": big_steps,
+                        "forward_ms_per_step": f_ms / big_steps,
+                        "tangent_ms_per_step": t_ms / big_steps,
+                        "tangent_over_forward": t_ms / f_ms}
+    return res
+
+
 def cpu_baseline(seconds=15.0, Lx=0.075):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the
     workload: the first Lx of the channel at the same spacing, from t = 0."""
@@ -265,6 +314,7 @@ def main():
     ap.add_argument("--dx", type=float, default=DX)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-tangent", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -340,6 +390,7 @@ def main():
 
     case.close()
     sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
+    tangent = None if args.no_tangent else tangent_benchmark(stream, xy, p)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -379,6 +430,7 @@ def main():
                          "peak_source": src, "bytes_per_particle": ALG_BYTES_PER_PARTICLE},
         "kernel_groups_ms": groups,
         "batched_sweep": sweep,
+        "tangent": tangent,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

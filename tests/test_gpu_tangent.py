@@ -24,10 +24,12 @@ from paper_2609_05494_b300 import (Batch, Case, HramError, TANGENT_PARAMS, _lib,
 
 N_STEPS = 250
 FD_EPS = 1e-5      # relative central-difference step of the oracle
-# FP32 tangents against FP64 differences: 2 % of the derivative, with a floor
-# of 1e-4 of the output per unit ln(theta) for derivatives that are nearly zero
-REL_TOL = 2e-2
-FLOOR = 1e-4
+# FP32 tangents against FP64 differences: 2e-3 of the derivative, with a floor
+# of 1e-5 of the output per unit ln(theta) for derivatives that are nearly
+# zero.  Measured on B300: 3e-7 .. 6e-4 (the worst is d peak / d ln c0 under
+# the drag law, where the peak's step sits on a steep front).
+REL_TOL = 2e-3
+FLOOR = 1e-5
 
 
 def tangent_case(**kw):
