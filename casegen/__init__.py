@@ -119,6 +119,9 @@ def base_params() -> dict:
     3 ghost layers per side wall, a 5 mm disk entering at the mid-height of the
     x = 0 face with a 5 us ramp and exponential deceleration tau = 200 us;
     disk density 7850 kg/m^3 (steel) for the two-way coupled motion.
+    closure 0 selects the workloads' closure (Wendland, continuity, Tait);
+    closure 1 the paper's (cubic B-spline, summation density, Mie-Grueneisen
+    water with S1 1.979, gamma0 0.11, a 3.0, compression cap mu <= 0.25).
     """
     return dict(
         dx=2e-3, h_over_dx=1.3, Lx=0.150, W=0.150,
@@ -129,6 +132,7 @@ def base_params() -> dict:
         eps_xsph=0.02, mu_lam=8.9e-4, gx=0.0, gy=-9.81, cfl=0.2, dt_mode=0,
         rho_lo=0.5, rho_hi=1.5, box_pad=-1.0, cell_factor=1.001,
         seed=DEFAULT_SEED, jitter=0.01, disk_density=7850.0,
+        closure=0, mg_S1=1.979, mg_gamma0=0.11, mg_a=3.0, mg_mu_max=0.25,
         probes=[],
     )
 
@@ -160,6 +164,21 @@ def config_scaling(dx: float) -> dict:
     p = config_production(900.0)
     p.update(dx=float(dx))
     p.pop("t_end")
+    return p
+
+
+def config_paper(v0: float = 900.0) -> dict:
+    """The paper's own set-up (closure 1): a 750 x 150 mm channel at dx = 1.5 mm
+    (500 x 100 lattice points before the disk interior is removed), a
+    12.5 mm disk entering on the centreline at v0 with the 5 us ramp and then
+    the quadratic drag law (M = 8.01 g, Cd = 0.05, R = 6.25 mm), water with
+    C = c0 = 1448 m/s, alpha 0.03, CFL 0.25, and the probes PTn and PTf on the
+    centreline at x = 30 and 105 mm; 250 us of simulated time."""
+    p = base_params()
+    p.update(dx=1.5e-3, Lx=0.750, W=0.150, R_disk=6.25e-3, x_c0=-6.25e-3, v0=float(v0),
+             motion=1, c0=1448.0, alpha=0.03, cfl=0.25, closure=1)
+    p["probes"] = [(0.030, 0.0), (0.105, 0.0)]
+    p["t_end"] = 250e-6
     return p
 
 

@@ -26,7 +26,7 @@ _lib = None
 N_PROBE_MAX = 16
 
 MUT = dict(ghost_printed_sign=1, drop_pj=2, kernel_norm=4, av_sign=8, dt_no_ghosts=16,
-           grad_sign=32, ghost_vel=64)
+           grad_sign=32, ghost_vel=64, energy_half=128, sum_no_self=256)
 
 DIAG_FIELDS = ("mass", "px", "py", "KE", "PE", "E_el", "rho_min", "rho_max", "p_min",
                "p_max", "vmax_fluid", "n_in", "penetrated", "t", "dt", "W_boundary",
@@ -52,6 +52,9 @@ class OracleParams(C.Structure):
         ("probe_xy", C.c_double * (2 * N_PROBE_MAX)),
         ("mutation", C.c_int32), ("brute", C.c_int32),
         ("disk_density", C.c_double),
+        ("closure", C.c_int32),
+        ("mg_S1", C.c_double), ("mg_gamma0", C.c_double), ("mg_a", C.c_double),
+        ("mg_mu_max", C.c_double),
     ]
 
 
@@ -103,6 +106,13 @@ def lib() -> C.CDLL:
         L.orc_predicate32.restype = C.c_int
         L.orc_predicate32.argtypes = [C.c_float] * 5
         L.orc_kinematics.argtypes = [P(OracleParams), C.c_double, vp, vp, vp]
+        L.orc_cubic_W.restype = C.c_double
+        L.orc_cubic_W.argtypes = [C.c_double, C.c_double]
+        L.orc_cubic_F.restype = C.c_double
+        L.orc_cubic_F.argtypes = [C.c_double, C.c_double]
+        L.orc_mg_p.restype = C.c_double
+        L.orc_mg_p.argtypes = [P(OracleParams), C.c_double, C.c_double]
+        L.orc_get_energy.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -175,6 +185,13 @@ class OracleCase:
                                        ("xy", "vel", "rho", "p", "acc", "drho", "X", "out")))
         return out
 
+    def energy(self) -> dict:
+        """Specific internal energy e and its rate De (closure 1)."""
+        n = self.nf
+        out = dict(e=np.empty(n), de=np.empty(n))
+        lib().orc_get_energy(self._h, _ptr(out["e"]), _ptr(out["de"]))
+        return out
+
     def ghosts(self) -> dict:
         n = self.ngh
         out = dict(xy=np.empty((n, 2)), p=np.empty(n), rho=np.empty(n), vel=np.empty((n, 2)),
@@ -236,6 +253,21 @@ def kernel_W(r: float, h: float, mutation: int = 0) -> float:
 def kernel_F(r: float, h: float, mutation: int = 0) -> float:
     """F(r) with grad_i W_ij = F(r) (r_i - r_j)."""
     return lib().orc_kernel_F(float(r), float(h), int(mutation))
+
+
+def cubic_W(r: float, h: float) -> float:
+    """Cubic B-spline kernel of the paper (closure 1)."""
+    return lib().orc_cubic_W(float(r), float(h))
+
+
+def cubic_F(r: float, h: float) -> float:
+    return lib().orc_cubic_F(float(r), float(h))
+
+
+def mg_p(params: dict, rho: float, e: float) -> float:
+    """Mie-Grueneisen pressure of the paper's closure (with the cutoff)."""
+    p = make_params(params)
+    return lib().orc_mg_p(C.byref(p), float(rho), float(e))
 
 
 def predicate32(xi, yi, xj, yj, s2) -> bool:

@@ -43,7 +43,9 @@ enum {
     MUT_AV_SIGN = 8,             /* artificial viscosity switched on under separation */
     MUT_DT_NO_GHOSTS = 16,       /* v_max taken over fluid only */
     MUT_GRAD_SIGN = 32,          /* grad W pointing the wrong way */
-    MUT_GHOST_VEL = 64           /* v_g = v_w + <v>  instead of 2 v_w - <v> */
+    MUT_GHOST_VEL = 64,          /* v_g = v_w + <v>  instead of 2 v_w - <v> */
+    MUT_ENERGY_HALF = 128,       /* energy equation without its factor 1/2 */
+    MUT_SUM_NO_SELF = 256        /* summation density without the particle itself */
 };
 
 typedef struct {
@@ -58,6 +60,11 @@ typedef struct {
     double probe_xy[32];
     int32_t mutation, brute;
     double disk_density;
+    /* closure 0: the workloads' (Wendland, continuity density, Tait);
+     * closure 1: the paper's own (cubic B-spline, summation density,
+     * Mie-Grueneisen EOS with the internal-energy equation) */
+    int32_t closure;
+    double mg_S1, mg_gamma0, mg_a, mg_mu_max;
 } orc_params;
 
 enum { KIND_FLUID = 0, KIND_SIDE = 1, KIND_END = 2, KIND_DISK = 3 };
@@ -72,6 +79,8 @@ typedef struct {
     int64_t nf;
     double *x, *y, *vx, *vy, *rho, *ax, *ay, *drho, *Xx, *Xy;
     double *vhx, *vhy, *rhoh, *p, *aavx, *aavy, *drho_prev;
+    double *e, *eh, *de;   /* closure 1: specific internal energy, its prediction, rate */
+    double *vkx, *vky;     /* closure 1: v^{n+1/2} while the operators see v predicted */
     unsigned char *out;
     /* ghosts: walls first, then disk */
     int64_t nw, nd, ngh;
@@ -97,10 +106,35 @@ typedef struct {
 
 /* --------------------------------------------------------------- kernel */
 
+/* Cubic B-spline kernel in two dimensions (Section "SPH Fundamentals", eq.
+ * cubic-kernel; closure 1):
+ *   W(q) = s_d (1 - 3/2 q^2 + 3/4 q^3)  for q <= 1,
+ *          s_d (2 - q)^3 / 4            for 1 < q <= 2,  s_d = 10 / (7 pi h^2),
+ * and F = (dW/dr) / r:
+ *   F = s_d / h^2 (-3 + 9/4 q)          for q <= 1,
+ *       s_d / h^2 (-3/4 (2 - q)^2 / q)  for 1 < q < 2. */
+static double cubic_W(double h, double r)
+{
+    double q = r / h, sd = 10.0 / (7.0 * M_PI * h * h);
+    if (q >= 2.0) return 0.0;
+    if (q <= 1.0) return sd * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    return sd * 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+}
+
+static double cubic_F(double h, double r)
+{
+    double q = r / h, sd = 10.0 / (7.0 * M_PI * h * h);
+    if (q >= 2.0) return 0.0;
+    if (q <= 1.0) return sd / (h * h) * (-3.0 + 2.25 * q);
+    return sd / (h * h) * (-0.75 * (2.0 - q) * (2.0 - q) / q);
+}
+
 /* Wendland C2 kernel in two dimensions (reading R1, the workloads' kernel):
- *   W(q) = a_d (1 - q/2)^4 (1 + 2q),  q = r/h in [0, 2],  a_d = 7 / (4 pi h^2). */
+ *   W(q) = a_d (1 - q/2)^4 (1 + 2q),  q = r/h in [0, 2],  a_d = 7 / (4 pi h^2).
+ * Closure 1 uses the cubic B-spline above instead. */
 static double kernel_W(const orc_case *c, double r)
 {
+    if (c->P.closure == 1) return cubic_W(c->h, r);
     double q = r / c->h;
     if (q >= 2.0) return 0.0;
     double t = 1.0 - 0.5 * q;
@@ -111,6 +145,10 @@ static double kernel_W(const orc_case *c, double r)
  * of the kernel above divided by r). */
 static double kernel_F(const orc_case *c, double r)
 {
+    if (c->P.closure == 1) {
+        double F = cubic_F(c->h, r);
+        return (c->P.mutation & MUT_GRAD_SIGN) ? -F : F;
+    }
     double q = r / c->h;
     if (q >= 2.0) return 0.0;
     double t = 1.0 - 0.5 * q;
@@ -143,6 +181,9 @@ double orc_kernel_F(double r, double h, int32_t mutation)
     return kernel_F(&c, r);
 }
 
+double orc_cubic_W(double r, double h) { return cubic_W(h, r); }
+double orc_cubic_F(double r, double h) { return cubic_F(h, r); }
+
 /* ------------------------------------------------------------ predicate */
 
 /* Neighbour predicate of reading R2, float arithmetic, no contraction. */
@@ -172,9 +213,43 @@ static double eos_p(const orc_case *c, double rho)
     return p > c->P.p_cav ? p : c->P.p_cav;
 }
 
-/* Sound speed c = c0 (rho/rho0)^((gamma-1)/2) (reading R5). */
+/* Mie-Grueneisen equation of state with a linear Us-Up Hugoniot reference
+ * (Section "Closure", eq. eos; closure 1), mu = rho/rho0 - 1, C = c0:
+ *   mu >= 0:  p = rho0 C^2 mu [1 + (1 - gamma0/2) mu] / [1 - (S1 - 1) mu]^2
+ *                 + (gamma0 + a mu) rho e,
+ *   mu <  0:  p = rho0 C^2 mu + gamma0 rho e,
+ * then p >= p_cav.  Reading P3: the compression cap mu <= mu_max (0.25) is
+ * applied to the state, i.e. the whole formula is evaluated at
+ * rho = rho0 (1 + min(mu, mu_max)). */
+static double mg_p(const orc_case *c, double rho, double e)
+{
+    const orc_params *P = &c->P;
+    double mu = rho / P->rho0 - 1.0;
+    if (mu > P->mg_mu_max) mu = P->mg_mu_max;
+    double rc = P->rho0 * (1.0 + mu), K = P->rho0 * P->c0 * P->c0, p;
+    if (mu >= 0.0) {
+        double den = 1.0 - (P->mg_S1 - 1.0) * mu;
+        p = K * mu * (1.0 + (1.0 - 0.5 * P->mg_gamma0) * mu) / (den * den)
+            + (P->mg_gamma0 + P->mg_a * mu) * rc * e;
+    } else {
+        p = K * mu + P->mg_gamma0 * rc * e;
+    }
+    return p > P->p_cav ? p : P->p_cav;
+}
+
+double orc_mg_p(const orc_params *P, double rho, double e)
+{
+    orc_case c;
+    memset(&c, 0, sizeof c);
+    c.P = *P;
+    return mg_p(&c, rho, e);
+}
+
+/* Sound speed c = c0 (rho/rho0)^((gamma-1)/2) (reading R5).  Closure 1
+ * (reading P4): the reference celerity c0 = C throughout. */
 static double sound_speed(const orc_case *c, double rho)
 {
+    if (c->P.closure == 1) return c->P.c0;
     return c->P.c0 * pow(rho / c->P.rho0, 0.5 * (c->P.gamma - 1.0));
 }
 
@@ -507,6 +582,9 @@ static void ghost_operator(orc_case *c)
 /* Interaction operator L (Section "Governing Equations"; continuity route of
  * reading R3).  For fluid i over its neighbours j (fluid or ghost):
  *   D rho_i = sum m_j v_ij . grad_i W_ij                               (R3)
+ *   closure 1 instead (reading P5, the internal-energy equation that goes
+ *   with the momentum equation's pair terms):
+ *   D e_i = 1/2 sum m_j (p_i/rho_i^2 + p_j/rho_j^2 + Pi_ij) v_ij . grad_i W_ij
  *   a_i = - sum m_j (p_i/rho_i^2 + p_j/rho_j^2 + Pi_ij) grad_i W_ij    (momentum)
  *         + sum m_j 4 nu (r_ij . grad_i W_ij) / ((rho_i + rho_j)(r^2 + eta^2 h^2)) v_ij
  *                                                    (laminar term, reading R7)
@@ -523,9 +601,10 @@ static void interaction_operator(orc_case *c)
     for (int64_t i = 0; i < c->nf; ++i) {
         c->ax[i] = c->ay[i] = c->drho[i] = c->Xx[i] = c->Xy[i] = 0.0;
         c->aavx[i] = c->aavy[i] = 0.0;
+        c->de[i] = 0.0;
         if (c->out[i]) continue;
         double rhoi = c->rhoh[i], Pi_ = c->p[i] / (rhoi * rhoi), ci = sound_speed(c, rhoi);
-        double ax = 0, ay = 0, dr = 0, Xx = 0, Xy = 0, avx = 0, avy = 0;
+        double ax = 0, ay = 0, dr = 0, Xx = 0, Xy = 0, avx = 0, avy = 0, de = 0;
         for (int64_t a = c->nb_off[i]; a < c->nb_off[i + 1]; ++a) {
             int64_t j = c->nb_id[a];
             int ghost = j >= c->nf;
@@ -552,6 +631,9 @@ static void interaction_operator(orc_case *c)
                 Pij = -c->P.alpha * cbar * mu / rhobar;
             }
             double Pj = (c->P.mutation & MUT_DROP_PJ) ? 0.0 : pj / (rhoj * rhoj);
+            /* internal energy (closure 1) */
+            double half_e = (c->P.mutation & MUT_ENERGY_HALF) ? 1.0 : 0.5;
+            de += half_e * mj * (Pi_ + Pj + Pij) * F * vr;
             double fx = -mj * (Pi_ + Pj + Pij) * F * rx;
             double fy = -mj * (Pi_ + Pj + Pij) * F * ry;
             /* laminar viscosity */
@@ -578,7 +660,8 @@ static void interaction_operator(orc_case *c)
         }
         c->ax[i] = ax + c->P.gx;
         c->ay[i] = ay + c->P.gy;
-        c->drho[i] = dr;
+        c->drho[i] = c->P.closure == 1 ? 0.0 : dr;
+        c->de[i] = c->P.closure == 1 ? de : 0.0;
         c->Xx[i] = Xx;
         c->Xy[i] = Xy;
         c->aavx[i] = avx;
@@ -589,6 +672,36 @@ static void interaction_operator(orc_case *c)
     c->Fdy = Fdy;
     c->Fwall = Fw;
     c->diss_rate = diss;
+}
+
+/* Summation density (Section "Density Summation", eq. density-sum; closure
+ * 1): rho_i = sum_j m_j W_ij over the particle itself and its fluid and ghost
+ * neighbours (the ghosts complete the sum near a boundary, Section "The
+ * Projectile"), then the band [rho_lo, rho_hi] rho0.  A frozen particle keeps
+ * its density. */
+static void summation_density(orc_case *c)
+{
+    for (int64_t i = 0; i < c->nf; ++i) {
+        if (c->out[i]) { c->rhoh[i] = c->rho[i]; continue; }
+        double rho = (c->P.mutation & MUT_SUM_NO_SELF) ? 0.0 : c->m * kernel_W(c, 0.0);
+        for (int64_t a = c->nb_off[i]; a < c->nb_off[i + 1]; ++a) {
+            int64_t j = c->nb_id[a];
+            int ghost = j >= c->nf;
+            double xj = ghost ? c->gx[j - c->nf] : c->x[j];
+            double yj = ghost ? c->gy[j - c->nf] : c->y[j];
+            double mj = ghost ? c->gm[j - c->nf] : c->m;
+            double rx = c->x[i] - xj, ry = c->y[i] - yj;
+            rho += mj * kernel_W(c, sqrt(rx * rx + ry * ry));
+        }
+        c->rho[i] = clamp_rho(c, rho);
+        c->rhoh[i] = c->rho[i];
+    }
+}
+
+/* Pressure of fluid particle i at its end-of-step state. */
+static double fluid_p(const orc_case *c, int64_t i)
+{
+    return c->P.closure == 1 ? mg_p(c, c->rho[i], c->e[i]) : eos_p(c, c->rho[i]);
 }
 
 /* Probe value (reading R13): the wall-ghost formula (a = 0, body-force term
@@ -604,7 +717,7 @@ static double probe_value(orc_case *c, double px, double py)
         double rx = px - c->x[j], ry = py - c->y[j];
         double Wj = kernel_W(c, sqrt(rx * rx + ry * ry));
         SW += Wj;
-        Sp += eos_p(c, c->rho[j]) * Wj;
+        Sp += fluid_p(c, j) * Wj;
         Srx += c->rho[j] * rx * Wj;
         Sry += c->rho[j] * ry * Wj;
     }
@@ -680,7 +793,7 @@ orc_case *orc_create(const orc_params *P, int64_t nf, const double *xy, const do
     size_t sz = (size_t)(nf > 0 ? nf : 1) * sizeof(double);
     double **arrs[] = {&c->x, &c->y, &c->vx, &c->vy, &c->rho, &c->ax, &c->ay, &c->drho,
                        &c->Xx, &c->Xy, &c->vhx, &c->vhy, &c->rhoh, &c->p, &c->aavx, &c->aavy,
-                       &c->drho_prev};
+                       &c->drho_prev, &c->e, &c->eh, &c->de, &c->vkx, &c->vky};
     for (size_t k = 0; k < sizeof arrs / sizeof arrs[0]; ++k) *arrs[k] = (double *)calloc(1, sz);
     c->out = (unsigned char *)calloc((size_t)(nf > 0 ? nf : 1), 1);
     for (int64_t i = 0; i < nf; ++i) {
@@ -723,7 +836,8 @@ void orc_destroy(orc_case *c)
 {
     if (!c) return;
     double *arrs[] = {c->x, c->y, c->vx, c->vy, c->rho, c->ax, c->ay, c->drho, c->Xx, c->Xy,
-                      c->vhx, c->vhy, c->rhoh, c->p, c->aavx, c->aavy, c->drho_prev, c->gx, c->gy, c->gnx,
+                      c->vhx, c->vhy, c->rhoh, c->p, c->aavx, c->aavy, c->drho_prev, c->e, c->eh,
+                      c->de, c->vkx, c->vky, c->gx, c->gy, c->gnx,
                       c->gny, c->gm, c->gp, c->grho, c->gvx, c->gvy, c->doffx, c->doffy,
                       c->probe_hist, c->probe_t, c->probe_imp};
     for (size_t k = 0; k < sizeof arrs / sizeof arrs[0]; ++k) free(arrs[k]);
@@ -760,8 +874,21 @@ void orc_prime(orc_case *c)
         c->rho[i] = clamp_rho(c, c->rho[i]);
         c->out[i] = c->out[i] || !in_box(c, c->x[i], c->y[i]);
     }
-    take_half_state_as_current(c);
-    build_neighbours(c);
+    if (c->P.closure == 1) {
+        /* the density is a function of the positions: the summation replaces
+         * the given density; the internal energy starts at zero */
+        for (int64_t i = 0; i < c->nf; ++i) {
+            c->vhx[i] = c->vx[i];
+            c->vhy[i] = c->vy[i];
+            c->eh[i] = c->e[i];
+        }
+        build_neighbours(c);
+        summation_density(c);
+        for (int64_t i = 0; i < c->nf; ++i) c->p[i] = mg_p(c, c->rhoh[i], c->eh[i]);
+    } else {
+        take_half_state_as_current(c);
+        build_neighbours(c);
+    }
     ghost_operator(c);
     interaction_operator(c);
     for (int64_t i = 0; i < c->nf; ++i) c->drho_prev[i] = c->drho[i];
@@ -792,9 +919,12 @@ void orc_prime(orc_case *c)
  *   (5) interaction sums L on (r^{n+1}, v^{n+1/2}, rho~^{n+1}) -> a, D rho, X
  *   (6) rho^{n+1} = band(rho^n + dt D rho^{n+1}); v^{n+1} = v^{n+1/2} + dt/2 a^{n+1}
  *   (7) dt^{n+1} from the CFL gate over fluid and ghosts. */
-void orc_step(orc_case *c)
+static void drift_and_walls(orc_case *c, double dt);
+static void close_step(orc_case *c, double dt);
+
+static void step_continuity(orc_case *c)
 {
-    const double dt = c->dt, half = 0.5 * dt, W2 = 0.5 * c->P.W, eps = 1e-6;
+    const double dt = c->dt, half = 0.5 * dt;
     const double ratio = c->dt_prev > 0.0 ? dt / c->dt_prev : 1.0;
     /* (1) opening half kick of the velocity */
     for (int64_t i = 0; i < c->nf; ++i) {
@@ -803,20 +933,7 @@ void orc_step(orc_case *c)
         c->vhy[i] = c->vy[i] + half * c->ay[i];
     }
     /* (2) drift with the XSPH velocity, then wall enforcement (reading R14) */
-    for (int64_t i = 0; i < c->nf; ++i) {
-        if (c->out[i]) continue;
-        c->x[i] += dt * (c->vhx[i] + c->P.eps_xsph * c->Xx[i]);
-        c->y[i] += dt * (c->vhy[i] + c->P.eps_xsph * c->Xy[i]);
-        if (c->P.wall_layers > 0) {
-            if (c->y[i] > W2) { c->y[i] = W2 - eps; c->vhy[i] = -c->vhy[i]; }
-            else if (c->y[i] < -W2) { c->y[i] = -W2 + eps; c->vhy[i] = -c->vhy[i]; }
-            if (c->P.end_walls) {
-                if (c->x[i] > c->P.Lx) { c->x[i] = c->P.Lx - eps; c->vhx[i] = -c->vhx[i]; }
-                else if (c->x[i] < 0.0) { c->x[i] = eps; c->vhx[i] = -c->vhx[i]; }
-            }
-        }
-        if (!in_box(c, c->x[i], c->y[i])) c->out[i] = 1;
-    }
+    drift_and_walls(c, dt);
     /* (3) time and projectile kinematics at t^{n+1} */
     c->t += dt;
     kinematics_advance(c, dt);
@@ -842,6 +959,95 @@ void orc_step(orc_case *c)
         c->vx[i] = c->vhx[i] + half * c->ax[i];
         c->vy[i] = c->vhy[i] + half * c->ay[i];
     }
+    close_step(c, dt);
+}
+
+static void drift_and_walls(orc_case *c, double dt)
+{
+    const double W2 = 0.5 * c->P.W, eps = 1e-6;
+    for (int64_t i = 0; i < c->nf; ++i) {
+        if (c->out[i]) continue;
+        c->x[i] += dt * (c->vhx[i] + c->P.eps_xsph * c->Xx[i]);
+        c->y[i] += dt * (c->vhy[i] + c->P.eps_xsph * c->Xy[i]);
+        if (c->P.wall_layers > 0) {
+            if (c->y[i] > W2) { c->y[i] = W2 - eps; c->vhy[i] = -c->vhy[i]; }
+            else if (c->y[i] < -W2) { c->y[i] = -W2 + eps; c->vhy[i] = -c->vhy[i]; }
+            if (c->P.end_walls) {
+                if (c->x[i] > c->P.Lx) { c->x[i] = c->P.Lx - eps; c->vhx[i] = -c->vhx[i]; }
+                else if (c->x[i] < 0.0) { c->x[i] = eps; c->vhx[i] = -c->vhx[i]; }
+            }
+        }
+        if (!in_box(c, c->x[i], c->y[i])) c->out[i] = 1;
+    }
+}
+
+/* Closure 1 (reading P6): the paper's kick-drift-kick step with the
+ * summation density, one interaction pass per step.  The pass sees the state
+ * predicted at t^{n+1}: velocities v* = v^{n+1/2} + dt/2 a^n and energies
+ * e* = e^n + dt De^n, so that the velocity-dependent terms (artificial
+ * viscosity, the energy equation) are centred where the forces are; with
+ * v^{n+1/2} instead, the kinetic plus internal energy would drift by
+ * dt^2/2 sum m |a|^2 every step (first order overall).
+ *   (1) v^{n+1/2} = v^n + dt/2 a^n
+ *   (2) r^{n+1} = r^n + dt (v^{n+1/2} + eps X^n); wall enforcement (R14)
+ *   (3) t^{n+1}; projectile kinematics at t^{n+1}
+ *   (4) rho^{n+1} = band(sum_j m_j W_ij(r^{n+1})); v* and e* as above;
+ *       p = MG(rho^{n+1}, e*); ghosts G from (r^{n+1}, v*, p)
+ *   (5) interaction sums L on (r^{n+1}, v*, rho^{n+1}, p) -> a^{n+1}, De^{n+1}, X^{n+1}
+ *   (6) v^{n+1} = v^{n+1/2} + dt/2 a^{n+1},  e^{n+1} = e^n + dt/2 (De^n + De^{n+1})
+ *   (7) dt^{n+1} from the CFL gate. */
+static void step_summation(orc_case *c)
+{
+    const double dt = c->dt, half = 0.5 * dt;
+    for (int64_t i = 0; i < c->nf; ++i) {
+        if (c->out[i]) {
+            c->vhx[i] = c->vx[i];
+            c->vhy[i] = c->vy[i];
+            continue;
+        }
+        c->vhx[i] = c->vx[i] + half * c->ax[i];
+        c->vhy[i] = c->vy[i] + half * c->ay[i];
+    }
+    drift_and_walls(c, dt);
+    c->t += dt;
+    kinematics_advance(c, dt);
+    place_disk(c);
+    build_neighbours(c);
+    summation_density(c);
+    for (int64_t i = 0; i < c->nf; ++i) {
+        c->vkx[i] = c->vhx[i];
+        c->vky[i] = c->vhy[i];
+        if (c->out[i]) {
+            c->eh[i] = c->e[i];
+        } else {
+            c->vhx[i] += half * c->ax[i];
+            c->vhy[i] += half * c->ay[i];
+            c->eh[i] = c->e[i] + dt * c->de[i];
+        }
+        c->p[i] = mg_p(c, c->rhoh[i], c->eh[i]);
+    }
+    ghost_operator(c);
+    double *de_old = (double *)malloc((size_t)(c->nf > 0 ? c->nf : 1) * sizeof(double));
+    memcpy(de_old, c->de, (size_t)c->nf * sizeof(double));
+    interaction_operator(c);
+    for (int64_t i = 0; i < c->nf; ++i) {
+        if (c->out[i]) {
+            c->vx[i] = c->vkx[i];
+            c->vy[i] = c->vky[i];
+            c->ax[i] = c->ay[i] = c->de[i] = c->Xx[i] = c->Xy[i] = 0.0;
+            continue;
+        }
+        c->vx[i] = c->vkx[i] + half * c->ax[i];
+        c->vy[i] = c->vky[i] + half * c->ay[i];
+        c->e[i] += half * (de_old[i] + c->de[i]);
+    }
+    free(de_old);
+    close_step(c, dt);
+}
+
+/* Accumulators, probes and the CFL gate at the end of a step. */
+static void close_step(orc_case *c, double dt)
+{
     /* accumulated boundary work, wall impulse, dissipation (R16, R17) */
     c->Wb += dt * (c->Fdx * c->vproj);
     c->impulse += dt * c->Fwall;
@@ -851,6 +1057,12 @@ void orc_step(orc_case *c)
     record_probes(c);
     c->dt_prev = dt;
     c->dt = cfl_dt(c);
+}
+
+void orc_step(orc_case *c)
+{
+    if (c->P.closure == 1) step_summation(c);
+    else step_continuity(c);
 }
 
 void orc_run(orc_case *c, int64_t n)
@@ -871,11 +1083,19 @@ void orc_get_fluid(const orc_case *c, double *xy, double *vel, double *rho, doub
         if (xy) { xy[2 * i] = c->x[i]; xy[2 * i + 1] = c->y[i]; }
         if (vel) { vel[2 * i] = c->vx[i]; vel[2 * i + 1] = c->vy[i]; }
         if (rho) rho[i] = c->rho[i];
-        if (p) p[i] = eos_p(c, c->rho[i]);
+        if (p) p[i] = fluid_p(c, i);
         if (acc) { acc[2 * i] = c->ax[i]; acc[2 * i + 1] = c->ay[i]; }
         if (drho) drho[i] = c->drho[i];
         if (X) { X[2 * i] = c->Xx[i]; X[2 * i + 1] = c->Xy[i]; }
         if (out) out[i] = c->out[i];
+    }
+}
+
+void orc_get_energy(const orc_case *c, double *e, double *de)
+{
+    for (int64_t i = 0; i < c->nf; ++i) {
+        if (e) e[i] = c->e[i];
+        if (de) de[i] = c->de[i];
     }
 }
 
@@ -923,7 +1143,8 @@ int64_t orc_neighbours(const orc_case *c, int64_t *off, int32_t *ids, int64_t ca
 void orc_refresh_neighbours(orc_case *c) { build_neighbours(c); }
 
 /* Diagnostics in FP64 (the paper logs mass and mechanical energy; readings
- * R16-R18 add the impulse, boundary work and Tait elastic energy):
+ * R16-R18 add the impulse, boundary work and Tait elastic energy; with
+ * closure 1, E_el is the internal energy sum m e of the energy equation):
  *  0 mass  1 px  2 py  3 KE  4 PE  5 E_el  6 rho_min  7 rho_max  8 p_min
  *  9 p_max 10 vmax_fluid 11 n_in 12 penetrated 13 t 14 dt 15 Wb 16 impulse
  * 17 diss 18 step */
@@ -941,8 +1162,8 @@ void orc_diagnostics(const orc_case *c, double *d)
         py += c->m * c->vy[i];
         ke += 0.5 * c->m * v2;
         pe += -c->m * (c->P.gx * c->x[i] + c->P.gy * c->y[i]);
-        eel += c->m * tait_energy(c, c->rho[i]);
-        double pr = eos_p(c, c->rho[i]);
+        eel += c->m * (c->P.closure == 1 ? c->e[i] : tait_energy(c, c->rho[i]));
+        double pr = fluid_p(c, i);
         if (c->rho[i] < rmin) rmin = c->rho[i];
         if (c->rho[i] > rmax) rmax = c->rho[i];
         if (pr < pmin) pmin = pr;
