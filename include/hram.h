@@ -82,7 +82,19 @@ extern "C" {
  *  probe_xy        wall probe points, n_probes of them
  *  probe_capacity  probe history rows kept on the device
  *  diag_every      record FP64 diagnostics every k steps (0 = never)
- *  flags           HR_FLAG_* */
+ *  flags           HR_FLAG_*
+ *  disk_density    disk material density for motion 3 [kg/m^3]
+ *  closure         0: Wendland C2 kernel, continuity density, Tait EOS (above);
+ *                  1: the paper's own closure -- cubic B-spline (eq.
+ *                  cubic-kernel), summation density with the band (eq.
+ *                  density-sum), Mie-Grueneisen EOS (eq. eos) with C = c0 and
+ *                  an internal-energy equation.  The input rho is then
+ *                  ignored (the density is summed from the positions), the
+ *                  internal energy starts at 0, and artificial viscosity uses
+ *                  c = c0.  Closure 1 cases cannot be batched or run in
+ *                  tangent mode.
+ *  mg_S1, mg_gamma0, mg_a, mg_mu_max   Mie-Grueneisen S1, gamma0, a and the
+ *                  compression cap on mu = rho/rho0 - 1 (1.979, 0.11, 3.0, 0.25) */
 typedef struct hr_params {
     double dx, h_over_dx, Lx, W;
     int32_t wall_layers, end_walls;
@@ -96,6 +108,8 @@ typedef struct hr_params {
     int64_t probe_capacity;
     int32_t diag_every, flags;
     double disk_density;
+    int32_t closure;
+    double mg_S1, mg_gamma0, mg_a, mg_mu_max;
 } hr_params;
 
 /* FP64 diagnostics (Section 2.10 and eq. energy-audit of Section 4.7). */
@@ -151,6 +165,11 @@ int hr_diag_history(hr_case *c, double *host_out, int64_t cap_rows, int64_t *n_r
 /* Current fluid state in ID order (any pointer may be NULL).  xy, vel: cap x 2;
  * rho, p: cap.  cap must be >= n_fluid (else HR_ERANGE).  Synchronises. */
 int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_t cap);
+
+/* Closure 1 only: specific internal energy e [J/kg] and its rate De [W/kg]
+ * of the energy equation, in fluid-ID order (either pointer may be NULL),
+ * cap >= n_fluid.  HR_EINVAL for a closure 0 case.  Synchronises. */
+int hr_get_energy(hr_case *c, float *e, float *de, int64_t cap);
 
 /* Replaces the fluid state (ID order, n == n_fluid), resets t = 0, the step
  * counter, probe history and accumulators, and recomputes a, D rho, X, dt as

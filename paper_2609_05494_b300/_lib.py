@@ -32,11 +32,10 @@ HR_FLAG_TANGENT = 2
 EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",
     "hr_probe_times", "hr_diagnostics", "hr_diag_history", "hr_get_state", "hr_set_state",
-    "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors", "hr_kernel_times",
-    "hr_save_state", "hr_load_state", "hr_tangent_outputs", "hr_neighbor_counts_static",
-    "hr_batch_create",
-    "hr_batch_step", "hr_batch_run", "hr_batch_done", "hr_batch_destroy", "hr_destroy",
-    "hr_status_str",
+    "hr_get_energy", "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors",
+    "hr_kernel_times", "hr_save_state", "hr_load_state", "hr_tangent_outputs",
+    "hr_neighbor_counts_static", "hr_batch_create", "hr_batch_step", "hr_batch_run",
+    "hr_batch_done", "hr_batch_destroy", "hr_destroy", "hr_status_str",
 )
 HR_STATIC_NEIGHBOR_MAX = 1 << 21
 
@@ -60,6 +59,9 @@ class HrParams(C.Structure):
         ("probe_capacity", C.c_int64),
         ("diag_every", C.c_int32), ("flags", C.c_int32),
         ("disk_density", C.c_double),
+        ("closure", C.c_int32),
+        ("mg_S1", C.c_double), ("mg_gamma0", C.c_double), ("mg_a", C.c_double),
+        ("mg_mu_max", C.c_double),
     ]
 
 
@@ -94,6 +96,7 @@ def lib() -> C.CDLL:
     L.hr_diag_history.argtypes = [vp, vp, i64, P(i64)]
     L.hr_get_state.argtypes = [vp, vp, vp, vp, vp, i64]
     L.hr_set_state.argtypes = [vp, vp, vp, vp, i64]
+    L.hr_get_energy.argtypes = [vp, vp, vp, i64]
     L.hr_get_ghosts.argtypes = [vp, vp, vp, vp, vp, i64]
     L.hr_get_scalars.argtypes = [vp, vp, C.c_int]
     L.hr_case_info.argtypes = [vp, vp, C.c_int]

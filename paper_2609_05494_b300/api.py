@@ -176,6 +176,13 @@ class Case:
                                  _ptr(out["p"]), n), "hr_get_state")
         return out
 
+    def energy(self) -> dict:
+        """Internal energy e and its rate De in ID order (closure 1)."""
+        n = self.n
+        out = dict(e=np.empty(n, np.float32), de=np.empty(n, np.float32))
+        check(lib().hr_get_energy(self._h, _ptr(out["e"]), _ptr(out["de"]), n), "hr_get_energy")
+        return out
+
     def set_state(self, xy, vel=None, rho=None) -> int:
         n = self.n
         self.last_status = check(lib().hr_set_state(self._h, _ptr(_f32(xy, (n, 2))),

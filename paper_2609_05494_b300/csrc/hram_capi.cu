@@ -64,9 +64,16 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Consts K, Bufs B,
             v[1] = K.m * u.y;
             v[2] = 0.5f * K.m * v2;
             v[3] = -K.m * (K.gx * r.x + K.gy * r.y);
-            v[4] = K.m * (K.B / K.rho0) * tait_energy_scaled(K, d);
+            if (K.closure == 1) {
+                // the internal energy of the energy equation
+                const float e = B.st_D[i].y;
+                v[4] = K.m * e;
+                v[7] = v[8] = mg_p(K, d, e);
+            } else {
+                v[4] = K.m * (K.B / K.rho0) * tait_energy_scaled(K, d);
+                v[7] = v[8] = tait_p(K, d);
+            }
             v[5] = v[6] = K.rho0 * (1.0f + d);
-            v[7] = v[8] = tait_p(K, d);
             v[9] = sqrtf(v2);
             v[10] = 1.0f;
             const float dx = r.x - B.S->xc_f, dy = r.y - B.S->yc_f;
@@ -132,7 +139,18 @@ __global__ void k_unsort(Consts K, Bufs B, float2 *xy, float2 *vel, float *rho, 
     xy[id] = B.s_pos[i];
     vel[id] = B.st_vel[i];
     rho[id] = K.rho0 * (1.0f + d);
-    p[id] = tait_p(K, d);
+    p[id] = K.closure == 1 ? mg_p(K, d, B.st_D[i].y) : tait_p(K, d);
+}
+
+// Sorted internal energy and its rate -> fluid-ID order (closure 1).
+__global__ void k_unsort_energy(Consts K, Bufs B, float *e, float *de)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    const int id = B.s_id[i];
+    const float2 D = B.st_D[i];
+    e[id] = D.y;
+    de[id] = D.x;
 }
 
 // Debug neighbour enumeration with the same candidate loops and predicate
@@ -328,6 +346,12 @@ int validate(const hr_params *P, long long nf)
     if (P->cell_factor < 1.0) return HR_EINVAL;
     // tangent mode: fixed time step (smooth in c0) and a prescribed motion
     if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
+    if (P->closure < 0 || P->closure > 1) return HR_EINVAL;
+    if (P->closure == 1) {
+        if ((P->flags & HR_FLAG_TANGENT) || !(P->mg_mu_max > 0)) return HR_EINVAL;
+        // the Hugoniot denominator 1 - (S1 - 1) mu must stay positive up to the cap
+        if (!((P->mg_S1 - 1.0) * P->mg_mu_max < 1.0)) return HR_EINVAL;
+    }
     return HR_OK;
 }
 
@@ -485,6 +509,19 @@ void make_consts(hr_case *c)
     c->tpass_blocks = (int)((c->nf + kTPassThreads - 1) / kTPassThreads);
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
+    K.closure = P.closure;
+    const double sd = 10.0 / (7.0 * M_PI * h * h);
+    K.cub_sd = (float)sd;
+    K.cub_Fc = (float)(sd / (h * h));
+    K.inv_h = (float)(1.0 / h);
+    K.self_w = (float)(P.dx * P.dx * sd);
+    K.c_av = (float)(-P.alpha * h * P.c0);
+    K.mg_K = (float)(P.rho0 * P.c0 * P.c0);
+    K.mg_k1 = (float)(1.0 - 0.5 * P.mg_gamma0);
+    K.mg_s1m1 = (float)(P.mg_S1 - 1.0);
+    K.mg_g0 = (float)P.mg_gamma0;
+    K.mg_a = (float)P.mg_a;
+    K.mg_mu_max = (float)P.mg_mu_max;
 }
 
 struct Offsets {
@@ -493,6 +530,7 @@ struct Offsets {
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
         probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
         fin_part, fin_vmax, fin_npen, fin_ticket;
+    size_t s_ex;  // closure 1 only
     // tangent arrays (zero-sized unless HR_FLAG_TANGENT)
     size_t t_begin, t_s_pos, t_s_vel, t_s_aux, t_s_rd, t_st_vel, t_st_rho, t_st_a, t_st_D, t_st_X,
         t_u_pos, t_u_vel, t_g_vel, t_g_aux, t_perm, t_part, t_sc, t_end;
@@ -551,6 +589,7 @@ Offsets plan(const hr_case *c)
     const long long dcap = c->P.diag_every > 0 ? 4096 : 1;
     o.diag_hist = L.add((size_t)dcap * kDiagFields * 8);
     o.io = L.add(n * 6 * 4);
+    o.s_ex = L.add(c->P.closure == 1 ? n * 16 : 0);
     const size_t tn = (c->P.flags & HR_FLAG_TANGENT) ? n * kDir : 0;
     const size_t tg = (c->P.flags & HR_FLAG_TANGENT) ? ng * kDir : 0;
     const bool tm = (c->P.flags & HR_FLAG_TANGENT) != 0;
@@ -632,6 +671,7 @@ void bind(hr_case *c, const Offsets &o)
     c->diag_cap = c->P.diag_every > 0 ? 4096 : 1;
     c->io = at<float>(w, o.io);
     c->tangent = (c->P.flags & HR_FLAG_TANGENT) != 0;
+    B.s_ex = c->P.closure == 1 ? at<float4>(w, o.s_ex) : nullptr;
     B.perm_dst = nullptr;
     if (c->tangent) {
         TBufs &T = c->T;
@@ -693,17 +733,27 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     k_scan_tiles<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
-    k_rank_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    const bool paper = K.closure == 1;
+    if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    else k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
     if (side) CK(cudaStreamWaitEvent(s, c->join, 0));
-    k_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+    if (paper) {
+        // closure 1: the summed density needs the disk ghosts at t^{n+1}
+        k_density<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+        k_ghost<1><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+    } else {
+        k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+    }
     if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
-    k_pass<<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    if (paper) k_pass<1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-    k_finalize<<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    if (paper) k_finalize<1><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    else k_finalize<0><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_finalize<<<1, 256, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
@@ -1051,6 +1101,20 @@ int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_
     return st;
 }
 
+int hr_get_energy(hr_case *c, float *e, float *de, int64_t cap)
+{
+    if (!c || c->K.closure != 1) return HR_EINVAL;
+    if (cap < c->nf) return HR_ERANGE;
+    const size_t n = (size_t)c->nf;
+    float *de_ = c->io, *dd = c->io + n;
+    k_unsort_energy<<<c->drift_blocks, 256, 0, c->stream>>>(c->K, c->B, de_, dd);
+    const int st = device_status(c);
+    if (st < 0 && st != HR_ENAN) return st;
+    if (e && cudaMemcpy(e, de_, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    if (de && cudaMemcpy(de, dd, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return HR_ECUDA;
+    return st;
+}
+
 int hr_set_state(hr_case *c, const float *xy, const float *vel, const float *rho, int64_t n)
 {
     if (!c || !xy || n != c->nf) return HR_EINVAL;
@@ -1391,7 +1455,8 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
         return code;
     };
     for (int k = 0; k < n_cases; ++k) {
-        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent) return fail(HR_EINVAL);
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->K.closure != 0)
+            return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }
     b->stream = (cudaStream_t)cuda_stream;

@@ -70,6 +70,13 @@ struct Consts {
     float probe_x[kMaxProbes], probe_y[kMaxProbes];
     long long probe_cap;
     int n_pass_blocks, n_ghost_blocks;
+    // closure 1 (the paper's): cubic B-spline, summation density,
+    // Mie-Grueneisen EOS with the internal-energy equation
+    int closure;
+    float cub_sd, cub_Fc, inv_h;   // sigma = 10/(7 pi h^2), sigma/h^2, 1/h
+    float self_w;                  // (m / rho0) W(0): a particle's own share of its density
+    float c_av;                    // -alpha h C: the artificial-viscosity factor of every particle
+    float mg_K, mg_k1, mg_s1m1, mg_g0, mg_a, mg_mu_max;  // rho0 C^2, 1 - gamma0/2, S1 - 1, gamma0, a, cap
 };
 
 // Device-resident scalars of the case.
@@ -122,6 +129,7 @@ struct Bufs {
     int *tile_sum;
     int *perm_tmp;   // fluid IDs in provisional cell order
     int *perm_dst;   // previous slot -> slot of this step (tangent mode only, else null)
+    float4 *s_ex;    // closure 1: {a^n, e^n, De^n} in this step's cell order (else null)
     // wall ghosts (static, cell order) and disk ghosts
     float2 *gw_pos;
     float2 *gw_nrm;
@@ -212,6 +220,65 @@ __device__ __forceinline__ float4 eos_record(const Consts &K, float d)
 __device__ __forceinline__ float band(const Consts &K, float d)
 {
     return fminf(fmaxf(d, K.d_lo), K.d_hi);
+}
+
+// Cubic B-spline of the paper (eq. cubic-kernel), q = r/h:
+//   W = sigma (1 - 3/2 q^2 + 3/4 q^3) for q < 1, sigma (2 - q)^3 / 4 for q >= 1,
+// and F = (dW/dr)/r = sigma/h^2 (-3 + 9/4 q), resp. -3/4 sigma/h^2 (2 - q)^2 / q.
+__device__ __forceinline__ float cubic_w(const Consts &K, float r)
+{
+    const float q = r * K.inv_h;
+    const float u = fmaxf(2.0f - q, 0.0f);
+    const float inner = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
+    return K.cub_sd * (q < 1.0f ? inner : 0.25f * u * u * u);
+}
+
+__device__ __forceinline__ float cubic_F(const Consts &K, float r)
+{
+    const float q = r * K.inv_h;
+    const float u = fmaxf(2.0f - q, 0.0f);
+    return K.cub_Fc * (q < 1.0f ? fmaf(2.25f, q, -3.0f) : -0.75f * u * u / q);
+}
+
+// The closure's smoothing kernel W(r): Wendland C2 (closure 0) or the cubic
+// B-spline (closure 1).
+template <int CL>
+__device__ __forceinline__ float kernel_w(const Consts &K, float r)
+{
+    if constexpr (CL == 1) {
+        return cubic_w(K, r);
+    } else {
+        const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+        const float t2 = t * t;
+        return K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+    }
+}
+
+// Mie-Grueneisen pressure (eq. eos) of the deviation d = mu and the specific
+// internal energy e, with the compression cap mu <= mu_max applied to the
+// state and the cavitation cutoff.
+__device__ __forceinline__ float mg_p(const Consts &K, float d, float e)
+{
+    const float mu = fminf(d, K.mg_mu_max);
+    const float rho = fmaf(K.rho0, mu, K.rho0);
+    float p;
+    if (mu >= 0.0f) {
+        const float den = fmaf(-K.mg_s1m1, mu, 1.0f);
+        p = K.mg_K * mu * fmaf(K.mg_k1, mu, 1.0f) / (den * den) +
+            fmaf(K.mg_a, mu, K.mg_g0) * rho * e;
+    } else {
+        p = fmaf(K.mg_K, mu, K.mg_g0 * rho * e);
+    }
+    return fmaxf(p, K.p_cav);
+}
+
+// {d, p, p / rho^2, e} of closure 1 (its artificial-viscosity factor is the
+// constant c_av, so the fourth slot carries the energy the pressure used).
+__device__ __forceinline__ float4 mg_record(const Consts &K, float d, float e)
+{
+    const float p = mg_p(K, d, e);
+    const float rho = K.rho0 * (1.0f + d);
+    return make_float4(d, p, p / (rho * rho), e);
 }
 
 template <typename T>
@@ -522,9 +589,12 @@ __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int
 }
 
 // Stable order inside a cell: rank by fluid ID among the cell's members.
-// Then the reorder into the SoA arrays of this step, with the predicted
-// density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n - D^{n-1})))
-// and its Tait pressure.
+// Then the reorder into the SoA arrays of this step.  Closure 0: with the
+// predicted density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n -
+// D^{n-1}))) and its Tait pressure.  Closure 1: with the predicted velocity
+// v* = v^{n+1/2} + dt/2 a^n that the pass sees, and {a^n, e^n, De^n} for the
+// closing kick (the density comes from k_density).
+template <int CL>
 __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     const int i = bx * blockDim.x + threadIdx.x;
@@ -538,6 +608,21 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     const int dst = cs + rank;
     const float d = B.st_rho[i];
     const float2 D = B.st_D[i];
+    if constexpr (CL == 1) {
+        const float2 a = B.st_a[i];
+        float2 v = B.u_vel[i];
+        if (key != K.ncell) {
+            const float hdt = prime ? 0.0f : 0.5f * B.S->dt_f;
+            v.x = fmaf(hdt, a.x, v.x);
+            v.y = fmaf(hdt, a.y, v.y);
+        }
+        B.s_pos[dst] = B.u_pos[i];
+        B.s_vel[dst] = v;
+        B.s_ex[dst] = make_float4(a.x, a.y, D.y, D.x);
+        B.s_rd[dst] = make_float2(d, D.x);
+        B.s_id[dst] = id;
+        return;
+    }
     float dp = d;
     if (key != K.ncell) {
         const float dt = prime ? 0.0f : B.S->dt_f;
@@ -552,6 +637,57 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     if (B.perm_dst) B.perm_dst[i] = dst;
 }
 
+// ------------------------------------- closure 1: summation density
+
+// rho_i = sum_j m_j W_ij over the particle itself, its fluid neighbours and
+// the wall and disk ghosts (eq. density-sum; the ghosts complete the sum at
+// a boundary), in units of the deviation d = rho/rho0 - 1, then the band.
+// The pressure uses the predicted energy e* = e^n + dt De^n.  A particle
+// outside the box keeps its density and energy.
+__device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+{
+    const int i = bx * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    const float2 ri = B.s_pos[i];
+    const float4 ex = B.s_ex[i];
+    float d, e;
+    if (outside_box(K, ri.x, ri.y)) {
+        d = B.s_rd[i].x;
+        e = ex.z;
+    } else {
+        auto w_at = [&](float x, float y) {
+            const float dx = ri.x - x, dy = ri.y - y;
+            return cubic_w(K, sqrtf(fmaf(dx, dx, dy * dy)));
+        };
+        float S = K.self_w - 1.0f;
+        const int c = cell_of(K, ri.x, ri.y);
+        for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+            const float2 rj = __ldg(&B.s_pos[j]);
+            if (j == i || !in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) return;
+            S = fmaf(K.m_over_rho0, w_at(rj.x, rj.y), S);
+        });
+        if (K.nw > 0) {
+            const float mw = K.m_over_rho0 * K.wall_over_m;
+            for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                const float2 rg = __ldg(&B.gw_pos[k]);
+                if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) S = fmaf(mw, w_at(rg.x, rg.y), S);
+            });
+        }
+        if (K.ng > 0 && near_disk(K, ri.x, ri.y, B.S->xc_f, B.S->yc_f)) {
+            const float md = K.m_over_rho0 * K.disk_over_m;
+            for (int k = 0; k < K.ng; ++k) {
+                const float2 rg = B.gd_pos[k];
+                if (outside_box(K, rg.x, rg.y) || !in_support(ri.x, ri.y, rg.x, rg.y, K.s2))
+                    continue;
+                S = fmaf(md, w_at(rg.x, rg.y), S);
+            }
+        }
+        d = band(K, S);
+        e = fmaf(prime ? 0.0f : B.S->dt_f, ex.w, ex.z);
+    }
+    B.s_aux[i] = mg_record(K, d, e);
+}
+
 // ------------------------------------------------------- a4: ghosts G
 
 // Adami extrapolation (eqs. adami-p, adami-v) for wall ghosts [0, nw) and
@@ -560,6 +696,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
 //   rho_g = rho0 (1 + p_g / (rho0 c0^2)),  v_g = 2 v_w - S_v / S_W.
 // One warp per ghost: the lanes split the stencil's candidates, then the six
 // Shepard sums are reduced across the warp.
+template <int CL>
 __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ float red[kGhostWarps];
@@ -583,10 +720,7 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
                     const float2 rj = __ldg(&B.s_pos[j]);
                     if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
                     const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
-                    const float r = sqrtf(fmaf(dx, dx, dy2 * dy2));
-                    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
-                    const float t2 = t * t;
-                    const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+                    const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy2 * dy2)));
                     const float4 aux = __ldg(&B.s_aux[j]);
                     const float2 vj = __ldg(&B.s_vel[j]);
                     const float rw = (1.0f + aux.x) * W;
@@ -614,10 +748,11 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
             pg = fmaxf(pg, K.p_cav);
             const float dg = pg * K.inv_rho0c02;
             const float rho = K.rho0 * (1.0f + dg);
-            aux = make_float4(dg, pg, pg / (rho * rho), -K.alpha_h * sound_speed(K, dg));
+            aux = make_float4(dg, pg, pg / (rho * rho),
+                              CL == 1 ? 0.0f : -K.alpha_h * sound_speed(K, dg));
             vg = make_float2(2.0f * vwx - Svx * inv, -Svy * inv);
         } else {
-            aux = make_float4(0.0f, 0.0f, 0.0f, -K.alpha_h * K.c0);
+            aux = make_float4(0.0f, 0.0f, 0.0f, CL == 1 ? 0.0f : -K.alpha_h * K.c0);
             vg = make_float2(vwx, 0.0f);
         }
         if (lane == 0) {
@@ -652,6 +787,10 @@ struct Acc {
 // acceleration contribution of j on i per unit mass mj.  I.c and cj hold
 // -alpha h c, so Pi_ij = (c'_i + c'_j) min(v_ij . r_ij, 0) / ((r^2 + eta^2 h^2)
 // (rho_i + rho_j)) is -alpha cbar mu / rhobar under approach and 0 otherwise.
+// Closure 0 accumulates the continuity sum in A.dr; closure 1 the energy
+// equation's sum (P_i + P_j + Pi_ij) v_ij . m_j grad_i W_ij (halved and
+// scaled by the fluid mass in the epilogue).
+template <int CL>
 __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float xj, float yj,
                                              float vxj, float vyj, float rhoj, float Pj,
                                              float cj, float mj, bool xsph, Acc &A)
@@ -659,16 +798,22 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     const float dx = I.x - xj, dy = I.y - yj;
     const float r2 = fmaf(dx, dx, dy * dy);
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
-    const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
-    const float t3 = t * t * t;
-    const float F = mj * K.Fc * t3;                     // m_j grad_i W = F r_ij
+    float t = 0.0f, t3 = 0.0f, F;
+    if constexpr (CL == 1) {
+        F = mj * cubic_F(K, r);
+    } else {
+        t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
+        t3 = t * t * t;
+        F = mj * K.Fc * t3;                             // m_j grad_i W = F r_ij
+    }
     const float vx = I.vx - vxj, vy = I.vy - vyj;
     const float vr = fmaf(vx, dx, vy * dy);
-    A.dr = fmaf(F, vr, A.dr);                           // continuity
+    if constexpr (CL == 0) A.dr = fmaf(F, vr, A.dr);   // continuity
     const float e = r2 + K.eh2;
     const float inv = __fdividef(1.0f, e * (I.rho + rhoj));
     const float Pi_ij = (I.c + cj) * fminf(vr, 0.0f) * inv;
     const float PF = (I.P + Pj + Pi_ij) * F;
+    if constexpr (CL == 1) A.dr = fmaf(PF, vr, A.dr);  // internal energy
     const float lam = K.nu4 * F * r2 * inv;             // laminar
     const float fx = fmaf(-PF, dx, lam * vx);
     const float fy = fmaf(-PF, dy, lam * vy);
@@ -679,7 +824,9 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     A.avy = fmaf(-av, dy, A.avy);
     if (xsph) {
         // -(m_j / rhobar) W = -2 W / (rho_i + rho_j) (mj = 1)
-        const float wx = K.m2Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f) * (inv * e);
+        float wx;
+        if constexpr (CL == 1) wx = -2.0f * cubic_w(K, r) * (inv * e);
+        else wx = K.m2Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f) * (inv * e);
         A.Xx = fmaf(wx, vx, A.Xx);
         A.Xy = fmaf(wx, vy, A.Xy);
     }
@@ -711,6 +858,7 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
 // density and the closing half kick.  Block partials of the ghost forces,
 // the dissipation rate and max |v| are reduced in FP32 per warp and in FP64
 // per block.
+template <int CL>
 __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     __shared__ float red[kPassThreads / 32][5];
@@ -730,17 +878,18 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
             B.st_vel[i] = vi;
             B.st_rho[i] = rd.x;
             B.st_a[i] = make_float2(0.f, 0.f);
-            B.st_D[i] = make_float2(0.f, 0.f);
+            B.st_D[i] = make_float2(0.f, CL == 1 ? B.s_ex[i].z : 0.f);
             B.st_X[i] = make_float2(0.f, 0.f);
         } else {
-            const Self I{ri.x, ri.y, vi.x, vi.y, fmaf(K.rho0, ai.x, K.rho0), ai.z, ai.w};
+            const float ci = CL == 1 ? K.c_av : ai.w;
+            const Self I{ri.x, ri.y, vi.x, vi.y, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
             Acc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             auto fluid_pair = [&](int j) {
                 const float2 rj = __ldg(&B.s_pos[j]);
                 const float2 vj = __ldg(&B.s_vel[j]);
                 const float4 aj = __ldg(&B.s_aux[j]);
-                pair_terms(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z, aj.w,
-                           1.0f, true, A);
+                pair_terms<CL>(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                               CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
             };
             const int c = cell_of(K, ri.x, ri.y);
             int base0, base1, base2;
@@ -796,9 +945,10 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                     if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
                     const float4 ag = B.g_aux[k];
                     const float2 vg = B.g_vel[k];
-                    const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                fmaf(K.rho0, ag.x, K.rho0), ag.z, ag.w,
-                                                K.wall_over_m, false, A);
+                    const float2 f = pair_terms<CL>(K, I, rg.x, rg.y, vg.x, vg.y,
+                                                    fmaf(K.rho0, ag.x, K.rho0), ag.z,
+                                                    CL == 1 ? K.c_av : ag.w, K.wall_over_m,
+                                                    false, A);
                     if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
                         const float2 e = __ldg(&B.gw_nrm[k]);
                         fw -= f.x * e.x + f.y * e.y;
@@ -815,9 +965,10 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                         if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
                         const float4 ag = B.g_aux[K.nw + k];
                         const float2 vg = B.g_vel[K.nw + k];
-                        const float2 f = pair_terms(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                    fmaf(K.rho0, ag.x, K.rho0), ag.z, ag.w,
-                                                    K.disk_over_m, false, A);
+                        const float2 f = pair_terms<CL>(K, I, rg.x, rg.y, vg.x, vg.y,
+                                                        fmaf(K.rho0, ag.x, K.rho0), ag.z,
+                                                        CL == 1 ? K.c_av : ag.w, K.disk_over_m,
+                                                        false, A);
                         fdx += f.x;
                         fdy += f.y;
                     }
@@ -825,17 +976,32 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                     npen = ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
                 }
             }
-            // epilogue: the fluid mass, corrected density, closing half kick (T)
             const float ax = fmaf(K.m, A.ax, K.gx), ay = fmaf(K.m, A.ay, K.gy);
-            const float Dd = A.dr * K.m_over_rho0;
-            const float dnew = band(K, fmaf(dt, Dd, rd.x));
-            const float2 vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
-            if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
-                atomicOr(&B.S->status, ST_NAN);
+            float2 vnew;
+            if constexpr (CL == 1) {
+                // closing kick from the predicted velocity, v^{n+1} = v* +
+                // dt/2 (a^{n+1} - a^n); energy e^{n+1} = e^n + dt/2 (De^n + De^{n+1})
+                const float4 ex = B.s_ex[i];
+                const float De = 0.5f * K.m * A.dr;
+                const float hdt = 0.5f * dt;
+                vnew = make_float2(fmaf(hdt, ax - ex.x, vi.x), fmaf(hdt, ay - ex.y, vi.y));
+                const float enew = fmaf(hdt, ex.w + De, ex.z);
+                if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(enew))
+                    atomicOr(&B.S->status, ST_NAN);
+                B.st_rho[i] = ai.x;
+                B.st_D[i] = make_float2(De, enew);
+            } else {
+                // epilogue: the fluid mass, corrected density, closing half kick (T)
+                const float Dd = A.dr * K.m_over_rho0;
+                const float dnew = band(K, fmaf(dt, Dd, rd.x));
+                vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
+                if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
+                    atomicOr(&B.S->status, ST_NAN);
+                B.st_rho[i] = dnew;
+                B.st_D[i] = make_float2(Dd, prime ? Dd : rd.y);
+            }
             B.st_vel[i] = vnew;
-            B.st_rho[i] = dnew;
             B.st_a[i] = make_float2(ax, ay);
-            B.st_D[i] = make_float2(Dd, prime ? Dd : rd.y);
             B.st_X[i] = make_float2(K.m * A.Xx, K.m * A.Xy);
             vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
             diss = -K.m * K.m * (vi.x * A.avx + vi.y * A.avy);
@@ -880,6 +1046,7 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
 // force kept, cutoff applied) at (px, py) over the end-of-step fluid, by one
 // warp.  The three stencil rows are flattened into one candidate range so
 // the lanes' loads go out together.
+template <int CL>
 __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, float px, float py)
 {
     const int lane = threadIdx.x & 31;
@@ -896,13 +1063,11 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
             const float d = B.st_rho[j];
             if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
             const float dx = px - rj.x, dy = py - rj.y;
-            const float r = sqrtf(fmaf(dx, dx, dy * dy));
-            const float t = fmaxf(fmaf(-r, K.half_inv_h, 1.0f), 0.0f);
-            const float t2 = t * t;
-            const float W = K.Wc * t2 * t2 * fmaf(r, K.two_inv_h, 1.0f);
+            const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy * dy)));
             const float rw = (1.0f + d) * W;
+            const float pj = CL == 1 ? mg_p(K, d, B.st_D[j].y) : tait_p(K, d);
             SW += W;
-            Sp = fmaf(tait_p(K, d), W, Sp);
+            Sp = fmaf(pj, W, Sp);
             Srx = fmaf(rw, dx, Srx);
             Sry = fmaf(rw, dy, Sry);
         }
@@ -921,6 +1086,7 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 // Block q < n_probes first samples wall probe q (a7) into probe_now[q].  The
 // sums are compensated FP32 (two-float) in a fixed tree order, converted to
 // FP64 once at the end.
+template <int CL>
 __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     constexpr int NW = kFinalizeThreads / 32;
@@ -936,7 +1102,7 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = nbx;
     if (!prime && (int)bx < K.n_probes && w == 0) {
-        const float pv = probe_value(K, B, K.probe_x[bx], K.probe_y[bx]);
+        const float pv = probe_value<CL>(K, B, K.probe_x[bx], K.probe_y[bx]);
         if (lane == 0) B.probe_now[bx] = pv;
     }
     // reduce one (value per thread) set of four sums, max and count over the
@@ -1108,24 +1274,33 @@ __global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
     b_slot(K, B, blockIdx.x, gridDim.x);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prime)
 {
-    b_rank_scatter(K, B, blockIdx.x, gridDim.x, prime);
+    b_rank_scatter<CL>(K, B, blockIdx.x, gridDim.x, prime);
 }
 
+__global__ void __launch_bounds__(256) k_density(Consts K, Bufs B, int prime)
+{
+    b_density(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+template <int CL>
 __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
 {
-    b_ghost(K, B, blockIdx.x, gridDim.x);
+    b_ghost<CL>(K, B, blockIdx.x, gridDim.x);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
 {
-    b_pass(K, B, blockIdx.x, gridDim.x, prime);
+    b_pass<CL>(K, B, blockIdx.x, gridDim.x, prime);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
 {
-    b_finalize(K, B, blockIdx.x, gridDim.x, prime);
+    b_finalize<CL>(K, B, blockIdx.x, gridDim.x, prime);
 }
 
 // --------------------------------------------- kernels (a batch of cases)
@@ -1203,7 +1378,7 @@ __global__ void __launch_bounds__(256) kb_rank_scatter(const Consts *Ks, const B
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_rank_scatter(K, B, m.local, m.nlocal, 0);
+    b_rank_scatter<0>(K, B, m.local, m.nlocal, 0);
 }
 
 __global__ void __launch_bounds__(kGhostWarps * 32) kb_ghost(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
@@ -1212,7 +1387,7 @@ __global__ void __launch_bounds__(kGhostWarps * 32) kb_ghost(const Consts *Ks, c
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_ghost(K, B, m.local, m.nlocal);
+    b_ghost<0>(K, B, m.local, m.nlocal);
 }
 
 __global__ void __launch_bounds__(kPassThreads) kb_pass(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
@@ -1221,7 +1396,7 @@ __global__ void __launch_bounds__(kPassThreads) kb_pass(const Consts *Ks, const 
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_pass(K, B, m.local, m.nlocal, 0);
+    b_pass<0>(K, B, m.local, m.nlocal, 0);
 }
 
 __global__ void __launch_bounds__(kFinalizeThreads) kb_finalize(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
@@ -1230,7 +1405,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) kb_finalize(const Consts *Ks
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_finalize(K, B, m.local, m.nlocal, 0);
+    b_finalize<0>(K, B, m.local, m.nlocal, 0);
 }
 
 }  // namespace hr

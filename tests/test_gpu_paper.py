@@ -1,0 +1,162 @@
+"""CUDA path, the paper's closure (closure 1: cubic B-spline, summation
+density, Mie-Grueneisen EOS, internal-energy equation) against the FP64
+oracle on identical seeded inputs, with the gates of the closure-0 parity
+tests: density 1e-5 relative, pressure 1e-5 of max(max |p|, rho0 c0^2),
+positions 1e-6 m, probe histories 1e-3 relative L2 (plus, for weak probes,
+the 1e-5 rho0 c0^2 pressure floor that float32 positions put on a summed
+density)."""
+import numpy as np
+import pytest
+
+import casegen
+import oracle
+from helpers import as64, impact_case, p_scale, perturbed, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2609_05494_b300 import Batch, Case, HramError, _lib  # noqa: E402
+
+
+def paper_case(**kw):
+    q = dict(closure=1, c0=1448.0, alpha=0.03, cfl=0.25, motion=1)
+    q.update(kw)
+    return impact_case(**q)
+
+
+def both(p, xy32, vel=None, rho=None, **kw):
+    return Case(p, xy32, vel, rho, **kw), oracle.OracleCase(p, as64(xy32), as64(vel), as64(rho))
+
+
+def compare_state(p, g, o, dens_rel=1e-5, e_rel=1e-4):
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= dens_rel
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+    eg, eo = g.energy(), o.energy()
+    escale = max(np.abs(eo["e"]).max(), 1e-3)
+    assert np.abs(eg["e"] - eo["e"]).max() <= e_rel * escale
+    dscale = max(np.abs(eo["de"]).max(), 1e-3)
+    assert np.abs(eg["de"] - eo["de"]).max() <= e_rel * dscale
+
+
+def test_prime_summation_density_and_pressure():
+    p, xy = paper_case()
+    g, o = both(p, xy)
+    sg, fo = g.get_state(), o.fluid()
+    # the summed density replaces the given one, on both sides
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-6
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert np.all(g.energy()["e"] == 0.0)
+
+
+@pytest.mark.parametrize("state", ["rest_impact", "perturbed"])
+def test_one_step(state):
+    p, xy = paper_case()
+    vel = None
+    if state == "perturbed":
+        vel, _ = perturbed(p, xy)
+    g, o = both(p, xy, vel)
+    g.step()
+    o.step()
+    compare_state(p, g, o)
+    assert abs(g.scalars()["dt"] / o.scalars()["dt"] - 1.0) <= 1e-6
+
+
+def test_ghosts_after_steps():
+    p, xy = paper_case()
+    g, o = both(p, xy)
+    g.run(5)
+    o.run(5)
+    gg, go = g.ghosts(), o.ghosts()
+    pmax = max(np.abs(go["p"]).max(), 1.0)
+    assert np.abs(gg["p"] - go["p"]).max() <= 1e-5 * max(pmax, p["rho0"] * p["c0"] ** 2)
+    vmax = max(np.abs(go["vel"]).max(), 1.0)
+    assert np.abs(gg["vel"] - go["vel"]).max() <= 1e-4 * vmax
+
+
+def test_probe_history_and_diagnostics_window():
+    p, xy = paper_case()
+    p["probes"] = list(p["probes"]) + [(0.030, 0.0), (0.020, 0.030), (0.060, 0.0)]
+    g, o = both(p, xy)
+    n = p["n_steps"]
+    g.run(n)
+    o.run(n)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    assert pg.shape == po.shape == (n, len(p["probes"]))
+    # Summed density makes the pressure a direct function of the float32
+    # positions: the GPU state carries a pressure floor of about 1e-5 rho0 c0^2
+    # (the one-step gate's pressure scale).  Probes that see the entry shock
+    # (peak > 10 MPa) meet 1e-3 relative L2 outright; every probe meets
+    # 1e-3 relative L2 plus that floor.
+    floor = 1e-5 * p["rho0"] * p["c0"] ** 2
+    strong = 0
+    for k in range(po.shape[1]):
+        err = np.sqrt(np.mean((pg[:, k] - po[:, k]) ** 2))
+        rms = np.sqrt(np.mean(po[:, k] ** 2))
+        assert err <= 1e-3 * rms + floor, k
+        if np.abs(po[:, k]).max() > 1e7:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
+            strong += 1
+    assert strong >= 2
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("KE", "E_el", "W_boundary", "dissipation", "wall_impulse"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-3), k
+    assert dg["n_in"] == do["n_in"]
+
+
+def test_state_moves_with_summation_not_input_density():
+    # closure 1 ignores the density handed in: two uploads that differ only
+    # in rho give bit-identical states
+    p, xy = paper_case(Lx=0.04, W=0.04, x_c0=0.01, v0=100.0)
+    _, rho = perturbed(p, xy)
+    with Case(p, xy) as a, Case(p, xy, rho=rho) as b:
+        a.run(10)
+        b.run(10)
+        sa, sb = a.get_state(), b.get_state()
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), key
+
+
+def test_closure_restrictions():
+    p, xy = paper_case(Lx=0.04, W=0.04)
+    with Case(p, xy) as c:
+        with pytest.raises(HramError) as e:
+            Batch([c], 1e-5)
+        assert e.value.code == _lib.HR_EINVAL
+    q = dict(p)
+    q["dt_mode"] = 1
+    q["motion"] = 0
+    with pytest.raises(HramError):
+        Case(q, xy, tangent=True)
+    r = dict(p)
+    r["mg_mu_max"] = 1.5      # 1 - (S1 - 1) mu would cross zero below the cap
+    with pytest.raises(HramError):
+        Case(r, xy)
+    with Case(dict(p, closure=0), xy) as c0:
+        with pytest.raises(HramError):
+            c0.energy()
+
+
+def test_paper_setup_runs_and_peaks_in_the_papers_range():
+    # the paper's own geometry and closure (750 x 150 mm, dx = 1.5 mm, drag
+    # law, centreline probes PTn / PTf), 40 us of the entry phase.  Magnitude
+    # sanity only: the paper's table gives PTn peaks of 850-894 MPa at
+    # 900 m/s; a planar 2-D run at this resolution is not a parity target.
+    p = casegen.config_paper(900.0)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+    with Case(p, xy) as c:
+        st = c.run(0, 40e-6)
+        assert st >= 0
+        pr = c.probe_pressure()
+        d = c.diagnostics()
+    assert np.all(np.isfinite(pr))
+    ptn = pr[:, 0].max()
+    assert 1e8 < ptn < 3e9
+    assert d["n_in"] == xy.shape[0]
