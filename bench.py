@@ -254,6 +254,36 @@ def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
     return res
 
 
+def paper_event_benchmark(stream):
+    """The paper's own set-up and closure (750 x 150 mm, dx = 1.5 mm, about
+    50,000 particles, cubic spline, summation density, Mie-Grueneisen water,
+    drag law) run through its whole 150 us event, as the paper times it
+    (Section "Speed": about 14 s on a TITAN RTX).  Wall clock from the first
+    step to the synchronised end, with the probes PTn and PTf recorded."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    p = casegen.config_paper(900.0)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+    with torch.cuda.stream(stream):
+        c = Case(p, xy, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = c.run(0, p["t_end"])
+    c.sync()
+    wall = time.perf_counter() - t0
+    steps = int(c.scalars()["step"])
+    pr = c.probe_pressure()
+    c.close()
+    return {"workload": "paper set-up: 750 x 150 mm, dx = 1.5 mm, %d particles, 900 m/s, "
+                        "closure 1, 150 us" % xy.shape[0],
+            "steps": steps, "wall_s": wall, "ms_per_step": 1e3 * wall / steps,
+            "particle_steps_per_s": xy.shape[0] * steps / wall,
+            "ptn_peak_MPa": float(pr[:, 0].max()) * 1e-6,
+            "ptf_peak_MPa": float(pr[:, 1].max()) * 1e-6, "status": st,
+            "paper_wall_s_titan_rtx": 14.0}
+
+
 def cpu_baseline(seconds=15.0, Lx=0.075):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of the
     workload: the first Lx of the channel at the same spacing, from t = 0."""
@@ -315,6 +345,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tangent", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -391,6 +422,7 @@ def main():
     case.close()
     sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
     tangent = None if args.no_tangent else tangent_benchmark(stream, xy, p)
+    paper = None if args.no_paper else paper_event_benchmark(stream)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -431,6 +463,7 @@ def main():
         "kernel_groups_ms": groups,
         "batched_sweep": sweep,
         "tangent": tangent,
+        "paper_event": paper,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

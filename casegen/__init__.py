@@ -173,12 +173,12 @@ def config_paper(v0: float = 900.0) -> dict:
     12.5 mm disk entering on the centreline at v0 with the 5 us ramp and then
     the quadratic drag law (M = 8.01 g, Cd = 0.05, R = 6.25 mm), water with
     C = c0 = 1448 m/s, alpha 0.03, CFL 0.25, and the probes PTn and PTf on the
-    centreline at x = 30 and 105 mm; 250 us of simulated time."""
+    centreline at x = 30 and 105 mm; the 150 us event of the paper's timing."""
     p = base_params()
     p.update(dx=1.5e-3, Lx=0.750, W=0.150, R_disk=6.25e-3, x_c0=-6.25e-3, v0=float(v0),
              motion=1, c0=1448.0, alpha=0.03, cfl=0.25, closure=1)
     p["probes"] = [(0.030, 0.0), (0.105, 0.0)]
-    p["t_end"] = 250e-6
+    p["t_end"] = 150e-6
     return p
 
 
