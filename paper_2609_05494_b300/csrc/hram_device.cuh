@@ -165,6 +165,59 @@ __device__ __forceinline__ bool in_support(float xi, float yi, float xj, float y
     return r2 < s2;
 }
 
+// Packed FP32 pairs: the sm_100-family .f32x2 instructions do two IEEE
+// round-to-nearest operations in one issue slot, each lane bit-identical to
+// the scalar operation (add/sub/mul rounded once, fma rounded once).
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// The neighbour predicate on packed pairs: the same three roundings as
+// in_support (dx, dy; dx^2, dy^2; their sum).
+__device__ __forceinline__ bool in_support2(float2 ri, float2 rj, float s2)
+{
+    const float2 d = p2_sub(ri, rj);
+    const float2 q = p2_mul(d, d);
+    return __fadd_rn(q.x, q.y) < s2;
+}
+
 __device__ __forceinline__ int cell_of(const Consts &K, float x, float y)
 {
     int cx = __float2int_rd(__fmul_rn(__fsub_rn(x, K.x0), K.inv_dc));
@@ -773,11 +826,13 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
 // --------------------------------------------- a5: fused interaction L
 
 struct Self {
-    float x, y, vx, vy, rho, P, c;
+    float2 r, v;
+    float rho, P, c;
 };
 
 struct Acc {
-    float ax, ay, dr, Xx, Xy, avx, avy;
+    float2 a, X, av;
+    float dr;
 };
 
 // One pair (i, j): continuity, momentum with artificial and laminar
@@ -790,12 +845,14 @@ struct Acc {
 // Closure 0 accumulates the continuity sum in A.dr; closure 1 the energy
 // equation's sum (P_i + P_j + Pi_ij) v_ij . m_j grad_i W_ij (halved and
 // scaled by the fluid mass in the epilogue).
+// The x and y halves of the vector terms run as packed pairs.
 template <int CL>
-__device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float xj, float yj,
-                                             float vxj, float vyj, float rhoj, float Pj,
-                                             float cj, float mj, bool xsph, Acc &A)
+__device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, float2 rj, float2 vj,
+                                             float rhoj, float Pj, float cj, float mj, bool xsph,
+                                             Acc &A)
 {
-    const float dx = I.x - xj, dy = I.y - yj;
+    const float2 d = p2_sub(I.r, rj);
+    const float dx = d.x, dy = d.y;
     const float r2 = fmaf(dx, dx, dy * dy);
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     float t = 0.0f, t3 = 0.0f, F;
@@ -806,8 +863,8 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
         t3 = t * t * t;
         F = mj * K.Fc * t3;                             // m_j grad_i W = F r_ij
     }
-    const float vx = I.vx - vxj, vy = I.vy - vyj;
-    const float vr = fmaf(vx, dx, vy * dy);
+    const float2 v = p2_sub(I.v, vj);
+    const float vr = fmaf(v.x, dx, v.y * dy);
     if constexpr (CL == 0) A.dr = fmaf(F, vr, A.dr);   // continuity
     const float e = r2 + K.eh2;
     const float inv = __fdividef(1.0f, e * (I.rho + rhoj));
@@ -815,34 +872,30 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     const float PF = (I.P + Pj + Pi_ij) * F;
     if constexpr (CL == 1) A.dr = fmaf(PF, vr, A.dr);  // internal energy
     const float lam = K.nu4 * F * r2 * inv;             // laminar
-    const float fx = fmaf(-PF, dx, lam * vx);
-    const float fy = fmaf(-PF, dy, lam * vy);
-    A.ax += fx;
-    A.ay += fy;
+    const float2 f = p2_fma(make_float2(-PF, -PF), d, p2_mul(make_float2(lam, lam), v));
+    A.a = p2_add(A.a, f);
     const float av = Pi_ij * F;                         // minus the AV acceleration factor
-    A.avx = fmaf(-av, dx, A.avx);
-    A.avy = fmaf(-av, dy, A.avy);
+    A.av = p2_fma(make_float2(-av, -av), d, A.av);
     if (xsph) {
         // -(m_j / rhobar) W = -2 W / (rho_i + rho_j) (mj = 1)
         float wx;
         if constexpr (CL == 1) wx = -2.0f * cubic_w(K, r) * (inv * e);
         else wx = K.m2Wc * t3 * t * fmaf(r, K.two_inv_h, 1.0f) * (inv * e);
-        A.Xx = fmaf(wx, vx, A.Xx);
-        A.Xy = fmaf(wx, vy, A.Xy);
+        A.X = p2_fma(make_float2(wx, wx), v, A.X);
     }
-    return make_float2(fx, fy);
+    return f;
 }
 
 // Predicate mask of the candidates [base, base + cnt), cnt <= 32.
-__device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float x,
-                                                 float y, float s2)
+__device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float2 ri,
+                                                 float s2)
 {
     unsigned m = 0u;
     const float2 *pp = pos + base;
 #pragma unroll 8
     for (int k = 0; k < cnt; ++k) {
         const float2 rj = __ldg(pp + k);
-        m |= (unsigned)in_support(x, y, rj.x, rj.y, s2) << k;
+        m |= (unsigned)in_support2(ri, rj, s2) << k;
     }
     return m;
 }
@@ -882,13 +935,13 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
             B.st_X[i] = make_float2(0.f, 0.f);
         } else {
             const float ci = CL == 1 ? K.c_av : ai.w;
-            const Self I{ri.x, ri.y, vi.x, vi.y, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
-            Acc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
+            Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
             auto fluid_pair = [&](int j) {
                 const float2 rj = __ldg(&B.s_pos[j]);
                 const float2 vj = __ldg(&B.s_vel[j]);
                 const float4 aj = __ldg(&B.s_aux[j]);
-                pair_terms<CL>(K, I, rj.x, rj.y, vj.x, vj.y, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
                                CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
             };
             const int c = cell_of(K, ri.x, ri.y);
@@ -903,11 +956,10 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                           e2 = B.cell_start[r2 + 2];
                 // rows longer than 32 candidates: chunks evaluated right away
                 auto row_mask = [&](int a, int b) -> unsigned {
-                    if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri.x, ri.y, K.s2);
+                    if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri, K.s2);
 #pragma unroll 1
                     for (int base = a; base < b; base += 32) {
-                        unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri.x, ri.y,
-                                                  K.s2);
+                        unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
                         if (i >= base && i < base + 32) m &= ~(1u << (i - base));
                         while (m) {
                             const int j = base + __ffs(m) - 1;
@@ -945,10 +997,9 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                     if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
                     const float4 ag = B.g_aux[k];
                     const float2 vg = B.g_vel[k];
-                    const float2 f = pair_terms<CL>(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                    fmaf(K.rho0, ag.x, K.rho0), ag.z,
-                                                    CL == 1 ? K.c_av : ag.w, K.wall_over_m,
-                                                    false, A);
+                    const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
+                                                    ag.z, CL == 1 ? K.c_av : ag.w,
+                                                    K.wall_over_m, false, A);
                     if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
                         const float2 e = __ldg(&B.gw_nrm[k]);
                         fw -= f.x * e.x + f.y * e.y;
@@ -965,10 +1016,9 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                         if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
                         const float4 ag = B.g_aux[K.nw + k];
                         const float2 vg = B.g_vel[K.nw + k];
-                        const float2 f = pair_terms<CL>(K, I, rg.x, rg.y, vg.x, vg.y,
-                                                        fmaf(K.rho0, ag.x, K.rho0), ag.z,
-                                                        CL == 1 ? K.c_av : ag.w, K.disk_over_m,
-                                                        false, A);
+                        const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
+                                                        ag.z, CL == 1 ? K.c_av : ag.w,
+                                                        K.disk_over_m, false, A);
                         fdx += f.x;
                         fdy += f.y;
                     }
@@ -976,7 +1026,7 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
                     npen = ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
                 }
             }
-            const float ax = fmaf(K.m, A.ax, K.gx), ay = fmaf(K.m, A.ay, K.gy);
+            const float ax = fmaf(K.m, A.a.x, K.gx), ay = fmaf(K.m, A.a.y, K.gy);
             float2 vnew;
             if constexpr (CL == 1) {
                 // closing kick from the predicted velocity, v^{n+1} = v* +
@@ -1002,9 +1052,9 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
             }
             B.st_vel[i] = vnew;
             B.st_a[i] = make_float2(ax, ay);
-            B.st_X[i] = make_float2(K.m * A.Xx, K.m * A.Xy);
+            B.st_X[i] = make_float2(K.m * A.X.x, K.m * A.X.y);
             vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
-            diss = -K.m * K.m * (vi.x * A.avx + vi.y * A.avy);
+            diss = -K.m * K.m * (vi.x * A.av.x + vi.y * A.av.y);
         }
     }
     // block partials: FP32 within the warp, FP64 across warps (fixed order)
