@@ -543,7 +543,7 @@ Offsets plan(const hr_case *c)
     const size_t n = (size_t)c->nf, ng = (size_t)(c->nw + c->ng), nc = (size_t)K.ncell;
     Layout L;
     Offsets o;
-    o.s_pos = L.add(n * 8);
+    o.s_pos = L.add((n + kPosPad) * 8);  // padded for the predicate's block reads
     o.s_vel = L.add(n * 8);
     o.s_aux = L.add(n * 16);
     o.s_rd = L.add(n * 8);

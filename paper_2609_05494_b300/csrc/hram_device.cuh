@@ -886,16 +886,32 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     return f;
 }
 
-// Predicate mask of the candidates [base, base + cnt), cnt <= 32.
+// Predicate mask of the candidates [base, base + cnt), cnt <= 32, in fixed
+// blocks of kMaskChunk candidates: each block is unrolled with constant bit
+// positions, and the warp's trip count is the largest ceil(cnt / kMaskChunk)
+// of its lanes (rows of 17-24 candidates all take three blocks of 8).  The
+// last block reads up to kMaskChunk - 1 entries past the row; the position
+// array is padded by kPosPad entries so those reads stay inside it, and
+// their bits are masked off.
+#ifndef HR_MASK_CHUNK
+#define HR_MASK_CHUNK 8
+#endif
+constexpr int kMaskChunk = HR_MASK_CHUNK;
+constexpr int kPosPad = 32;
 __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float2 ri,
                                                  float s2)
 {
     unsigned m = 0u;
     const float2 *pp = pos + base;
-#pragma unroll 8
-    for (int k = 0; k < cnt; ++k) {
-        const float2 rj = __ldg(pp + k);
-        m |= (unsigned)in_support2(ri, rj, s2) << k;
+#pragma unroll 1
+    for (int k0 = 0; k0 < cnt; k0 += kMaskChunk) {
+        unsigned sub = 0u;
+#pragma unroll
+        for (int u = 0; u < kMaskChunk; ++u)
+            sub |= (unsigned)in_support2(ri, __ldg(pp + k0 + u), s2) << u;
+        const int rem = cnt - k0;
+        if (rem < kMaskChunk) sub &= (1u << rem) - 1u;
+        m |= sub << k0;
     }
     return m;
 }
