@@ -461,13 +461,40 @@ __device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, flo
 
 // ----------------------------------------------------- a2: drift and key
 
+__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, int prime);
+
 // Opening kick, XSPH drift, wall enforcement and cell key (the predicted
 // density is formed in k_rank_scatter from the same state).  prime = 1
-// evaluates the current state without advancing (dt = 0).
+// evaluates the current state without advancing (dt = 0).  The cell
+// histogram is counted with one atomic per run of equal keys in consecutive
+// lanes: the previous step's cell order keeps most of a warp's particles in
+// a few runs.  (Counting the scan's tile sums the same way was slower: a few
+// dozen tile counters take every warp's atomic and serialise them.)
 __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     const int i = bx * blockDim.x + threadIdx.x;
-    if (i >= K.nf) return;
+    const int key = i < K.nf ? b_drift_one(K, B, i, prime) : -1;
+    const int lane = threadIdx.x & 31;
+    const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;   // lanes 0..lane
+    // runs of equal values in consecutive lanes: head lane and length
+    auto run = [&](int v, int &head, int &len) {
+        const int prev = __shfl_up_sync(0xffffffffu, v, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != v);
+        head = 31 - __clz(heads & upto);
+        const unsigned after = heads & ~upto;
+        len = (after ? __ffs(after) - 1 : 32) - head;
+    };
+    int head, len;
+    run(key, head, len);
+    int slot0 = 0;
+    if (key >= 0 && lane == head) slot0 = atomicAdd(&B.cell_count[key], len);
+    slot0 = __shfl_sync(0xffffffffu, slot0, head);
+    if (key >= 0) B.u_slot[i] = slot0 + (lane - head);
+}
+
+// The per-particle part of b_drift_key; returns the cell key.
+__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, int prime)
+{
     const float dt = prime ? 0.0f : B.S->dt_f;
     float2 r = B.s_pos[i];
     const float2 v = B.st_vel[i];
@@ -504,7 +531,7 @@ __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, cons
     B.u_vel[i] = vh;
     B.u_id[i] = B.s_id[i];
     B.u_key[i] = key;
-    B.u_slot[i] = atomicAdd(&B.cell_count[key], 1);
+    return key;
 }
 
 // ---------------------------------------------------- a3: counting sort
@@ -633,6 +660,7 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
 }
 
+// Provisional scatter of the IDs by (cell start + atomic slot).
 __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     const int i = bx * blockDim.x + threadIdx.x;
