@@ -369,8 +369,11 @@ def main():
     p, xy = workload(args.dx)
     n = xy.shape[0]
     stream = torch.cuda.Stream()
+    # the headline graph carries no timing events (each event node in a graph
+    # costs about 2.6 us of step time); kernel durations come from a second
+    # case whose graph records them (HR_FLAG_TIMING), run right after
     with torch.cuda.stream(stream):
-        case = Case(p, xy, stream=stream, timing=True, probe_capacity=args.steps + args.warmup + 8)
+        case = Case(p, xy, stream=stream, probe_capacity=args.steps + args.warmup + 8)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # pairs per step (for the flop count), from the neighbour lists of the start state
@@ -382,22 +385,19 @@ def main():
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    pass_ms = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)               # write 256 MB > L2 between timed steps
-                ev[k][0].record(stream)
-                case.step()
-                ev[k][1].record(stream)
-            stream.synchronize()
-            pass_ms.append(case.kernel_times()["pass"])
-        torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.__enter__()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)               # write 256 MB > L2 between timed steps
+            ev[k][0].record(stream)
+            case.step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    groups = case.kernel_times()
     total_ms = max_over_ranks(total_ms, dist)
     if dist:
         dist.barrier()
@@ -420,6 +420,28 @@ def main():
     d2h = probes.nbytes + sum(v.nbytes for v in final.values())
 
     case.close()
+
+    # kernel durations: the same workload, graph with timing events, the same
+    # flushed-L2 steps; k_pass's mean duration feeds the roofline
+    with torch.cuda.stream(stream):
+        tcase = Case(p, xy, stream=stream, timing=True, probe_capacity=args.steps + args.warmup + 8)
+    tcase.run(args.warmup)
+    tcase.sync()
+    k_timed = min(args.steps, 100)
+    pass_ms, gsum = [], {}
+    for k in range(k_timed):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            tcase.step()
+        stream.synchronize()
+        kt = tcase.kernel_times()
+        pass_ms.append(kt["pass"])
+        for g, v in kt.items():
+            gsum[g] = gsum.get(g, 0.0) + v
+    groups = {g: v / k_timed for g, v in gsum.items()}
+    groups["steps"] = k_timed
+    tcase.close()
+    clk.__exit__(None, None, None)
     sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
     tangent = None if args.no_tangent else tangent_benchmark(stream, xy, p)
     paper = None if args.no_paper else paper_event_benchmark(stream)
@@ -444,6 +466,8 @@ def main():
                                "particles, disk 5 mm at 900 m/s, impact phase from t = 0" % n,
                    "particles": n, "dx_mm": args.dx * 1e3, "parallelism": "replicas" if world > 1
                    else "single", "l2": "256 MB buffer written between timed steps",
+                   "timing": "step graph without timing events; kernel durations from a "
+                             "second run of the workload with in-graph CUDA events",
                    "status": status},
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT,
