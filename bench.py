@@ -254,6 +254,68 @@ def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
     return res
 
 
+def scaling_benchmark(stream, flush, dxs=(1e-3, 5e-4, 2.5e-4, 2e-4, 1e-4), steps=30, warmup=5):
+    """The scaling sweep of the same channel at spacing dx (45,000 to 4.5M
+    particles): ms per step (L2 flushed between steps, graph without timing
+    events), particle-steps/s, and the algorithmic HBM rate of the whole step
+    (40 B per particle-step)."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    out = []
+    for dx in dxs:
+        p, xy = workload(dx)
+        with torch.cuda.stream(stream):
+            c = Case(p, xy, stream=stream, probe_capacity=steps + warmup + 8)
+        c.run(warmup)
+        c.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                c.step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        n = xy.shape[0]
+        out.append({"dx_mm": dx * 1e3, "particles": n, "ms_per_step": ms,
+                    "particle_steps_per_s": n / (ms * 1e-3),
+                    "alg_hbm_gbs": ALG_BYTES_PER_PARTICLE * n / (ms * 1e-3) / 1e9,
+                    "status": c.sync()})
+        c.close()
+    return out
+
+
+def production_benchmark(stream):
+    """The production runs: 300 x 150 mm at dx = 0.5 mm (180,000 particles),
+    1 ms of simulated time at v0 = 900 and 600 m/s; wall clock of the whole
+    run (hr_run to t_end, synchronised) and the four wall probes' peaks."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    out = []
+    for v0 in (900.0, 600.0):
+        p = casegen.config_production(v0)
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                                   disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+        with torch.cuda.stream(stream):
+            c = Case(p, xy, stream=stream, probe_capacity=1 << 16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = c.run(0, p["t_end"])
+        c.sync()
+        wall = time.perf_counter() - t0
+        steps = int(c.scalars()["step"])
+        pr = c.probe_pressure()
+        d = c.diagnostics()
+        c.close()
+        out.append({"v0": v0, "particles": int(xy.shape[0]), "t_end_s": p["t_end"],
+                    "steps": steps, "wall_s": wall, "ms_per_step": 1e3 * wall / steps,
+                    "probe_peaks_MPa": [float(x) * 1e-6 for x in pr.max(axis=0)],
+                    "wall_impulse": d["wall_impulse"], "status": st})
+    return out
+
+
 def paper_event_benchmark(stream):
     """The paper's own set-up and closure (750 x 150 mm, dx = 1.5 mm, about
     50,000 particles, cubic spline, summation density, Mie-Grueneisen water,
@@ -346,6 +408,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tangent", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--no-scaling", action="store_true")
+    ap.add_argument("--no-production", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -445,6 +509,8 @@ def main():
     sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
     tangent = None if args.no_tangent else tangent_benchmark(stream, xy, p)
     paper = None if args.no_paper else paper_event_benchmark(stream)
+    scaling = None if args.no_scaling else scaling_benchmark(stream, flush)
+    production = None if args.no_production else production_benchmark(stream)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -488,6 +554,8 @@ def main():
         "batched_sweep": sweep,
         "tangent": tangent,
         "paper_event": paper,
+        "size_sweep": scaling,
+        "production": production,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

@@ -140,3 +140,26 @@ def test_unsupported_set_ups_are_refused():
             t.save(path)
             with pytest.raises(HramError):
                 t.load(path)
+
+
+def test_adjoint_workload_gradients_within_two_percent():
+    # the 22,500-particle fixed-dt workload (150 x 150 mm, dx = 1 mm, 400
+    # steps): every derivative against central differences of the FP64
+    # oracle with relative step 1e-4, within 2 % (the workload's own bar)
+    p = casegen.config_adjoint()
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+    n = int(p["n_steps"])
+    out, _ = gpu_tangent(p, xy, n)
+    pr, J = oracle_outputs(p, xy, n)
+    assert out["peak"] == pytest.approx(pr.max(), rel=1e-3)
+    assert out["impulse"] == pytest.approx(J, rel=1e-3)
+    for k, name in enumerate(TANGENT_PARAMS):
+        hi, lo = dict(p), dict(p)
+        hi[name] = p[name] * (1.0 + 1e-4)
+        lo[name] = p[name] * (1.0 - 1e-4)
+        ph, jh = oracle_outputs(hi, xy, n)
+        pl, jl = oracle_outputs(lo, xy, n)
+        dP, dJ = (ph.max() - pl.max()) / 2e-4, (jh - jl) / 2e-4
+        assert abs(out["dpeak"][k] - dP) <= 0.02 * abs(dP) + 1e-6 * out["peak"], (name, out["dpeak"][k], dP)
+        assert abs(out["dimpulse"][k] - dJ) <= 0.02 * abs(dJ) + 1e-6 * out["impulse"], (name, out["dimpulse"][k], dJ)
