@@ -754,7 +754,7 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
     if (paper) k_finalize<1><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
     else k_finalize<0><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
-    if (c->tangent) kt_finalize<<<1, 256, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
+    if (c->tangent) kt_finalize<<<1, kTFinThreads, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
     return HR_OK;

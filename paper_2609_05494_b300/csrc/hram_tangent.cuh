@@ -178,8 +178,9 @@ __device__ __forceinline__ D3 dwarp_sum(D3 a)
     return a;
 }
 
-// Tangent buffers: direction k of particle i at [k * n + i] (fluid, current
-// cell order) or [k * ngh + g] (ghosts).
+// Tangent buffers: direction k of particle i at [i * kDir + k] (fluid, current
+// cell order; ghosts by ghost index), so that one neighbour's three
+// derivatives share cache lines in the gathers.
 struct TBufs {
     int n, ngh;
     float2 *s_pos, *s_vel;
@@ -216,7 +217,7 @@ __device__ __forceinline__ Dual<R> tload(const float *base, int stride, int i, R
     Dual<R> a;
     a.v = v;
 #pragma unroll
-    for (int k = 0; k < kDir; ++k) a.d[k] = R(base[k * stride + i]);
+    for (int k = 0; k < kDir; ++k) a.d[k] = R(base[i * kDir + k]);
     return a;
 }
 
@@ -226,7 +227,7 @@ __device__ __forceinline__ void tload2(const float2 *base, int stride, int i, fl
     y.v = v.y;
 #pragma unroll
     for (int k = 0; k < kDir; ++k) {
-        const float2 t = base[k * stride + i];
+        const float2 t = base[i * kDir + k];
         x.d[k] = t.x;
         y.d[k] = t.y;
     }
@@ -235,13 +236,13 @@ __device__ __forceinline__ void tload2(const float2 *base, int stride, int i, fl
 __device__ __forceinline__ void tstore2(float2 *base, int stride, int i, const D3 &x, const D3 &y)
 {
 #pragma unroll
-    for (int k = 0; k < kDir; ++k) base[k * stride + i] = make_float2(x.d[k], y.d[k]);
+    for (int k = 0; k < kDir; ++k) base[i * kDir + k] = make_float2(x.d[k], y.d[k]);
 }
 
 __device__ __forceinline__ void tstore1(float *base, int stride, int i, const D3 &x)
 {
 #pragma unroll
-    for (int k = 0; k < kDir; ++k) base[k * stride + i] = x.d[k];
+    for (int k = 0; k < kDir; ++k) base[i * kDir + k] = x.d[k];
 }
 
 // the parameters as duals along their own (relative) directions
@@ -488,10 +489,10 @@ __global__ void __launch_bounds__(256) kt_scatter(Consts K, Bufs B, TBufs T, int
     D3 rec[4];
     eos_record_T(K, dp, rec);
     for (int k = 0; k < kDir; ++k) {
-        T.s_pos[k * n + dst] = T.u_pos[k * n + i];
-        T.s_vel[k * n + dst] = T.u_vel[k * n + i];
-        T.s_aux[k * n + dst] = make_float4(rec[0].d[k], rec[1].d[k], rec[2].d[k], rec[3].d[k]);
-        T.s_rd[k * n + dst] = make_float2(dd.d[k], Dx.d[k]);
+        T.s_pos[dst * kDir + k] = T.u_pos[i * kDir + k];
+        T.s_vel[dst * kDir + k] = T.u_vel[i * kDir + k];
+        T.s_aux[dst * kDir + k] = make_float4(rec[0].d[k], rec[1].d[k], rec[2].d[k], rec[3].d[k]);
+        T.s_rd[dst * kDir + k] = make_float2(dd.d[k], Dx.d[k]);
     }
 }
 
@@ -505,7 +506,7 @@ __device__ __forceinline__ void fluid_dual(const Bufs &B, const TBufs &T, int j,
     const float av[4] = {a.x, a.y, a.z, a.w};
     for (int q = 0; q < 4; ++q) aux[q].v = av[q];
     for (int k = 0; k < kDir; ++k) {
-        const float4 t = T.s_aux[k * n + j];
+        const float4 t = T.s_aux[j * kDir + k];
         aux[0].d[k] = t.x;
         aux[1].d[k] = t.y;
         aux[2].d[k] = t.z;
@@ -522,7 +523,7 @@ __device__ __forceinline__ void ghost_dual(const Bufs &B, const TBufs &T, int g,
     const float av[4] = {a.x, a.y, a.z, a.w};
     for (int q = 0; q < 4; ++q) aux[q].v = av[q];
     for (int k = 0; k < kDir; ++k) {
-        const float4 t = T.g_aux[k * m + g];
+        const float4 t = T.g_aux[g * kDir + k];
         aux[0].d[k] = t.x;
         aux[1].d[k] = t.y;
         aux[2].d[k] = t.z;
@@ -610,8 +611,8 @@ __global__ void __launch_bounds__(kGhostWarps * 32) kt_ghost(Consts K, Bufs B, T
     }
     const int m = T.ngh;
     for (int k = 0; k < kDir; ++k) {
-        T.g_aux[k * m + g] = make_float4(rec[0].d[k], rec[1].d[k], rec[2].d[k], rec[3].d[k]);
-        T.g_vel[k * m + g] = make_float2(vgx.d[k], vgy.d[k]);
+        T.g_aux[g * kDir + k] = make_float4(rec[0].d[k], rec[1].d[k], rec[2].d[k], rec[3].d[k]);
+        T.g_vel[g * kDir + k] = make_float2(vgx.d[k], vgy.d[k]);
     }
 }
 
@@ -643,14 +644,28 @@ __global__ void __launch_bounds__(kTPassThreads) kt_pass(Consts K, Bufs B, TBufs
             AccT A{z, z, z, z, z};
             D3 fx, fy;
             const int c = cell_of(K, ri.x, ri.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
-                const float2 rj = B.s_pos[j];
-                if (j == i || !in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) return;
-                D3 xj, yj, vxj, vyj, aj[4];
-                fluid_dual(B, T, j, xj, yj, vxj, vyj, aj);
-                pair_T(K, I, xj, yj, vxj, vyj, K.rho0 * (aj[0] + 1.0f), aj[2], aj[3], 1.0f, true,
-                       A, fx, fy);
-            });
+            // the forward pass's candidate masks (same predicate, same order), so
+            // that a warp evaluates the dual pair terms with all lanes that have
+            // a neighbour, not once per candidate under a branch
+#pragma unroll 1
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int row = c + dy * K.ncx;
+                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+#pragma unroll 1
+                for (int base = a; base < b; base += 32) {
+                    unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
+                    if (i >= base && i < base + 32) m &= ~(1u << (i - base));
+#pragma unroll 1
+                    while (m) {
+                        const int j = base + __ffs(m) - 1;
+                        m &= m - 1u;
+                        D3 xj, yj, vxj, vyj, aj[4];
+                        fluid_dual(B, T, j, xj, yj, vxj, vyj, aj);
+                        pair_T(K, I, xj, yj, vxj, vyj, K.rho0 * (aj[0] + 1.0f), aj[2], aj[3],
+                               1.0f, true, A, fx, fy);
+                    }
+                }
+            }
             if (K.nw > 0)
                 for_fluid_candidates(K, B.wall_start, c, [&](int k) {
                     const float2 rg = B.gw_pos[k];
@@ -705,16 +720,20 @@ __global__ void __launch_bounds__(kTPassThreads) kt_pass(Consts K, Bufs B, TBufs
 
 // Step close of the tangents (after k_finalize): wall-impulse derivative and
 // the probe-0 peak's derivative at the argmax step.
-__global__ void __launch_bounds__(256) kt_finalize(Consts K, Bufs B, TBufs T, int prime, int nblk)
+constexpr int kTFinThreads = 1024;
+__global__ void __launch_bounds__(kTFinThreads) kt_finalize(Consts K, Bufs B, TBufs T, int prime, int nblk)
 {
-    __shared__ double red[8][kDir];
+    __shared__ double red[kTFinThreads / 32][kDir];
     __shared__ float probe_d[kDir + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double s[kDir] = {0.0, 0.0, 0.0};
+    // the per-block partials: float sums per thread (loads unrolled so they
+    // stay in flight), FP64 from the warp level up
+    float s[kDir] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 4
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-        for (int k = 0; k < kDir; ++k) s[k] += (double)T.part[b * kDir + k];
+        for (int k = 0; k < kDir; ++k) s[k] += T.part[b * kDir + k];
     for (int k = 0; k < kDir; ++k) {
-        const double v = warp_sum(s[k]);
+        const double v = warp_sum((double)s[k]);
         if (lane == 0) red[w][k] = v;
     }
     // probe 0 on duals, one warp
@@ -764,7 +783,7 @@ __global__ void __launch_bounds__(256) kt_finalize(Consts K, Bufs B, TBufs T, in
     const double Fw = B.S->Fwall;
     for (int k = 0; k < kDir; ++k) {
         double f = 0.0;
-        for (int q = 0; q < 8; ++q) f += red[q][k];
+        for (int q = 0; q < kTFinThreads / 32; ++q) f += red[q][k];
         sc[TSC_FW + k] = m2 * f;
         sc[TSC_IMP + k] += sc[TSC_DT + k] * Fw + dt * sc[TSC_FW + k];
     }
