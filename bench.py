@@ -473,12 +473,16 @@ def main():
     h_xy = torch.from_numpy(xy).pin_memory().numpy()
     h_v = torch.from_numpy(vel0).pin_memory().numpy()
     h_r = torch.from_numpy(rho0).pin_memory().numpy()
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float32).pin_memory().numpy()
+    h_probes = pinned((args.steps + args.warmup + 8, max(len(p["probes"]), 1)))
+    h_final = dict(xy=pinned((n, 2)), vel=pinned((n, 2)), rho=pinned((n,)), p=pinned((n,)))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     case.set_state(h_xy, h_v, h_r)
     case.run(args.steps)
-    probes = case.probe_pressure()
-    final = case.get_state()
+    probes = case.probe_pressure(out=h_probes)
+    final = case.get_state(out=h_final)
     e2e_s = time.perf_counter() - t0
     h2d = h_xy.nbytes + h_v.nbytes + h_r.nbytes
     d2h = probes.nbytes + sum(v.nbytes for v in final.values())

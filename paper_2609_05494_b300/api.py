@@ -139,13 +139,23 @@ class Case:
         return self.last_status
 
     # -- outputs
-    def probe_pressure(self) -> np.ndarray:
+    def probe_pressure(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Probe history [steps, n_probes] (float32).  ``out``: a caller-owned
+        C-contiguous float32 buffer (for instance pinned) with room for at
+        least the recorded rows; the filled rows are returned as a view."""
         L = lib()
         n = C.c_int64(0)
         check(L.hr_probe_pressure(self._h, None, 0, C.byref(n)), "hr_probe_pressure")
-        out = np.zeros((n.value, max(self.n_probes, 1)), dtype=np.float32)
-        check(L.hr_probe_pressure(self._h, _ptr(out), n.value, C.byref(n)), "hr_probe_pressure")
-        return out[:, :self.n_probes]
+        width = max(self.n_probes, 1)
+        if out is None:
+            out = np.zeros((n.value, width), dtype=np.float32)
+        elif (out.dtype != np.float32 or not out.flags.c_contiguous or out.ndim != 2
+              or out.shape[1] != width or out.shape[0] < n.value):
+            raise ValueError("out must be C-contiguous float32 of shape (>= %d, %d)"
+                             % (n.value, width))
+        check(L.hr_probe_pressure(self._h, _ptr(out), out.shape[0], C.byref(n)),
+              "hr_probe_pressure")
+        return out[:n.value, :self.n_probes]
 
     def probe_times(self) -> np.ndarray:
         L = lib()
@@ -168,10 +178,20 @@ class Case:
         check(L.hr_diag_history(self._h, _ptr(out), n.value, C.byref(n)), "hr_diag_history")
         return out
 
-    def get_state(self) -> dict:
+    def get_state(self, out: dict | None = None) -> dict:
+        """Fluid state in ID order.  ``out``: caller-owned float32 arrays
+        xy (N, 2), vel (N, 2), rho (N,), p (N,) (for instance pinned), filled
+        in place."""
         n = self.n
-        out = dict(xy=np.empty((n, 2), np.float32), vel=np.empty((n, 2), np.float32),
-                   rho=np.empty(n, np.float32), p=np.empty(n, np.float32))
+        if out is None:
+            out = dict(xy=np.empty((n, 2), np.float32), vel=np.empty((n, 2), np.float32),
+                       rho=np.empty(n, np.float32), p=np.empty(n, np.float32))
+        else:
+            shapes = dict(xy=(n, 2), vel=(n, 2), rho=(n,), p=(n,))
+            for k, shp in shapes.items():
+                a = out[k]
+                if a.dtype != np.float32 or a.shape != shp or not a.flags.c_contiguous:
+                    raise ValueError("out[%r] must be C-contiguous float32 %s" % (k, shp))
         check(lib().hr_get_state(self._h, _ptr(out["xy"]), _ptr(out["vel"]), _ptr(out["rho"]),
                                  _ptr(out["p"]), n), "hr_get_state")
         return out

@@ -129,6 +129,16 @@ __global__ void k_diag_final(Consts K, Bufs B, const double *part, int nblocks, 
         for (int k = 0; k < kDiagFields; ++k) hist[(size_t)rec * kDiagFields + k] = d[k];
 }
 
+// Uploaded densities -> deviations d = rho / rho0 - 1 (FP64, rounded once),
+// and the identity order of the fluid IDs.
+__global__ void k_upload_fix(Consts K, Bufs B, const float *rho, double rho0)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K.nf) return;
+    if (rho) B.st_rho[i] = (float)((double)rho[i] / rho0 - 1.0);
+    B.s_id[i] = i;
+}
+
 // Sorted state -> fluid-ID order.
 __global__ void k_unsort(Consts K, Bufs B, float2 *xy, float2 *vel, float *rho, float *p)
 {
@@ -797,24 +807,23 @@ int device_status(hr_case *c)
 // Uploads a fluid state in ID order (identity permutation), zero derivatives.
 int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho)
 {
+    // straight from the caller's buffers (pinned ones copy at full speed);
+    // the density conversion and the IDs are made on the device
     const size_t n = (size_t)c->nf;
-    std::vector<float> d(n), v(2 * n, 0.0f);
-    std::vector<int> id(n);
-    std::iota(id.begin(), id.end(), 0);
-    for (size_t i = 0; i < n; ++i) d[i] = rho ? (float)((double)rho[i] / c->P.rho0 - 1.0) : 0.0f;
-    if (vel) std::memcpy(v.data(), vel, 2 * n * sizeof(float));
     CK(cudaMemcpyAsync(c->B.s_pos, xy, n * 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->B.st_vel, v.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->B.st_rho, d.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    if (vel) CK(cudaMemcpyAsync(c->B.st_vel, vel, n * 8, cudaMemcpyHostToDevice, c->stream));
+    else CK(cudaMemsetAsync(c->B.st_vel, 0, n * 8, c->stream));
+    if (rho) CK(cudaMemcpyAsync(c->io, rho, n * 4, cudaMemcpyHostToDevice, c->stream));
+    else CK(cudaMemsetAsync(c->B.st_rho, 0, n * 4, c->stream));
+    k_upload_fix<<<c->drift_blocks, 256, 0, c->stream>>>(c->K, c->B, rho ? c->io : nullptr,
+                                                         c->P.rho0);
+    CK(cudaGetLastError());
     CK(cudaMemsetAsync(c->B.st_a, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.st_D, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.st_X, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4, c->stream));
     CK(cudaMemsetAsync(c->B.fin_ticket, 0, 4, c->stream));
-    Scalars S;
-    std::memset(&S, 0, sizeof S);
-    CK(cudaMemcpyAsync(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->B.S, 0, sizeof(Scalars), c->stream));
     if (c->tangent) {
         // the uploaded state does not depend on the parameters; dt = C h /
         // (c0 + v0) has d dt / d ln c0 = -dt c0 / (c0 + v0)

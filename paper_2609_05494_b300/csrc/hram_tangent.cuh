@@ -609,7 +609,6 @@ __global__ void __launch_bounds__(kGhostWarps * 32) kt_ghost(Consts K, Bufs B, T
         vgx = vw;
         vgy = dconst(0.0f);
     }
-    const int m = T.ngh;
     for (int k = 0; k < kDir; ++k) {
         T.g_aux[g * kDir + k] = make_float4(rec[0].d[k], rec[1].d[k], rec[2].d[k], rec[3].d[k]);
         T.g_vel[g * kDir + k] = make_float2(vgx.d[k], vgy.d[k]);
