@@ -152,6 +152,31 @@ def test_checkpoint_resume_bitwise():
     assert a.scalars() == b.scalars()
 
 
+def test_caller_owned_output_buffers():
+    # pinned (page-locked) caller buffers receive exactly what the library's
+    # own arrays receive; wrong shapes or dtypes are refused before any copy
+    p, xy = impact_case()
+    with Case(p, xy) as c:
+        c.run(12)
+        ref_state, ref_probe = c.get_state(), c.probe_pressure()
+        n = xy.shape[0]
+
+        def pinned(shape):
+            return torch.empty(shape, dtype=torch.float32).pin_memory().numpy()
+        out = dict(xy=pinned((n, 2)), vel=pinned((n, 2)), rho=pinned((n,)), p=pinned((n,)))
+        got = c.get_state(out=out)
+        for k in ref_state:
+            assert np.array_equal(got[k], ref_state[k]), k
+            assert got[k] is out[k]
+        buf = pinned((40, len(p["probes"])))
+        pr = c.probe_pressure(out=buf)
+        assert pr.shape == ref_probe.shape and np.array_equal(pr, ref_probe)
+        with pytest.raises(ValueError):
+            c.probe_pressure(out=np.zeros((5, len(p["probes"])), np.float32))
+        with pytest.raises(ValueError):
+            c.get_state(out=dict(out, rho=np.zeros(n, np.float64)))
+
+
 def test_invalid_parameters_rejected():
     p, xy = impact_case()
     for bad in (dict(dx=0.0), dict(Ng=5000), dict(cfl=-1.0), dict(rho_hi=0.2)):
