@@ -1385,8 +1385,11 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
     b_ghost<CL>(K, B, blockIdx.x, gridDim.x);
 }
 
+// 10 resident blocks per SM (48 registers): 40 warps against 36 at the
+// compiler's own 54 registers, 3 % faster on the 1.125M workload, no spills
+constexpr int kPassMinBlocks = 10;
 template <int CL>
-__global__ void __launch_bounds__(kPassThreads) k_pass(Consts K, Bufs B, int prime)
+__global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass(Consts K, Bufs B, int prime)
 {
     b_pass<CL>(K, B, blockIdx.x, gridDim.x, prime);
 }
