@@ -680,39 +680,40 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
 {
     const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
+    // the particle's own data first, so their loads overlap the rank loop's
     const int key = B.u_key[i];
-    const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
     const int id = B.u_id[i];
+    const float d = B.st_rho[i];
+    const float2 D = B.st_D[i];
+    const float2 up = B.u_pos[i];
+    float2 uv = B.u_vel[i];
+    const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
+    float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 a = make_float2(0.f, 0.f);
+    if constexpr (CL == 1) {
+        a = B.st_a[i];
+        if (key != K.ncell) {
+            const float hdt = prime ? 0.0f : 0.5f * B.S->dt_f;
+            uv.x = fmaf(hdt, a.x, uv.x);
+            uv.y = fmaf(hdt, a.y, uv.y);
+        }
+    } else {
+        float dp = d;
+        if (key != K.ncell) {
+            const float dt = prime ? 0.0f : B.S->dt_f;
+            const float ratio = prime ? 1.0f : B.S->ratio_f;
+            dp = band(K, fmaf(dt, fmaf(ratio, D.x - D.y, D.x), d));
+        }
+        rec = eos_record(K, dp);
+    }
     int rank = 0;
 #pragma unroll 4
     for (int k = cs; k < ce; ++k) rank += __ldg(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
-    const float d = B.st_rho[i];
-    const float2 D = B.st_D[i];
-    if constexpr (CL == 1) {
-        const float2 a = B.st_a[i];
-        float2 v = B.u_vel[i];
-        if (key != K.ncell) {
-            const float hdt = prime ? 0.0f : 0.5f * B.S->dt_f;
-            v.x = fmaf(hdt, a.x, v.x);
-            v.y = fmaf(hdt, a.y, v.y);
-        }
-        B.s_pos[dst] = B.u_pos[i];
-        B.s_vel[dst] = v;
-        B.s_ex[dst] = make_float4(a.x, a.y, D.y, D.x);
-        B.s_rd[dst] = make_float2(d, D.x);
-        B.s_id[dst] = id;
-        return;
-    }
-    float dp = d;
-    if (key != K.ncell) {
-        const float dt = prime ? 0.0f : B.S->dt_f;
-        const float ratio = prime ? 1.0f : B.S->ratio_f;
-        dp = band(K, fmaf(dt, fmaf(ratio, D.x - D.y, D.x), d));
-    }
-    B.s_pos[dst] = B.u_pos[i];
-    B.s_vel[dst] = B.u_vel[i];
-    B.s_aux[dst] = eos_record(K, dp);
+    B.s_pos[dst] = up;
+    B.s_vel[dst] = uv;
+    if constexpr (CL == 1) B.s_ex[dst] = make_float4(a.x, a.y, D.y, D.x);
+    else B.s_aux[dst] = rec;
     B.s_rd[dst] = make_float2(d, D.x);
     B.s_id[dst] = id;
     if (B.perm_dst) B.perm_dst[i] = dst;
