@@ -10,8 +10,11 @@
  * interaction sums L (Section 2.2: XSPH, momentum with Monaghan artificial
  * viscosity and a laminar term, continuity density, Tait pressure with the
  * cavitation cutoff) and the kick-drift-kick time advance T with the CFL gate
- * (Section 2.5, eq. cfl).  Every step runs in CUDA kernels on the device; the
- * host only launches a captured CUDA graph.
+ * (Section 2.5, eq. cfl).  That is closure 0 (the default).  Closure 1 is
+ * the paper's own closure: cubic B-spline, summation density, Mie-Grueneisen
+ * EOS with an internal-energy equation (see hr_params.closure).  Every step
+ * runs in CUDA kernels on the device; the host only launches a captured CUDA
+ * graph.
  *
  * Conventions for every call:
  *   - SI units.  Fluid x in [0, Lx], y in [-W/2, W/2]; the disk moves along +x.
@@ -53,7 +56,9 @@ extern "C" {
 #define HR_WPROBEFULL 4   /* probe history capacity reached; later samples dropped */
 
 /* flags */
-#define HR_FLAG_TIMING 1  /* record CUDA events around the step's kernels */
+#define HR_FLAG_TIMING 1  /* record CUDA events around the step's kernel groups
+                            (hr_kernel_times); each event inside the step graph
+                            adds about 2.6 us to the step on a B300 */
 #define HR_FLAG_TANGENT 2 /* carry tangent-linear derivatives along the run
                             (see hr_tangent_outputs); needs dt_mode 1 and
                             motion 0-2 */
