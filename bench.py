@@ -37,7 +37,7 @@ DX = 2e-4
 ALG_BYTES_PER_PARTICLE = 40      # {x, y, vx, vy, rho} read and written once
 FLOP_PER_PAIR = 58               # pair terms of the interaction pass
 FLOP_PER_CANDIDATE = 6           # float predicate of one candidate
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_pass_c2_dx0.2mm_traffic.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_pass_channel300x150_dx0.2mm_traffic.txt")
 
 
 def workload(dx=DX, Lx=None):
@@ -47,6 +47,17 @@ def workload(dx=DX, Lx=None):
     xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
                                disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
     return p, xy.astype(np.float32)
+
+
+def workload_config(dx=DX, world=1):
+    """The workload's description, the same on both arms of the benchmark."""
+    p = casegen.config_scaling(dx)
+    n = casegen.n_lattice(p["Lx"], p["W"], dx)
+    return {"workload": "300 x 150 mm water channel, dx = %g mm, %d fluid particles, 5 mm disk "
+                        "entering at 900 m/s, impact phase from t = 0" % (dx * 1e3, n),
+            "particles": n, "dx_mm": dx * 1e3,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "256 MB buffer written between timed steps"}
 
 
 def peaks():
@@ -387,8 +398,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "c2-dx0.2mm sample", "particles": int(xy.shape[0]),
-                       "dx_mm": 0.2, "channel_mm": [Lx * 1e3, 150.0]},
+            "config": workload_config(DX, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -532,13 +542,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "c2-dx0.2mm: 300 x 150 mm channel, dx = 0.2 mm, %d fluid "
-                               "particles, disk 5 mm at 900 m/s, impact phase from t = 0" % n,
-                   "particles": n, "dx_mm": args.dx * 1e3, "parallelism": "replicas" if world > 1
-                   else "single", "l2": "256 MB buffer written between timed steps",
-                   "timing": "step graph without timing events; kernel durations from a "
-                             "second run of the workload with in-graph CUDA events",
-                   "status": status},
+        "config": workload_config(args.dx, world),
+        "timing": "step graph without timing events; kernel durations from a second run of "
+                  "the workload with in-graph CUDA events",
+        "status": status,
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
