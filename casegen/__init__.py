@@ -132,7 +132,7 @@ def base_params() -> dict:
         eps_xsph=0.02, mu_lam=8.9e-4, gx=0.0, gy=-9.81, cfl=0.2, dt_mode=0,
         rho_lo=0.5, rho_hi=1.5, box_pad=-1.0, cell_factor=1.001,
         seed=DEFAULT_SEED, jitter=0.01, disk_density=7850.0,
-        closure=0, mg_S1=1.979, mg_gamma0=0.11, mg_a=3.0, mg_mu_max=0.25,
+        closure=0, mg_S1=1.979, mg_gamma0=0.11, mg_a=3.0, mg_mu_max=0.25, wall_reflect=0,
         probes=[],
     )
 

@@ -99,7 +99,12 @@ extern "C" {
  *                  c = c0.  Closure 1 cases cannot be batched or run in
  *                  tangent mode.
  *  mg_S1, mg_gamma0, mg_a, mg_mu_max   Mie-Grueneisen S1, gamma0, a and the
- *                  compression cap on mu = rho/rho0 - 1 (1.979, 0.11, 3.0, 0.25) */
+ *                  compression cap on mu = rho/rho0 - 1 (1.979, 0.11, 3.0, 0.25)
+ *  wall_reflect    1 = with wall_layers = 0 the side walls still reflect
+ *                  particles (|y| > W/2: y pulled back to +-(W/2 - 1e-6 m),
+ *                  v_y reversed), the paper's baseline hard wall without
+ *                  ghosts (Section 2.6.2); it exerts no pressure, so the
+ *                  wall impulse stays 0 */
 typedef struct hr_params {
     double dx, h_over_dx, Lx, W;
     int32_t wall_layers, end_walls;
@@ -115,6 +120,7 @@ typedef struct hr_params {
     double disk_density;
     int32_t closure;
     double mg_S1, mg_gamma0, mg_a, mg_mu_max;
+    int32_t wall_reflect;
 } hr_params;
 
 /* FP64 diagnostics (Section 2.10 and eq. energy-audit of Section 4.7). */

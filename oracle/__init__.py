@@ -55,6 +55,7 @@ class OracleParams(C.Structure):
         ("closure", C.c_int32),
         ("mg_S1", C.c_double), ("mg_gamma0", C.c_double), ("mg_a", C.c_double),
         ("mg_mu_max", C.c_double),
+        ("wall_reflect", C.c_int32),
     ]
 
 

@@ -65,6 +65,9 @@ typedef struct {
      * Mie-Grueneisen EOS with the internal-energy equation) */
     int32_t closure;
     double mg_S1, mg_gamma0, mg_a, mg_mu_max;
+    /* 1: the side walls reflect particles even without ghost layers (the
+     * paper's baseline hard wall, Section "The Channel Walls") */
+    int32_t wall_reflect;
 } orc_params;
 
 enum { KIND_FLUID = 0, KIND_SIDE = 1, KIND_END = 2, KIND_DISK = 3 };
@@ -969,7 +972,7 @@ static void drift_and_walls(orc_case *c, double dt)
         if (c->out[i]) continue;
         c->x[i] += dt * (c->vhx[i] + c->P.eps_xsph * c->Xx[i]);
         c->y[i] += dt * (c->vhy[i] + c->P.eps_xsph * c->Xy[i]);
-        if (c->P.wall_layers > 0) {
+        if (c->P.wall_layers > 0 || c->P.wall_reflect) {
             if (c->y[i] > W2) { c->y[i] = W2 - eps; c->vhy[i] = -c->vhy[i]; }
             else if (c->y[i] < -W2) { c->y[i] = -W2 + eps; c->vhy[i] = -c->vhy[i]; }
             if (c->P.end_walls) {

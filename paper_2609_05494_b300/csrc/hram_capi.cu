@@ -357,6 +357,7 @@ int validate(const hr_params *P, long long nf)
     // tangent mode: fixed time step (smooth in c0) and a prescribed motion
     if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
     if (P->closure < 0 || P->closure > 1) return HR_EINVAL;
+    if (P->wall_reflect < 0 || P->wall_reflect > 1) return HR_EINVAL;
     if (P->closure == 1) {
         if ((P->flags & HR_FLAG_TANGENT) || !(P->mg_mu_max > 0)) return HR_EINVAL;
         // the Hugoniot denominator 1 - (S1 - 1) mu must stay positive up to the cap
@@ -447,7 +448,7 @@ void make_consts(hr_case *c)
     K.yhi = (float)yhi;
     K.W2 = (float)(0.5 * P.W);
     K.Lx = (float)P.Lx;
-    K.side_walls = P.wall_layers > 0;
+    K.side_walls = P.wall_layers > 0 || P.wall_reflect == 1;
     K.end_walls = P.end_walls && P.wall_layers > 0;
     const double ad = 7.0 / (4.0 * M_PI * h * h);
     K.h = (float)h;

@@ -160,3 +160,20 @@ def test_paper_setup_runs_and_peaks_in_the_papers_range():
     ptn = pr[:, 0].max()
     assert 1e8 < ptn < 3e9
     assert d["n_in"] == xy.shape[0]
+
+
+def test_hard_reflection_wall_matches_oracle():
+    # the paper's baseline wall: no ghost layers, reflection at |y| = W/2
+    p, xy = paper_case(wall_layers=0, wall_reflect=1)
+    g, o = both(p, xy)
+    g.run(3)
+    o.run(3)
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    # a summed density turns float32 position rounding into pressure (about
+    # 1e-4 in d per micrometre at this spacing), so a few steps in the gate
+    # is 1e-4 of the pressure scale
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-4 * p_scale(p, fo["p"])
+    g.run(40)
+    assert np.all(np.abs(g.get_state()["xy"][:, 1]) <= 0.5 * p["W"])
+    assert g.scalars()["wall_impulse"] == 0.0

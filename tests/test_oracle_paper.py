@@ -203,3 +203,23 @@ def test_paper_closure_momentum_and_galilean_invariance():
     assert np.allclose(f2["acc"], f["acc"], rtol=1e-9, atol=1e-9 * np.abs(f["acc"]).max())
     e1, e2 = o.energy(), o2.energy()
     assert np.allclose(e2["de"], e1["de"], rtol=1e-9, atol=1e-9 * np.abs(e1["de"]).max())
+
+
+def test_hard_reflection_wall_keeps_particles_in_the_channel():
+    # the paper's baseline wall (Section "The Channel Walls"): no ghosts, a
+    # particle crossing |y| = W/2 is put back inside and its normal velocity
+    # reversed; it carries no pressure, so no wall impulse is recorded
+    p = paper_params(wall_layers=0, wall_reflect=1, Lx=0.04, W=0.02, dx=1e-3, Ng=0,
+                     gy=0.0, box_pad=0.05)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.01, 9, disk=None)
+    vel = np.zeros_like(xy)
+    vel[:, 1] = np.where(xy[:, 1] > 0, 40.0, -40.0)     # everything pushed at the walls
+    o = oracle.OracleCase(p, xy, vel=vel)
+    o.run(60)
+    f = o.fluid()
+    assert np.all(np.abs(f["xy"][:, 1]) <= 0.5 * p["W"])
+    assert o.scalars()["wall_impulse"] == 0.0 and o.ngh == 0
+    q = dict(p, wall_reflect=0)
+    o2 = oracle.OracleCase(q, xy, vel=vel)
+    o2.run(60)
+    assert np.any(np.abs(o2.fluid()["xy"][:, 1]) > 0.5 * p["W"])
