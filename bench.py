@@ -328,33 +328,63 @@ def production_benchmark(stream):
 
 
 def paper_event_benchmark(stream):
-    """The paper's own set-up and closure (750 x 150 mm, dx = 1.5 mm, about
-    50,000 particles, cubic spline, summation density, Mie-Grueneisen water,
-    drag law) run through its whole 150 us event, as the paper times it
-    (Section "Speed": about 14 s on a TITAN RTX).  Wall clock from the first
-    step to the synchronised end, with the probes PTn and PTf recorded."""
+    """The paper's own set-up and closure (750 x 150 mm, cubic spline,
+    summation density, Mie-Grueneisen water, drag law, centreline probes PTn
+    and PTf) through its whole 150 us event: the production run (dx = 1.5 mm,
+    alpha 0.03, 900 m/s; the paper times it at about 14 s on a TITAN RTX,
+    Section "Speed"), the resolution sweep dx = 2.0 / 1.5 / 1.0 mm and the
+    alpha sweep 0.01-0.10 at 900 and 600 m/s (Tables tab:convergence and
+    tab:alpha-sweep, whose peaks are listed beside ours for magnitude only: a
+    planar model's peaks are not parity targets).  Wall clock from the first
+    step to the synchronised end."""
     import torch
     from paper_2609_05494_b300 import Case
-    p = casegen.config_paper(900.0)
-    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
-                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
-    with torch.cuda.stream(stream):
-        c = Case(p, xy, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = c.run(0, p["t_end"])
-    c.sync()
-    wall = time.perf_counter() - t0
-    steps = int(c.scalars()["step"])
-    pr = c.probe_pressure()
-    c.close()
-    return {"workload": "paper set-up: 750 x 150 mm, dx = 1.5 mm, %d particles, 900 m/s, "
-                        "closure 1, 150 us" % xy.shape[0],
-            "steps": steps, "wall_s": wall, "ms_per_step": 1e3 * wall / steps,
-            "particle_steps_per_s": xy.shape[0] * steps / wall,
-            "ptn_peak_MPa": float(pr[:, 0].max()) * 1e-6,
-            "ptf_peak_MPa": float(pr[:, 1].max()) * 1e-6, "status": st,
-            "paper_wall_s_titan_rtx": 14.0}
+
+    def event(dx, alpha, v0):
+        p = casegen.config_paper(v0)
+        p.update(dx=float(dx), alpha=float(alpha))
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                                   disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+        with torch.cuda.stream(stream):
+            c = Case(p, xy, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = c.run(0, p["t_end"])
+        c.sync()
+        wall = time.perf_counter() - t0
+        steps = int(c.scalars()["step"])
+        pr = c.probe_pressure()
+        c.close()
+        return {"dx_mm": dx * 1e3, "alpha": alpha, "v0": v0, "particles": int(xy.shape[0]),
+                "steps": steps, "wall_s": wall, "ms_per_step": 1e3 * wall / steps,
+                "ptn_peak_MPa": float(pr[:, 0].max()) * 1e-6,
+                "ptf_peak_MPa": float(pr[:, 1].max()) * 1e-6, "status": st}
+
+    main = event(1.5e-3, 0.03, 900.0)
+    main.update(particle_steps_per_s=main["particles"] * main["steps"] / main["wall_s"],
+                paper_wall_s_titan_rtx=14.0)
+    # the paper's printed peaks (MPa) for the same runs
+    paper_res = {2.0: (785.8, 658.0), 1.5: (850.3, 714.9), 1.0: (830.5, 737.5)}
+    paper_alpha = {(900.0, 0.01): 855.7, (900.0, 0.03): 850.3, (900.0, 0.06): 893.7,
+                   (900.0, 0.10): 871.9, (600.0, 0.01): 429.7, (600.0, 0.03): 446.0,
+                   (600.0, 0.06): 371.4, (600.0, 0.10): 367.1}
+    res = []
+    for dx in (2.0e-3, 1.5e-3, 1.0e-3):
+        r = main if dx == 1.5e-3 else event(dx, 0.03, 900.0)
+        res.append({k: r[k] for k in ("dx_mm", "particles", "steps", "wall_s", "ptn_peak_MPa",
+                                      "ptf_peak_MPa")})
+        res[-1]["paper_ptn_MPa"], res[-1]["paper_ptf_MPa"] = paper_res[round(dx * 1e3, 1)]
+    alph = []
+    for v0 in (900.0, 600.0):
+        for a in (0.01, 0.03, 0.06, 0.10):
+            r = main if (v0 == 900.0 and a == 0.03) else event(1.5e-3, a, v0)
+            alph.append({"v0": v0, "alpha": a, "ptn_peak_MPa": r["ptn_peak_MPa"],
+                         "paper_ptn_MPa": paper_alpha[(v0, a)], "wall_s": r["wall_s"]})
+    main["resolution"] = res
+    main["alpha_sweep"] = alph
+    main["workload"] = ("paper set-up: 750 x 150 mm, dx = 1.5 mm, %d particles, 900 m/s, "
+                        "closure 1, 150 us" % main["particles"])
+    return main
 
 
 def cpu_baseline(seconds=15.0, Lx=0.075):
