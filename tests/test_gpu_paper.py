@@ -177,3 +177,25 @@ def test_hard_reflection_wall_matches_oracle():
     g.run(40)
     assert np.all(np.abs(g.get_state()["xy"][:, 1]) <= 0.5 * p["W"])
     assert g.scalars()["wall_impulse"] == 0.0
+
+
+def test_checkpoint_resume_bitwise_paper_closure():
+    # closure 1 carries the internal energy and its rate in the checkpoint
+    import os
+    import tempfile
+    p, xy = paper_case()
+    a = Case(p, xy)
+    a.run(20)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        a.save(path)
+        a.run(15)
+        b = Case(p, xy)
+        b.load(path)
+        b.run(15)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    ea, eb = a.energy(), b.energy()
+    assert np.array_equal(ea["e"], eb["e"]) and np.array_equal(ea["de"], eb["de"])
+    assert np.array_equal(a.probe_pressure(), b.probe_pressure())
