@@ -134,3 +134,31 @@ def test_run_is_deterministic():
     for k in sa:
         assert np.array_equal(sa[k], sb[k])
     assert np.array_equal(a.probe_pressure(), b.probe_pressure())
+
+
+@pytest.mark.parametrize("closure", [0, 1])
+def test_dense_rows_over_32_candidates(closure):
+    # a patch at half the spacing the smoothing length is set for: about 27
+    # particles per cell, 80 per stencil row, so every row takes the pass's
+    # path for rows longer than one 32-bit mask
+    p = casegen.base_params()
+    p.update(dx=1e-3, Lx=0.02, W=0.02, Ng=0, wall_layers=3, closure=closure, gy=0.0,
+             c0=1448.0 if closure else 1480.0)
+    xy = casegen.fluid_lattice(0.012, 0.012, 0.5e-3, 0.01, 21, disk=None)
+    xy[:, 0] += 0.004
+    xy = xy.astype(np.float32)
+    vel, _ = perturbed(p, xy, seed=5, v_amp=3.0, rho_rel=0.0)
+    g, o = both(p, xy, vel)
+    off_g, ids_g = g.neighbours()
+    off_o, ids_o = o.neighbours()
+    assert csr_equal(off_g, ids_g, off_o, ids_o)
+    counts = np.diff(off_o)[:xy.shape[0]]
+    assert counts.max() > 60
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
