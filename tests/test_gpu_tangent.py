@@ -163,3 +163,40 @@ def test_adjoint_workload_gradients_within_two_percent():
         dP, dJ = (ph.max() - pl.max()) / 2e-4, (jh - jl) / 2e-4
         assert abs(out["dpeak"][k] - dP) <= 0.02 * abs(dP) + 1e-6 * out["peak"], (name, out["dpeak"][k], dP)
         assert abs(out["dimpulse"][k] - dJ) <= 0.02 * abs(dJ) + 1e-6 * out["impulse"], (name, out["dimpulse"][k], dJ)
+
+
+def test_tangents_on_rows_over_32_candidates():
+    # the tangent pass's path for stencil rows longer than one mask: a patch
+    # at half the spacing the smoothing length is set for, thrown at the
+    # upper wall, against central differences of the oracle
+    p = casegen.base_params()
+    p.update(dx=1e-3, Lx=0.02, W=0.02, Ng=0, wall_layers=3, gy=0.0, dt_mode=1, v0=0.0)
+    p["probes"] = [(0.010, 0.010)]
+    xy = casegen.fluid_lattice(0.012, 0.012, 0.5e-3, 0.01, 21, disk=None)
+    xy[:, 0] += 0.004
+    xy[:, 1] += 0.003
+    xy = xy.astype(np.float32)
+    vel = np.zeros_like(xy)
+    vel[:, 1] = 20.0
+    n = 30
+
+    def orc(q):
+        o = oracle.OracleCase(q, as64(xy), as64(vel))
+        o.run(n)
+        pr, _ = o.probes()
+        return pr[:, 0].max(), o.scalars()["wall_impulse"]
+
+    with Case(p, xy, vel, tangent=True) as c:
+        c.run(n)
+        c.sync()
+        out = c.tangent_outputs()
+    P0, J0 = orc(p)
+    assert out["peak"] == pytest.approx(P0, rel=1e-3) and out["impulse"] == pytest.approx(J0, rel=1e-3)
+    for k, name in enumerate(("alpha", "c0")):
+        hi, lo = dict(p), dict(p)
+        hi[name] = p[name] * (1.0 + FD_EPS)
+        lo[name] = p[name] * (1.0 - FD_EPS)
+        (ph, jh), (pl, jl) = orc(hi), orc(lo)
+        dP, dJ = (ph - pl) / (2 * FD_EPS), (jh - jl) / (2 * FD_EPS)
+        assert close(out["dpeak"][k], dP, out["peak"]), (name, out["dpeak"][k], dP)
+        assert close(out["dimpulse"][k], dJ, out["impulse"]), (name, out["dimpulse"][k], dJ)
