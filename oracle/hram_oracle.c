@@ -23,8 +23,14 @@
  * Parity status of each part (what pins it is in the tests):
  *   kernel, predicate, neighbour sets, EOS, pair sums, ghost operator,
  *   kinematics, mass and momentum invariants: pinned.
+ *   closure 1 (the paper's closure): cubic kernel by quadrature, summation
+ *   density by brute-force lattice sums, Mie-Grueneisen EOS against the
+ *   shock Hugoniot of the jump conditions, the energy equation by
+ *   conservation of kinetic plus internal energy: pinned.
+ *   two-way coupling: the disk's energy loss equals the boundary work.
  *   full multi-step run: no closed form -- pinned only through invariants,
- *   hydrostatic rest, added mass, reflection and arrival-time checks.
+ *   hydrostatic rest, added mass (partially: the planar closed form is the
+ *   incompressible limit), reflection and arrival-time checks.
  */
 #include <math.h>
 #include <stdint.h>
