@@ -956,172 +956,204 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
 // density and the closing half kick.  Block partials of the ghost forces,
 // the dissipation rate and max |v| are reduced in FP32 per warp and in FP64
 // per block.
+
+// Per-thread partials of a pass block.
+struct PassPart {
+    float fdx, fdy, fw, diss, vmax;
+    int npen;
+};
+
+// Phase 1 and 2 of particle i (inside the box): fluid neighbours into A.
 template <int CL>
-__device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+__device__ __forceinline__ void pass_fluid(const Consts &K, const Bufs &B, int i, float2 ri,
+                                           int c, const Self &I, Acc &A)
 {
-    __shared__ float red[kPassThreads / 32][5];
-    __shared__ int redn[kPassThreads / 32];
-    const int i = bx * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float dt = prime ? 0.0f : B.S->dt_f;
-    float fdx = 0.0f, fdy = 0.0f, fw = 0.0f, diss = 0.0f, vmax = 0.0f;
-    int npen = 0;
-    if (i < K.nf) {
-        const float2 ri = B.s_pos[i];
-        const float2 vi = B.s_vel[i];
-        const float4 ai = B.s_aux[i];
-        const float2 rd = B.s_rd[i];
-        if (outside_box(K, ri.x, ri.y)) {
-            // frozen: keeps its state, takes part in nothing
-            B.st_vel[i] = vi;
-            B.st_rho[i] = rd.x;
-            B.st_a[i] = make_float2(0.f, 0.f);
-            B.st_D[i] = make_float2(0.f, CL == 1 ? B.s_ex[i].z : 0.f);
-            B.st_X[i] = make_float2(0.f, 0.f);
+    auto fluid_pair = [&](int j) {
+        const float2 rj = __ldg(&B.s_pos[j]);
+        const float2 vj = __ldg(&B.s_vel[j]);
+        const float4 aj = __ldg(&B.s_aux[j]);
+        pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                       CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
+    };
+    int base0, base1, base2;
+    unsigned m0, m1, m2;
+    {
+        const int r0 = c - K.ncx, r1 = c, r2 = c + K.ncx;
+        base0 = B.cell_start[r0 - 1];
+        base1 = B.cell_start[r1 - 1];
+        base2 = B.cell_start[r2 - 1];
+        const int e0 = B.cell_start[r0 + 2], e1 = B.cell_start[r1 + 2],
+                  e2 = B.cell_start[r2 + 2];
+        // rows longer than 32 candidates: chunks evaluated right away
+        auto row_mask = [&](int a, int b) -> unsigned {
+            if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri, K.s2);
+#pragma unroll 1
+            for (int base = a; base < b; base += 32) {
+                unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
+                if (i >= base && i < base + 32) m &= ~(1u << (i - base));
+                while (m) {
+                    const int j = base + __ffs(m) - 1;
+                    m &= m - 1u;
+                    fluid_pair(j);
+                }
+            }
+            return 0u;
+        };
+        m0 = row_mask(base0, e0);
+        m1 = row_mask(base1, e1);
+        m2 = row_mask(base2, e2);
+        // the particle itself sits in the middle row
+        if (i >= base1 && i < base1 + 32) m1 &= ~(1u << (i - base1));
+    }
+#pragma unroll 1
+    while ((m0 | m1 | m2) != 0u) {
+        int j;
+        if (m0) {
+            j = base0 + __ffs(m0) - 1;
+            m0 &= m0 - 1u;
+        } else if (m1) {
+            j = base1 + __ffs(m1) - 1;
+            m1 &= m1 - 1u;
         } else {
-            const float ci = CL == 1 ? K.c_av : ai.w;
-            const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
-            Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
-            auto fluid_pair = [&](int j) {
-                const float2 rj = __ldg(&B.s_pos[j]);
-                const float2 vj = __ldg(&B.s_vel[j]);
-                const float4 aj = __ldg(&B.s_aux[j]);
-                pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
-                               CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
-            };
-            const int c = cell_of(K, ri.x, ri.y);
-            int base0, base1, base2;
-            unsigned m0, m1, m2;
-            {
-                const int r0 = c - K.ncx, r1 = c, r2 = c + K.ncx;
-                base0 = B.cell_start[r0 - 1];
-                base1 = B.cell_start[r1 - 1];
-                base2 = B.cell_start[r2 - 1];
-                const int e0 = B.cell_start[r0 + 2], e1 = B.cell_start[r1 + 2],
-                          e2 = B.cell_start[r2 + 2];
-                // rows longer than 32 candidates: chunks evaluated right away
-                auto row_mask = [&](int a, int b) -> unsigned {
-                    if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri, K.s2);
-#pragma unroll 1
-                    for (int base = a; base < b; base += 32) {
-                        unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
-                        if (i >= base && i < base + 32) m &= ~(1u << (i - base));
-                        while (m) {
-                            const int j = base + __ffs(m) - 1;
-                            m &= m - 1u;
-                            fluid_pair(j);
-                        }
-                    }
-                    return 0u;
-                };
-                m0 = row_mask(base0, e0);
-                m1 = row_mask(base1, e1);
-                m2 = row_mask(base2, e2);
-                // the particle itself sits in the middle row
-                if (i >= base1 && i < base1 + 32) m1 &= ~(1u << (i - base1));
+            j = base2 + __ffs(m2) - 1;
+            m2 &= m2 - 1u;
+        }
+        fluid_pair(j);
+    }
+}
+
+// Ghost neighbours and the epilogue of particle i (inside the box), its
+// fluid sums already in A.
+template <int CL>
+__device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int i, float2 ri,
+                                            float2 vi, float4 ai, float2 rd, int c, float dt,
+                                            int prime, const Self &I, Acc &A, PassPart &P)
+{
+    // wall ghosts (static cell list)
+    if (K.nw > 0) {
+        for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+            const float2 rg = __ldg(&B.gw_pos[k]);
+            if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
+            const float4 ag = B.g_aux[k];
+            const float2 vg = B.g_vel[k];
+            const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
+                                            ag.z, CL == 1 ? K.c_av : ag.w,
+                                            K.wall_over_m, false, A);
+            if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
+                const float2 e = __ldg(&B.gw_nrm[k]);
+                P.fw -= f.x * e.x + f.y * e.y;
             }
-#pragma unroll 1
-            while ((m0 | m1 | m2) != 0u) {
-                int j;
-                if (m0) {
-                    j = base0 + __ffs(m0) - 1;
-                    m0 &= m0 - 1u;
-                } else if (m1) {
-                    j = base1 + __ffs(m1) - 1;
-                    m1 &= m1 - 1u;
-                } else {
-                    j = base2 + __ffs(m2) - 1;
-                    m2 &= m2 - 1u;
-                }
-                fluid_pair(j);
+        });
+    }
+    // disk ghosts (the ring, only near the disk)
+    if (K.ng > 0) {
+        const float xc = B.S->xc_f, yc = B.S->yc_f;
+        if (near_disk(K, ri.x, ri.y, xc, yc)) {
+            for (int k = 0; k < K.ng; ++k) {
+                const float2 rg = B.gd_pos[k];
+                if (outside_box(K, rg.x, rg.y)) continue;
+                if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
+                const float4 ag = B.g_aux[K.nw + k];
+                const float2 vg = B.g_vel[K.nw + k];
+                const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
+                                                ag.z, CL == 1 ? K.c_av : ag.w,
+                                                K.disk_over_m, false, A);
+                P.fdx += f.x;
+                P.fdy += f.y;
             }
-            // wall ghosts (static cell list)
-            if (K.nw > 0) {
-                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
-                    const float2 rg = __ldg(&B.gw_pos[k]);
-                    if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
-                    const float4 ag = B.g_aux[k];
-                    const float2 vg = B.g_vel[k];
-                    const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
-                                                    ag.z, CL == 1 ? K.c_av : ag.w,
-                                                    K.wall_over_m, false, A);
-                    if (__ldg(&B.gw_kind[k]) == KIND_SIDE) {
-                        const float2 e = __ldg(&B.gw_nrm[k]);
-                        fw -= f.x * e.x + f.y * e.y;
-                    }
-                });
-            }
-            // disk ghosts (the ring, only near the disk)
-            if (K.ng > 0) {
-                const float xc = B.S->xc_f, yc = B.S->yc_f;
-                if (near_disk(K, ri.x, ri.y, xc, yc)) {
-                    for (int k = 0; k < K.ng; ++k) {
-                        const float2 rg = B.gd_pos[k];
-                        if (outside_box(K, rg.x, rg.y)) continue;
-                        if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
-                        const float4 ag = B.g_aux[K.nw + k];
-                        const float2 vg = B.g_vel[K.nw + k];
-                        const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
-                                                        ag.z, CL == 1 ? K.c_av : ag.w,
-                                                        K.disk_over_m, false, A);
-                        fdx += f.x;
-                        fdy += f.y;
-                    }
-                    const float ddx = ri.x - xc, ddy = ri.y - yc;
-                    npen = ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
-                }
-            }
-            const float ax = fmaf(K.m, A.a.x, K.gx), ay = fmaf(K.m, A.a.y, K.gy);
-            float2 vnew;
-            if constexpr (CL == 1) {
-                // closing kick from the predicted velocity, v^{n+1} = v* +
-                // dt/2 (a^{n+1} - a^n); energy e^{n+1} = e^n + dt/2 (De^n + De^{n+1})
-                const float4 ex = B.s_ex[i];
-                const float De = 0.5f * K.m * A.dr;
-                const float hdt = 0.5f * dt;
-                vnew = make_float2(fmaf(hdt, ax - ex.x, vi.x), fmaf(hdt, ay - ex.y, vi.y));
-                const float enew = fmaf(hdt, ex.w + De, ex.z);
-                if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(enew))
-                    atomicOr(&B.S->status, ST_NAN);
-                B.st_rho[i] = ai.x;
-                B.st_D[i] = make_float2(De, enew);
-            } else {
-                // epilogue: the fluid mass, corrected density, closing half kick (T)
-                const float Dd = A.dr * K.m_over_rho0;
-                const float dnew = band(K, fmaf(dt, Dd, rd.x));
-                vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
-                if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
-                    atomicOr(&B.S->status, ST_NAN);
-                B.st_rho[i] = dnew;
-                B.st_D[i] = make_float2(Dd, prime ? Dd : rd.y);
-            }
-            B.st_vel[i] = vnew;
-            B.st_a[i] = make_float2(ax, ay);
-            B.st_X[i] = make_float2(K.m * A.X.x, K.m * A.X.y);
-            vmax = sqrtf(vnew.x * vnew.x + vnew.y * vnew.y);
-            diss = -K.m * K.m * (vi.x * A.av.x + vi.y * A.av.y);
+            const float ddx = ri.x - xc, ddy = ri.y - yc;
+            P.npen += ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
         }
     }
-    // block partials: FP32 within the warp, FP64 across warps (fixed order)
-    fdx = warp_sum(fdx);
-    fdy = warp_sum(fdy);
-    fw = warp_sum(fw);
-    diss = warp_sum(diss);
-    vmax = warp_max(vmax);
-    npen = warp_sum(npen);
+    const float ax = fmaf(K.m, A.a.x, K.gx), ay = fmaf(K.m, A.a.y, K.gy);
+    float2 vnew;
+    if constexpr (CL == 1) {
+        // closing kick from the predicted velocity, v^{n+1} = v* +
+        // dt/2 (a^{n+1} - a^n); energy e^{n+1} = e^n + dt/2 (De^n + De^{n+1})
+        const float4 ex = B.s_ex[i];
+        const float De = 0.5f * K.m * A.dr;
+        const float hdt = 0.5f * dt;
+        vnew = make_float2(fmaf(hdt, ax - ex.x, vi.x), fmaf(hdt, ay - ex.y, vi.y));
+        const float enew = fmaf(hdt, ex.w + De, ex.z);
+        if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(enew))
+            atomicOr(&B.S->status, ST_NAN);
+        B.st_rho[i] = ai.x;
+        B.st_D[i] = make_float2(De, enew);
+    } else {
+        // epilogue: the fluid mass, corrected density, closing half kick (T)
+        const float Dd = A.dr * K.m_over_rho0;
+        const float dnew = band(K, fmaf(dt, Dd, rd.x));
+        vnew = make_float2(fmaf(0.5f * dt, ax, vi.x), fmaf(0.5f * dt, ay, vi.y));
+        if (!isfinite(vnew.x) || !isfinite(vnew.y) || !isfinite(dnew))
+            atomicOr(&B.S->status, ST_NAN);
+        B.st_rho[i] = dnew;
+        B.st_D[i] = make_float2(Dd, prime ? Dd : rd.y);
+    }
+    B.st_vel[i] = vnew;
+    B.st_a[i] = make_float2(ax, ay);
+    B.st_X[i] = make_float2(K.m * A.X.x, K.m * A.X.y);
+    P.vmax = fmaxf(P.vmax, sqrtf(vnew.x * vnew.x + vnew.y * vnew.y));
+    P.diss += -K.m * K.m * (vi.x * A.av.x + vi.y * A.av.y);
+}
+
+// A frozen particle (outside the box) keeps its state, takes part in nothing.
+template <int CL>
+__device__ __forceinline__ void pass_frozen(const Bufs &B, int i, float2 vi, float2 rd)
+{
+    B.st_vel[i] = vi;
+    B.st_rho[i] = rd.x;
+    B.st_a[i] = make_float2(0.f, 0.f);
+    B.st_D[i] = make_float2(0.f, CL == 1 ? B.s_ex[i].z : 0.f);
+    B.st_X[i] = make_float2(0.f, 0.f);
+}
+
+template <int CL>
+__device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int i, float dt,
+                                            int prime, PassPart &P)
+{
+    const float2 ri = B.s_pos[i];
+    const float2 vi = B.s_vel[i];
+    const float4 ai = B.s_aux[i];
+    const float2 rd = B.s_rd[i];
+    if (outside_box(K, ri.x, ri.y)) {
+        pass_frozen<CL>(B, i, vi, rd);
+        return;
+    }
+    const float ci = CL == 1 ? K.c_av : ai.w;
+    const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
+    Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+    const int c = cell_of(K, ri.x, ri.y);
+    pass_fluid<CL>(K, B, i, ri, c, I, A);
+    pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
+}
+
+// Block partials of a pass block: FP32 within the warp, then a fixed-order
+// sum over the block's warps.
+template <int NT>
+__device__ __forceinline__ void pass_block_partials(const Bufs &B, const int bx, PassPart P)
+{
+    __shared__ float red[NT / 32][5];
+    __shared__ int redn[NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    P.fdx = warp_sum(P.fdx);
+    P.fdy = warp_sum(P.fdy);
+    P.fw = warp_sum(P.fw);
+    P.diss = warp_sum(P.diss);
+    P.vmax = warp_max(P.vmax);
+    P.npen = warp_sum(P.npen);
     if (lane == 0) {
-        red[w][0] = fdx;
-        red[w][1] = fdy;
-        red[w][2] = fw;
-        red[w][3] = diss;
-        red[w][4] = vmax;
-        redn[w] = npen;
+        red[w][0] = P.fdx;
+        red[w][1] = P.fdy;
+        red[w][2] = P.fw;
+        red[w][3] = P.diss;
+        red[w][4] = P.vmax;
+        redn[w] = P.npen;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, v = 0.f;
         int np = 0;
-        for (int k = 0; k < kPassThreads / 32; ++k) {
+        for (int k = 0; k < NT / 32; ++k) {
             a0 += red[k][0];
             a1 += red[k][1];
             a2 += red[k][2];
@@ -1133,6 +1165,16 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
         B.part.vmax[bx] = v;
         B.part.npen[bx] = np;
     }
+}
+
+template <int CL>
+__device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+{
+    const int i = bx * blockDim.x + threadIdx.x;
+    const float dt = prime ? 0.0f : B.S->dt_f;
+    PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (i < K.nf) pass_single<CL>(K, B, i, dt, prime, P);
+    pass_block_partials<kPassThreads>(B, bx, P);
 }
 
 // ----------------------------------- a6, a7: probes, accumulators, gate
