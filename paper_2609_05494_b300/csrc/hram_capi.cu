@@ -25,6 +25,10 @@ namespace {
 constexpr int kDiagFields = 19;
 constexpr int kDiagThreads = 1024;
 constexpr int kTimingEvents = 6;
+// steps per graph launch in hr_run: a small case's step is bound by the
+// latency of its launches, and one graph of several steps leaves out the gaps
+// between graph launches
+constexpr int kMultiSteps = 4;
 
 // ------------------------------------------------ auxiliary device kernels
 
@@ -380,6 +384,9 @@ struct hr_case {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // kMultiSteps steps in one graph, for hr_run (absent with HR_FLAG_TIMING)
+    cudaGraph_t graph_multi = nullptr;
+    cudaGraphExec_t exec_multi = nullptr;
     cudaEvent_t ev[kTimingEvents] = {};
     bool timing = false;
     void *ws = nullptr;
@@ -789,6 +796,18 @@ int capture(hr_case *c)
     CK(e);
     c->graph = g;
     CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    if (!c->timing) {
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        int rcm = HR_OK;
+        for (int q = 0; q < kMultiSteps && rcm == HR_OK; ++q)
+            rcm = launch_step(c, c->cap, 0, false, c->cap2);
+        cudaGraph_t gm = nullptr;
+        const cudaError_t em = cudaStreamEndCapture(c->cap, &gm);
+        if (rcm != HR_OK) return rcm;
+        CK(em);
+        c->graph_multi = gm;
+        CK(cudaGraphInstantiate(&c->exec_multi, c->graph_multi, 0));
+    }
     return HR_OK;
 }
 
@@ -1001,14 +1020,34 @@ int hr_sync(hr_case *c)
     return device_status(c);
 }
 
+// k steps, kMultiSteps per graph launch where no periodic diagnostic falls
+// inside a group.
+static int run_steps(hr_case *c, int64_t k)
+{
+    while (k > 0) {
+        const bool diag = c->P.diag_every > 0;
+        if (c->exec_multi && k >= kMultiSteps && !diag) {
+            if (c->sticky < 0) return c->sticky;
+            if (cudaGraphLaunch(c->exec_multi, c->stream) != cudaSuccess)
+                return c->sticky = HR_ECUDA;
+            c->host_step += kMultiSteps;
+            k -= kMultiSteps;
+        } else {
+            const int rc = hr_step(c);
+            if (rc < 0) return rc;
+            --k;
+        }
+    }
+    return HR_OK;
+}
+
 int hr_run(hr_case *c, int64_t n_steps, double t_end)
 {
     if (!c) return HR_EINVAL;
+    if (!c->exec) return HR_EINVAL;
     if (t_end <= 0.0) {
-        for (int64_t k = 0; k < n_steps; ++k) {
-            const int rc = hr_step(c);
-            if (rc < 0) return rc;
-        }
+        const int rc = run_steps(c, n_steps);
+        if (rc < 0) return rc;
         return device_status(c);
     }
     int64_t done = 0;
@@ -1023,10 +1062,8 @@ int hr_run(hr_case *c, int64_t n_steps, double t_end)
         int64_t k = (int64_t)std::floor((t_end - sc[0]) / sc[1]);
         k = std::max<int64_t>(1, std::min<int64_t>(k / 2, 256));
         if (n_steps > 0) k = std::min<int64_t>(k, n_steps - done);
-        for (int64_t q = 0; q < k; ++q) {
-            const int rc = hr_step(c);
-            if (rc < 0) return rc;
-        }
+        const int rc = run_steps(c, k);
+        if (rc < 0) return rc;
         done += k;
     }
 }
@@ -1626,6 +1663,8 @@ void hr_destroy(hr_case *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->exec_multi) cudaGraphExecDestroy(c->exec_multi);
+    if (c->graph_multi) cudaGraphDestroy(c->graph_multi);
     for (int k = 0; k < kTimingEvents; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->cap) cudaStreamDestroy(c->cap);
