@@ -1,7 +1,8 @@
 // hram_device.cuh -- device data layout and kernels of the planar WCSPH
 // hydrodynamic-ram step on B300 (sm_103a).
 //
-// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is nine kernels:
+// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is nine kernels (ten with the
+// paper's closure, which adds k_density after the sort):
 //   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key and
 //                   in-cell slot (atomic count)                  [T, first half]
 //   k_kinematics     advances t, projectile kinematics (FP64), disk ghost ring
@@ -19,7 +20,8 @@
 // the Tait pressure B((1+d)^7 - 1) = B d (7 + 21 d + ...) then has no
 // cancellation and a pressure of 100 Pa is resolved (an FP32 rho near 1000
 // kg/m^3 resolves only 134 Pa).  Positions and velocities are FP32; time,
-// kinematics, and every global reduction are FP64.
+// kinematics and the accumulated diagnostics are FP64, and the step's global
+// sums are compensated FP32 (two-float) converted to FP64 once.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -954,8 +956,9 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
 // chunks on the spot.  Ghost neighbours follow (static wall lists, then the
 // disk ring).  The epilogue applies the uniform fluid mass, the corrected
 // density and the closing half kick.  Block partials of the ghost forces,
-// the dissipation rate and max |v| are reduced in FP32 per warp and in FP64
-// per block.
+// the dissipation rate and max |v| are reduced in FP32 per warp and over the
+// block's warps in a fixed order; k_finalize sums the block partials in
+// compensated FP32.
 
 // Per-thread partials of a pass block.
 struct PassPart {
