@@ -342,13 +342,17 @@ def paper_event_benchmark(stream):
     planar model's peaks are not parity targets).  Wall clock from the first
     step to the synchronised end."""
     import torch
-    from paper_2609_05494_b300 import Case
+    from paper_2609_05494_b300 import Batch, Case
 
-    def event(dx, alpha, v0):
+    def setup(dx, alpha, v0):
         p = casegen.config_paper(v0)
         p.update(dx=float(dx), alpha=float(alpha))
         xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
                                    disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+        return p, xy
+
+    def event(dx, alpha, v0):
+        p, xy = setup(dx, alpha, v0)
         with torch.cuda.stream(stream):
             c = Case(p, xy, stream=stream)
         torch.cuda.synchronize()
@@ -384,8 +388,30 @@ def paper_event_benchmark(stream):
             r = main if (v0 == 900.0 and a == 0.03) else event(1.5e-3, a, v0)
             alph.append({"v0": v0, "alpha": a, "ptn_peak_MPa": r["ptn_peak_MPa"],
                          "paper_ptn_MPa": paper_alpha[(v0, a)], "wall_s": r["wall_s"]})
+    # the same eight alpha-sweep events as one batch (one launch per kernel
+    # per step for all eight); the batched peaks must equal the lone runs'
+    cases = []
+    with torch.cuda.stream(stream):
+        for r in alph:
+            p, xy = setup(1.5e-3, r["alpha"], r["v0"])
+            cases.append(Case(p, xy, stream=stream))
+        b = Batch(cases, casegen.config_paper(900.0)["t_end"], stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = b.run()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    same = all(float(c.probe_pressure()[:, 0].max()) * 1e-6 == r["ptn_peak_MPa"]
+               for c, r in zip(cases, alph))
+    b.close()
+    for c in cases:
+        c.close()
     main["resolution"] = res
     main["alpha_sweep"] = alph
+    lone = sum(r["wall_s"] for r in alph)
+    main["alpha_sweep_batched"] = {"cases": len(alph), "wall_s": wall, "lone_wall_s": lone,
+                                   "speedup": lone / wall, "peaks_identical": bool(same),
+                                   "status": st}
     main["workload"] = ("paper set-up: 750 x 150 mm, dx = 1.5 mm, %d particles, 900 m/s, "
                         "closure 1, 150 us" % main["particles"])
     return main

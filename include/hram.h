@@ -231,7 +231,10 @@ typedef struct hr_batch hr_batch;
  * orders the blocks of each batched launch: 0 case after case, 1 round robin
  * over the cases, 2 case after case from the largest down (results do not
  * depend on it; the autotuner picks the fastest).  cuda_stream: the stream
- * the batch runs on.  Allocates a small device block for the case tables. */
+ * the batch runs on.  Allocates a small device block for the case tables.
+ * HR_EINVAL if a case is a tangent case, is in an error state, or has a
+ * different closure from cases[0] (one batch runs one closure: closure 1
+ * batches add the batched summation density after the sort). */
 int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedule,
                     void *cuda_stream, hr_batch **out);
 

@@ -418,8 +418,9 @@ struct hr_batch {
     Consts *dK = nullptr;
     Bufs *dB = nullptr;
     int *d_count = nullptr;
-    BatchBlock *map[9] = {};
-    int nblocks[9] = {};
+    BatchBlock *map[10] = {};
+    int nblocks[10] = {};
+    int closure = 0;  // shared by every case of the batch
     long long steps = 0;
 };
 
@@ -1451,7 +1452,8 @@ int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
 
 namespace {
 
-enum BatchKernel { BK_KIN, BK_DRIFT, BK_TILES, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN };
+enum BatchKernel { BK_KIN, BK_DRIFT, BK_TILES, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN, BK_DENS };
+constexpr int kBatchKernels = 10;
 
 __global__ void k_batch_count_done(const Bufs *Bs, int n, int *out)
 {
@@ -1480,11 +1482,20 @@ int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
     kb_scan_tiles<<<b->nblocks[BK_TILES], kScanThreads, 0, s>>>(K, B, b->map[BK_TILES]);
     kb_scan_apply<<<b->nblocks[BK_APPLY], kScanThreads, 0, s>>>(K, B, b->map[BK_APPLY]);
     kb_slot<<<b->nblocks[BK_SLOT], 256, 0, s>>>(K, B, b->map[BK_SLOT]);
-    kb_rank_scatter<<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
-    CK(cudaStreamWaitEvent(s, b->join, 0));
-    kb_ghost<<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
-    kb_pass<<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
-    kb_finalize<<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
+    if (b->closure == 1) {
+        kb_rank_scatter<1><<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
+        CK(cudaStreamWaitEvent(s, b->join, 0));
+        kb_density<<<b->nblocks[BK_DENS], 256, 0, s>>>(K, B, b->map[BK_DENS]);
+        kb_ghost<1><<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
+        kb_pass<1><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        kb_finalize<1><<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
+    } else {
+        kb_rank_scatter<0><<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
+        CK(cudaStreamWaitEvent(s, b->join, 0));
+        kb_ghost<0><<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
+        kb_pass<0><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        kb_finalize<0><<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
+    }
     CK(cudaGetLastError());
     return HR_OK;
 }
@@ -1502,7 +1513,9 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
         return code;
     };
     for (int k = 0; k < n_cases; ++k) {
-        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->K.closure != 0)
+        // one closure per batch (the kernels are templated on it); no tangents
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent ||
+            cases[k]->K.closure != cases[0]->K.closure)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }
@@ -1510,7 +1523,8 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     // per-kernel block maps: (case, local block, blocks of that case), in the
     // order of the schedule: 0 case after case, 1 round robin over the cases,
     // 2 case after case from the largest case down
-    std::vector<BatchBlock> maps[9];
+    b->closure = cases[0]->K.closure;
+    std::vector<BatchBlock> maps[kBatchKernels];
     std::vector<int> order(n_cases);
     std::iota(order.begin(), order.end(), 0);
     if (schedule == 2)
@@ -1519,11 +1533,12 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     auto nblk = [&](int k, int q) {
         const hr_case *c = cases[k];
         const int fin = std::max(4, c->K.n_probes);
-        const int nb[9] = {1, c->drift_blocks, c->n_tiles, c->n_tiles, c->drift_blocks,
-                           c->drift_blocks, c->ghost_blocks, c->pass_blocks, fin};
+        const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->n_tiles,
+                                       c->drift_blocks, c->drift_blocks, c->ghost_blocks,
+                                       c->pass_blocks, fin, c->drift_blocks};
         return nb[q];
     };
-    for (int q = 0; q < 9; ++q) {
+    for (int q = 0; q < kBatchKernels; ++q) {
         if (schedule == 1) {
             int most = 0;
             for (int k = 0; k < n_cases; ++k) most = std::max(most, nblk(k, q));
@@ -1537,8 +1552,8 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
         }
     }
     size_t bytes = align256(sizeof(Consts) * n_cases) + align256(sizeof(Bufs) * n_cases) + 256;
-    size_t off[9];
-    for (int q = 0; q < 9; ++q) {
+    size_t off[kBatchKernels];
+    for (int q = 0; q < kBatchKernels; ++q) {
         off[q] = bytes;
         bytes += align256(maps[q].size() * sizeof(BatchBlock));
     }
@@ -1560,7 +1575,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
             cudaSuccess ||
         cudaMemcpy(b->dB, hb.data(), sizeof(Bufs) * n_cases, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(HR_ECUDA);
-    for (int q = 0; q < 9; ++q) {
+    for (int q = 0; q < kBatchKernels; ++q) {
         b->map[q] = at<BatchBlock>(b->mem, off[q]);
         b->nblocks[q] = (int)maps[q].size();
         if (cudaMemcpy(b->map[q], maps[q].data(), maps[q].size() * sizeof(BatchBlock),

@@ -1515,40 +1515,53 @@ __global__ void __launch_bounds__(256) kb_slot(const Consts *Ks, const Bufs *Bs,
     b_slot(K, B, m.local, m.nlocal);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(256) kb_rank_scatter(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
 {
     __shared__ Consts K;
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_rank_scatter<0>(K, B, m.local, m.nlocal, 0);
+    b_rank_scatter<CL>(K, B, m.local, m.nlocal, 0);
 }
 
+__global__ void __launch_bounds__(256) kb_density(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
+{
+    __shared__ Consts K;
+    __shared__ Bufs B;
+    __shared__ BatchBlock m;
+    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
+    b_density(K, B, m.local, m.nlocal, 0);
+}
+
+template <int CL>
 __global__ void __launch_bounds__(kGhostWarps * 32) kb_ghost(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
 {
     __shared__ Consts K;
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_ghost<0>(K, B, m.local, m.nlocal);
+    b_ghost<CL>(K, B, m.local, m.nlocal);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kPassThreads) kb_pass(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
 {
     __shared__ Consts K;
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_pass<0>(K, B, m.local, m.nlocal, 0);
+    b_pass<CL>(K, B, m.local, m.nlocal, 0);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kFinalizeThreads) kb_finalize(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
 {
     __shared__ Consts K;
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_finalize<0>(K, B, m.local, m.nlocal, 0);
+    b_finalize<CL>(K, B, m.local, m.nlocal, 0);
 }
 
 }  // namespace hr
