@@ -771,8 +771,10 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     else k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-    if (paper) k_finalize<1><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
-    else k_finalize<0><<<kFinalizeBlocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    // kFinalizeBlocks reduction blocks, then one block per probe
+    const int fin_blocks = kFinalizeBlocks + K.n_probes;
+    if (paper) k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    else k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_finalize<<<1, kTFinThreads, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
@@ -1532,7 +1534,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
                          [&](int a, int c) { return cases[a]->nf > cases[c]->nf; });
     auto nblk = [&](int k, int q) {
         const hr_case *c = cases[k];
-        const int fin = std::max(4, c->K.n_probes);
+        const int fin = 4 + c->K.n_probes;  // four reduction blocks, one per probe
         const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->n_tiles,
                                        c->drift_blocks, c->drift_blocks, c->ghost_blocks,
                                        c->pass_blocks, fin, c->drift_blocks};

@@ -885,7 +885,7 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
     const float2 d = p2_sub(I.r, rj);
     const float dx = d.x, dy = d.y;
     const float r2 = fmaf(dx, dx, dy * dy);
-    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));     // 0 for coincident particles
     float t = 0.0f, t3 = 0.0f, F;
     if constexpr (CL == 1) {
         F = mj * cubic_F(K, r);
@@ -1220,12 +1220,13 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
     return 0.0f;
 }
 
-// Closes the step.  kFinalizeBlocks blocks reduce slices of the pass and
-// ghost partials; the block that finishes last (atomic ticket) reduces the
-// block results, updates the FP64 accumulators and applies the CFL gate (a6).
-// Block q < n_probes first samples wall probe q (a7) into probe_now[q].  The
-// sums are compensated FP32 (two-float) in a fixed tree order, converted to
-// FP64 once at the end.
+// Closes the step.  The first nbx - n_probes blocks reduce slices of the
+// pass and ghost partials; each of the last n_probes blocks samples one wall
+// probe (a7) into probe_now, so the probes and the reduction run side by
+// side.  The block that finishes last (atomic ticket) reduces the block
+// results, updates the FP64 accumulators and applies the CFL gate (a6); its
+// scalar updates are split over three warps.  The sums are compensated FP32
+// (two-float) in a fixed tree order, converted to FP64 once at the end.
 template <int CL>
 __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
@@ -1240,11 +1241,8 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     __shared__ float totv;
     __shared__ int totn;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nb = nbx;
-    if (!prime && (int)bx < K.n_probes && w == 0) {
-        const float pv = probe_value<CL>(K, B, K.probe_x[bx], K.probe_y[bx]);
-        if (lane == 0) B.probe_now[bx] = pv;
-    }
+    const int nb = nbx - K.n_probes;  // reduction blocks
+    const bool probe_block = bx >= nb;
     // reduce one (value per thread) set of four sums, max and count over the
     // block; the results land in tot[] (lane 0 of warp 0 writes them)
     auto block_reduce = [&](F2 a0, F2 a1, F2 a2, F2 a3, float v, int np) {
@@ -1284,7 +1282,19 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         }
         __syncthreads();
     };
-    {
+    if (probe_block) {
+        if (w == 0) {
+            const int q = bx - nb;
+            if (!prime) {
+                const float pv = probe_value<CL>(K, B, K.probe_x[q], K.probe_y[q]);
+                if (lane == 0) B.probe_now[q] = pv;
+            }
+            if (lane == 0) {
+                __threadfence();
+                is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
+            }
+        }
+    } else {
         F2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
         float vmax = 0.0f;
         int npen = 0;
@@ -1302,16 +1312,16 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
              b += nb * blockDim.x)
             vmax = fmaxf(vmax, B.ghost_vmax[b]);
         block_reduce(a0, a1, a2, a3, vmax, npen);
-    }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k) {
-            B.fin_part[bx * 8 + 2 * k] = tot[k].hi;
-            B.fin_part[bx * 8 + 2 * k + 1] = tot[k].lo;
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 4; ++k) {
+                B.fin_part[bx * 8 + 2 * k] = tot[k].hi;
+                B.fin_part[bx * 8 + 2 * k + 1] = tot[k].lo;
+            }
+            B.fin_vmax[bx] = totv;
+            B.fin_npen[bx] = totn;
+            __threadfence();
+            is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
         }
-        B.fin_vmax[bx] = totv;
-        B.fin_npen[bx] = totn;
-        __threadfence();
-        is_last = atomicAdd(B.fin_ticket, 1) == nb - 1;
     }
     __syncthreads();
     if (!is_last) return;
@@ -1334,17 +1344,17 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     }
     if (threadIdx.x < K.n_probes) probe_p[threadIdx.x] = __ldcg(&B.probe_now[threadIdx.x]);
     __syncthreads();
+    // the step's own dt and index, read by every thread before any update
+    const double dt = S.dt;
+    const long long k = S.step;
+    const double m2 = (double)K.m * (double)K.m;
+    __syncthreads();
     if (threadIdx.x == 0) {
         *B.fin_ticket = 0;
-        const double dt = S.dt;
-        const double m2 = (double)K.m * (double)K.m;
-        const double F0 = m2 * ((double)tot[0].hi + (double)tot[0].lo);
-        const double F2w = m2 * ((double)tot[2].hi + (double)tot[2].lo);
-        const double Dr = (double)tot[3].hi + (double)tot[3].lo;
-        S.Fdx = F0;
+        S.Fdx = m2 * ((double)tot[0].hi + (double)tot[0].lo);
         S.Fdy = m2 * ((double)tot[1].hi + (double)tot[1].lo);
-        S.Fwall = F2w;
-        S.diss_rate = Dr;
+        S.Fwall = m2 * ((double)tot[2].hi + (double)tot[2].lo);
+        S.diss_rate = (double)tot[3].hi + (double)tot[3].lo;
         if (totn > 0) S.status |= ST_PENETRATION;
         // a6: CFL gate over fluid and ghost velocities, FP32 (a float ulp of
         // dt is far below every tolerance); dt_mode 1 uses the fixed host value
@@ -1359,15 +1369,7 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         }
         if (!(dtn > 1e-14)) S.status |= ST_DT;
         if (!prime) {
-            S.Wb += dt * (F0 * S.vproj);
-            S.impulse += dt * F2w;
-            S.diss += dt * Dr;
-            const long long k = S.step;
             if (k < K.probe_cap) {
-                for (int q = 0; q < K.n_probes; ++q) {
-                    B.probe_hist[k * K.n_probes + q] = probe_p[q];
-                    S.probe_imp[q] += dt * (double)probe_p[q];
-                }
                 B.probe_t[k] = S.t;
                 S.hist_n = k + 1;
             } else if (K.n_probes > 0) {
@@ -1380,6 +1382,21 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         S.dt_prev = prime ? dtn : dt;
         S.dt = dtn;
         S.dt_f = dtf;
+    } else if (threadIdx.x == 32) {
+        // the FP64 time integrals, beside thread 0 (another warp)
+        if (!prime) {
+            const double F0 = m2 * ((double)tot[0].hi + (double)tot[0].lo);
+            S.Wb += dt * (F0 * S.vproj);
+            S.impulse += dt * (m2 * ((double)tot[2].hi + (double)tot[2].lo));
+            S.diss += dt * ((double)tot[3].hi + (double)tot[3].lo);
+        }
+    } else if (threadIdx.x >= 64 && threadIdx.x < 64 + K.n_probes) {
+        // one probe per thread: its history entry and its impulse
+        const int q = threadIdx.x - 64;
+        if (!prime && k < K.probe_cap) {
+            B.probe_hist[k * K.n_probes + q] = probe_p[q];
+            S.probe_imp[q] += dt * (double)probe_p[q];
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
