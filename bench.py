@@ -609,7 +609,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
-        "gpu_launches": 9 * args.steps,
+        "gpu_launches": 8 * args.steps,
         "roofline": {"kernel": "k_pass", "bound": "alu", "achieved": achieved_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
                      "traffic": traffic,

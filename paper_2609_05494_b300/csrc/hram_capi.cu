@@ -749,7 +749,6 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
-    k_scan_tiles<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
     const bool paper = K.closure == 1;
@@ -845,6 +844,7 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
     CK(cudaMemsetAsync(c->B.st_D, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.st_X, 0, n * 8, c->stream));
     CK(cudaMemsetAsync(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(c->B.tile_sum, 0, (size_t)c->n_tiles * 4, c->stream));
     CK(cudaMemsetAsync(c->B.fin_ticket, 0, 4, c->stream));
     CK(cudaMemsetAsync(c->B.S, 0, sizeof(Scalars), c->stream));
     if (c->tangent) {
@@ -1402,6 +1402,7 @@ int hr_load_state(hr_case *c, const char *path)
     CK(cudaMemcpy(c->B.st_X, X.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.s_id, id.data(), n * 4, cudaMemcpyHostToDevice));
     CK(cudaMemset(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4));
+    CK(cudaMemset(c->B.tile_sum, 0, (size_t)c->n_tiles * 4));
     CK(cudaMemset(c->B.fin_ticket, 0, 4));
     CK(cudaMemcpy(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice));
     if (hn > 0 && c->K.n_probes > 0) {
@@ -1454,8 +1455,8 @@ int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
 
 namespace {
 
-enum BatchKernel { BK_KIN, BK_DRIFT, BK_TILES, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN, BK_DENS };
-constexpr int kBatchKernels = 10;
+enum BatchKernel { BK_KIN, BK_DRIFT, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN, BK_DENS };
+constexpr int kBatchKernels = 9;
 
 __global__ void k_batch_count_done(const Bufs *Bs, int n, int *out)
 {
@@ -1481,7 +1482,6 @@ int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
     kb_kinematics<<<b->nblocks[BK_KIN], 128, 0, side>>>(K, B, b->map[BK_KIN]);
     CK(cudaEventRecord(b->join, side));
     kb_drift_key<<<b->nblocks[BK_DRIFT], 256, 0, s>>>(K, B, b->map[BK_DRIFT]);
-    kb_scan_tiles<<<b->nblocks[BK_TILES], kScanThreads, 0, s>>>(K, B, b->map[BK_TILES]);
     kb_scan_apply<<<b->nblocks[BK_APPLY], kScanThreads, 0, s>>>(K, B, b->map[BK_APPLY]);
     kb_slot<<<b->nblocks[BK_SLOT], 256, 0, s>>>(K, B, b->map[BK_SLOT]);
     if (b->closure == 1) {
@@ -1535,9 +1535,9 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     auto nblk = [&](int k, int q) {
         const hr_case *c = cases[k];
         const int fin = 4 + c->K.n_probes;  // four reduction blocks, one per probe
-        const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->n_tiles,
-                                       c->drift_blocks, c->drift_blocks, c->ghost_blocks,
-                                       c->pass_blocks, fin, c->drift_blocks};
+        const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->drift_blocks,
+                                       c->drift_blocks, c->ghost_blocks, c->pass_blocks, fin,
+                                       c->drift_blocks};
         return nb[q];
     };
     for (int q = 0; q < kBatchKernels; ++q) {

@@ -1,14 +1,14 @@
 // hram_device.cuh -- device data layout and kernels of the planar WCSPH
 // hydrodynamic-ram step on B300 (sm_103a).
 //
-// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is nine kernels (ten with the
+// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is eight kernels (nine with the
 // paper's closure, which adds k_density after the sort):
 //   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key and
 //                   in-cell slot (atomic count)                  [T, first half]
 //   k_kinematics     advances t, projectile kinematics (FP64), disk ghost ring
 //                    (a branch of the step graph, beside the drift and sort)
-//   k_scan_tiles     tile sums of the cell counts
-//   k_scan_apply     cell starts (each block scans the tile sums before it)
+//   k_scan_apply     cell starts (each block scans the tile sums before it;
+//                    k_drift_key counts the tile sums beside the cells)
 //   k_slot           provisional scatter of old indices into cell order
 //   k_rank_scatter   stable rank by fluid ID inside the cell, SoA reorder,
 //                    Tait pressure of the predicted density
@@ -492,6 +492,41 @@ __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, cons
     if (key >= 0 && lane == head) slot0 = atomicAdd(&B.cell_count[key], len);
     slot0 = __shfl_sync(0xffffffffu, slot0, head);
     if (key >= 0) B.u_slot[i] = slot0 + (lane - head);
+    // The scan's tile sums, counted here too.  A block's particles, in the
+    // previous step's cell order, almost always fall in one tile: then one
+    // atomic adds the block's count.  Otherwise each warp adds its own (one
+    // atomic per warp whose keys share a tile, else one per particle).
+    __shared__ int t_lo[32], t_hi[32], t_n[32];
+    __shared__ int one_tile;
+    const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int tile = key >= 0 ? key / kScanTile : -1;
+    const int wlo = __reduce_min_sync(0xffffffffu, key >= 0 ? tile : 0x7fffffff);
+    const int whi = __reduce_max_sync(0xffffffffu, tile);
+    const int wn = __popc(__ballot_sync(0xffffffffu, key >= 0));
+    if (lane == 0) {
+        t_lo[w] = wlo;
+        t_hi[w] = whi;
+        t_n[w] = wn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int lo = 0x7fffffff, hi = -1, n = 0;
+        for (int k = 0; k < nw; ++k) {
+            lo = min(lo, t_lo[k]);
+            hi = max(hi, t_hi[k]);
+            n += t_n[k];
+        }
+        one_tile = lo == hi;
+        if (lo == hi && n > 0) atomicAdd(&B.tile_sum[lo], n);
+    }
+    __syncthreads();
+    if (!one_tile) {
+        if (wlo == whi) {
+            if (lane == 0 && wn > 0) atomicAdd(&B.tile_sum[wlo], wn);
+        } else if (key >= 0) {
+            atomicAdd(&B.tile_sum[tile], 1);
+        }
+    }
 }
 
 // The per-particle part of b_drift_key; returns the cell key.
@@ -604,27 +639,10 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
     }
 }
 
-// Tile sums of the cell counts (ncell + 1 entries), one block per tile.
-__device__ __forceinline__ void b_scan_tiles(const Consts &K, const Bufs &B, const int bx, const int nbx)
-{
-    __shared__ int red[kScanThreads / 32];
-    const int n = K.ncell + 1;
-    const int base = bx * kScanTile + threadIdx.x * kScanItems;
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) s += (base + k < n) ? B.cell_count[base + k] : 0;
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int t = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
-        t = warp_sum(t);
-        if (threadIdx.x == 0) B.tile_sum[bx] = t;
-    }
-}
-
-// Cell starts: each block adds up the sums of the tiles before it, then an
-// exclusive scan of its own tile; the counts are reset for the next step.
+// Cell starts: each block adds up the sums of the tiles before it (counted
+// by k_drift_key), then an exclusive scan of its own tile; the counts are
+// reset for the next step (the tile sums in k_slot, once every block here
+// has read them).
 __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int wsum[kScanThreads / 32];
@@ -662,9 +680,14 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
 }
 
-// Provisional scatter of the IDs by (cell start + atomic slot).
+// Provisional scatter of the IDs by (cell start + atomic slot).  Block 0
+// also clears the tile sums for the next step's k_drift_key.
 __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
+    if (bx == 0) {
+        const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
+        for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
+    }
     const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
     const int dst = B.cell_start[B.u_key[i]] + B.u_slot[i];
@@ -1138,12 +1161,16 @@ __device__ __forceinline__ void pass_block_partials(const Bufs &B, const int bx,
     __shared__ float red[NT / 32][5];
     __shared__ int redn[NT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    P.fdx = warp_sum(P.fdx);
-    P.fdy = warp_sum(P.fdy);
-    P.fw = warp_sum(P.fw);
+    // most warps meet no ghost: their ghost sums are all zero, and lane 0
+    // already holds the warp's sum
+    if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0)) {
+        P.fdx = warp_sum(P.fdx);
+        P.fdy = warp_sum(P.fdy);
+        P.fw = warp_sum(P.fw);
+        P.npen = warp_sum(P.npen);
+    }
     P.diss = warp_sum(P.diss);
     P.vmax = warp_max(P.vmax);
-    P.npen = warp_sum(P.npen);
     if (lane == 0) {
         red[w][0] = P.fdx;
         red[w][1] = P.fdy;
@@ -1416,11 +1443,6 @@ __global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
     b_kinematics(K, B, blockIdx.x, gridDim.x, prime);
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Consts K, Bufs B)
-{
-    b_scan_tiles(K, B, blockIdx.x, gridDim.x);
-}
-
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
 {
     b_scan_apply(K, B, blockIdx.x, gridDim.x);
@@ -1503,15 +1525,6 @@ __global__ void __launch_bounds__(128) kb_kinematics(const Consts *Ks, const Buf
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
     b_kinematics(K, B, m.local, m.nlocal, 0);
-}
-
-__global__ void __launch_bounds__(kScanThreads) kb_scan_tiles(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
-{
-    __shared__ Consts K;
-    __shared__ Bufs B;
-    __shared__ BatchBlock m;
-    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_scan_tiles(K, B, m.local, m.nlocal);
 }
 
 __global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
