@@ -744,6 +744,36 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     if (B.perm_dst) B.perm_dst[i] = dst;
 }
 
+// Predicate mask of the candidates [base, base + cnt), cnt <= 32, in fixed
+// blocks of kMaskChunk candidates: each block is unrolled with constant bit
+// positions, and the warp's trip count is the largest ceil(cnt / kMaskChunk)
+// of its lanes (rows of 17-24 candidates all take three blocks of 8).  The
+// last block reads up to kMaskChunk - 1 entries past the row; the position
+// array is padded by kPosPad entries so those reads stay inside it, and
+// their bits are masked off.
+#ifndef HR_MASK_CHUNK
+#define HR_MASK_CHUNK 8
+#endif
+constexpr int kMaskChunk = HR_MASK_CHUNK;
+constexpr int kPosPad = 32;
+__device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float2 ri,
+                                                 float s2)
+{
+    unsigned m = 0u;
+    const float2 *pp = pos + base;
+#pragma unroll 1
+    for (int k0 = 0; k0 < cnt; k0 += kMaskChunk) {
+        unsigned sub = 0u;
+#pragma unroll
+        for (int u = 0; u < kMaskChunk; ++u)
+            sub |= (unsigned)in_support2(ri, __ldg(pp + k0 + u), s2) << u;
+        const int rem = cnt - k0;
+        if (rem < kMaskChunk) sub &= (1u << rem) - 1u;
+        m |= sub << k0;
+    }
+    return m;
+}
+
 // ------------------------------------- closure 1: summation density
 
 // rho_i = sum_j m_j W_ij over the particle itself, its fluid neighbours and
@@ -768,11 +798,25 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
         };
         float S = K.self_w - 1.0f;
         const int c = cell_of(K, ri.x, ri.y);
-        for_fluid_candidates(K, B.cell_start, c, [&](int j) {
-            const float2 rj = __ldg(&B.s_pos[j]);
-            if (j == i || !in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) return;
-            S = fmaf(K.m_over_rho0, w_at(rj.x, rj.y), S);
-        });
+        // the three stencil rows: predicate masks over blocks of up to 32
+        // candidates (unrolled, independent loads), then the set bits in
+        // ascending order
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int row = c + dy * K.ncx;
+            const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+#pragma unroll 1
+            for (int base = a; base < b; base += 32) {
+                unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
+                if (i >= base && i < base + 32) m &= ~(1u << (i - base));
+                while (m) {
+                    const int j = base + __ffs(m) - 1;
+                    m &= m - 1u;
+                    const float2 rj = __ldg(&B.s_pos[j]);
+                    S = fmaf(K.m_over_rho0, w_at(rj.x, rj.y), S);
+                }
+            }
+        }
         if (K.nw > 0) {
             const float mw = K.m_over_rho0 * K.wall_over_m;
             for_fluid_candidates(K, B.wall_start, c, [&](int k) {
@@ -938,36 +982,6 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
         A.X = p2_fma(make_float2(wx, wx), v, A.X);
     }
     return f;
-}
-
-// Predicate mask of the candidates [base, base + cnt), cnt <= 32, in fixed
-// blocks of kMaskChunk candidates: each block is unrolled with constant bit
-// positions, and the warp's trip count is the largest ceil(cnt / kMaskChunk)
-// of its lanes (rows of 17-24 candidates all take three blocks of 8).  The
-// last block reads up to kMaskChunk - 1 entries past the row; the position
-// array is padded by kPosPad entries so those reads stay inside it, and
-// their bits are masked off.
-#ifndef HR_MASK_CHUNK
-#define HR_MASK_CHUNK 8
-#endif
-constexpr int kMaskChunk = HR_MASK_CHUNK;
-constexpr int kPosPad = 32;
-__device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float2 ri,
-                                                 float s2)
-{
-    unsigned m = 0u;
-    const float2 *pp = pos + base;
-#pragma unroll 1
-    for (int k0 = 0; k0 < cnt; k0 += kMaskChunk) {
-        unsigned sub = 0u;
-#pragma unroll
-        for (int u = 0; u < kMaskChunk; ++u)
-            sub |= (unsigned)in_support2(ri, __ldg(pp + k0 + u), s2) << u;
-        const int rem = cnt - k0;
-        if (rem < kMaskChunk) sub &= (1u << rem) - 1u;
-        m |= sub << k0;
-    }
-    return m;
 }
 
 // The fused interaction pass.  One thread per sorted fluid particle i.
