@@ -499,6 +499,7 @@ void make_consts(hr_case *c)
     K.R2 = (float)(P.R_disk * P.R_disk);
     const double reach = P.R_disk + 1.02 * s;
     K.disk_reach2 = (float)(reach * reach);
+    K.ng_over_2pi = (float)((double)c->ng / (2.0 * M_PI));
     K.cfl_h = P.cfl * h;
     K.cfl_h_f = (float)K.cfl_h;
     K.dt_fixed = K.cfl_h / (P.c0 + P.v0);

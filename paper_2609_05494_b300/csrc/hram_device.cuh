@@ -63,6 +63,7 @@ struct Consts {
     // ghosts
     int nf, nw, ng;
     float m_wall, m_disk, wall_over_m, disk_over_m, m_over_rho0, m2Wc, R, disk_reach2, R2;
+    float ng_over_2pi;  // disk ghosts per radian of the ring
     // CFL and kinematics (FP64)
     double cfl_h, c0d, v0, tau, t_ramp, x_c0, y_c0, a_const, drag_k, dt_fixed, disk_mass;
     float cfl_h_f;
@@ -461,6 +462,47 @@ __device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, flo
     return dx * dx + dy * dy < K.disk_reach2;
 }
 
+// The disk ghosts that can lie within the support of a point near the disk.
+// Ghost k sits at angle 2 pi k / ng on the circle of radius R about the
+// centre, so at distance rho from the centre only ghosts within the angle
+// acos((rho^2 + R^2 - (2h)^2) / (2 rho R)) of the point's own angle can (the
+// law of cosines); three ghosts on each side are added against rounding.
+// The arc is returned as at most two ascending index ranges [a0, a1) and
+// [b0, b1), so a loop over them visits its ghosts in the order of a loop over
+// the whole ring, and the support test still decides each one.
+struct DiskArc {
+    int a0, a1, b0, b1;
+};
+
+__device__ __forceinline__ DiskArc disk_arc(const Consts &K, float x, float y, float xc, float yc)
+{
+    const DiskArc all{0, K.ng, 0, 0};
+    const float dx = x - xc, dy = y - yc;
+    const float rho = sqrtf(dx * dx + dy * dy);
+    if (!(rho > 1e-3f * K.R)) return all;
+    const float c = (rho * rho + K.R2 - K.s2) / (2.0f * rho * K.R);
+    if (!(c > -1.0f)) return all;
+    const float half = acosf(fminf(c, 1.0f)) * K.ng_over_2pi + 3.0f;
+    if (!(2.0f * half + 3.0f < (float)K.ng)) return all;   // the two ranges never overlap
+    float phi = atan2f(dy, dx);
+    if (phi < 0.0f) phi += 6.2831853f;
+    const float kc = phi * K.ng_over_2pi;
+    const int k0 = (int)floorf(kc - half), k1 = (int)ceilf(kc + half);   // inclusive
+    if (k0 < 0) return DiskArc{0, k1 + 1, k0 + K.ng, K.ng};
+    if (k1 >= K.ng) return DiskArc{0, k1 + 1 - K.ng, k0, K.ng};
+    return DiskArc{k0, k1 + 1, 0, 0};
+}
+
+// f(k) for the ghosts of the arc, in ascending k.
+template <class F>
+__device__ __forceinline__ void for_disk_arc(const DiskArc &A, F &&f)
+{
+#pragma unroll 1
+    for (int k = A.a0; k < A.a1; ++k) f(k);
+#pragma unroll 1
+    for (int k = A.b0; k < A.b1; ++k) f(k);
+}
+
 // ----------------------------------------------------- a2: drift and key
 
 __device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, int prime);
@@ -824,14 +866,15 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
                 if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) S = fmaf(mw, w_at(rg.x, rg.y), S);
             });
         }
-        if (K.ng > 0 && near_disk(K, ri.x, ri.y, B.S->xc_f, B.S->yc_f)) {
+        const float xc = B.S->xc_f, yc = B.S->yc_f;
+        if (K.ng > 0 && near_disk(K, ri.x, ri.y, xc, yc)) {
             const float md = K.m_over_rho0 * K.disk_over_m;
-            for (int k = 0; k < K.ng; ++k) {
+            for_disk_arc(disk_arc(K, ri.x, ri.y, xc, yc), [&](int k) {
                 const float2 rg = B.gd_pos[k];
                 if (outside_box(K, rg.x, rg.y) || !in_support(ri.x, ri.y, rg.x, rg.y, K.s2))
-                    continue;
+                    return;
                 S = fmaf(md, w_at(rg.x, rg.y), S);
-            }
+            });
         }
         d = band(K, S);
         e = fmaf(prime ? 0.0f : B.S->dt_f, ex.w, ex.z);
@@ -1089,10 +1132,10 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
     if (K.ng > 0) {
         const float xc = B.S->xc_f, yc = B.S->yc_f;
         if (near_disk(K, ri.x, ri.y, xc, yc)) {
-            for (int k = 0; k < K.ng; ++k) {
+            for_disk_arc(disk_arc(K, ri.x, ri.y, xc, yc), [&](int k) {
                 const float2 rg = B.gd_pos[k];
-                if (outside_box(K, rg.x, rg.y)) continue;
-                if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) continue;
+                if (outside_box(K, rg.x, rg.y)) return;
+                if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
                 const float4 ag = B.g_aux[K.nw + k];
                 const float2 vg = B.g_vel[K.nw + k];
                 const float2 f = pair_terms<CL>(K, I, rg, vg, fmaf(K.rho0, ag.x, K.rho0),
@@ -1100,7 +1143,7 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
                                                 K.disk_over_m, false, A);
                 P.fdx += f.x;
                 P.fdy += f.y;
-            }
+            });
             const float ddx = ri.x - xc, ddy = ri.y - yc;
             P.npen += ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
         }
