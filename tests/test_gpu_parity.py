@@ -81,6 +81,30 @@ def test_neighbour_sets_shuffled_order_several_scan_tiles():
 
 # ------------------------------------------------------------- one step
 
+@pytest.mark.parametrize("closure", [0, 1])
+@pytest.mark.parametrize("ng,R", [(7, 1.5e-3), (100, 5e-3), (400, 8e-3)])
+def test_one_step_around_the_disk_ring(ng, R, closure):
+    # The disk ring is scanned only over the arc of ghosts that can be in
+    # support.  A ring of 7 ghosts smaller than the support (2.6 mm), the
+    # usual 100 and a dense 400, the disk moving inside a patch of fluid, a
+    # jittered lattice all round it and five particles inside the disk: one
+    # step against the oracle, where every ghost is tested.
+    p, xy = impact_case(Lx=0.04, W=0.04, dx=1e-3, jitter=0.2, Ng=ng, R_disk=R, x_c0=0.02,
+                        v0=60.0, t_ramp=0.0, closure=closure, probes=[(0.01, 0.02)])
+    centre = np.array([p["x_c0"], p["y_c0"]])
+    inside = centre + np.array([[0.0, 0.0], [0.3, 0.1], [-0.5, 0.4], [0.2, -0.7], [0.8, 0.0]]) * R
+    xy = np.vstack([xy, inside.astype(np.float32)])
+    g, o = both(p, xy)
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+
+
 @pytest.mark.parametrize("state", ["rest_impact", "perturbed"])
 def test_one_step_density_pressure(state):
     p, xy = impact_case()
