@@ -148,22 +148,30 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
                  const float *rho, void *d_workspace, size_t workspace_bytes,
                  void *cuda_stream, hr_case **out);
 
-/* One step (graph replay), asynchronous.  Returns the last known status. */
+/* One time step U^{n+1} = T(L(G(U^n))) (operator order of Section 4.6; the
+ * velocity Stoermer-Verlet advance with the CFL gate of Section 2.5, eq. cfl),
+ * replayed from the captured step graph, asynchronous.  Returns the last
+ * known status. */
 int hr_step(hr_case *c);
 
-/* n_steps steps; with t_end > 0 stops at the first step that reaches t_end
- * (n_steps <= 0 then means "until t_end").  Synchronises and returns the
- * device status. */
+/* n_steps steps of hr_step (Sections 4.6 and 2.5); with t_end > 0 stops at
+ * the first step that reaches t_end (n_steps <= 0 then means "until t_end"),
+ * the event window of the paper's runs (Section 3).  Synchronises and
+ * returns the device status. */
 int hr_run(hr_case *c, int64_t n_steps, double t_end);
 
 /* Waits for the case's work and returns the device status. */
 int hr_sync(hr_case *c);
 
-/* Probe pressure history, row k = [p_probe0 .. p_probe(n-1)] after step k+1
- * (float, host, cap_rows x n_probes).  *n_rows = rows recorded. */
+/* Probe pressure history (the wall pressure stations of Section 3, the
+ * paper's PTn and PTf), row k = [p_probe0 .. p_probe(n-1)] after step k+1
+ * (float, host, cap_rows x n_probes).  Each value is the Adami wall-ghost
+ * formula (eq. adami-p with the wall at rest) evaluated at the probe point
+ * over the end-of-step fluid, cutoff applied.  *n_rows = rows recorded. */
 int hr_probe_pressure(hr_case *c, float *host_out, int64_t cap_rows, int64_t *n_rows);
 
-/* Simulated time after step k+1 (double, host). */
+/* Simulated time t^{k+1} after step k+1 (double, host): the time axis of the
+ * probe histories (Section 3), a sum of the CFL steps of eq. cfl. */
 int hr_probe_times(hr_case *c, double *host_out, int64_t cap, int64_t *n);
 
 /* FP64 diagnostics of the current state (synchronises). */
@@ -173,8 +181,11 @@ int hr_diagnostics(hr_case *c, hr_diag *out);
  * hr_diag field order.  *n_rows = rows recorded. */
 int hr_diag_history(hr_case *c, double *host_out, int64_t cap_rows, int64_t *n_rows);
 
-/* Current fluid state in ID order (any pointer may be NULL).  xy, vel: cap x 2;
- * rho, p: cap.  cap must be >= n_fluid (else HR_ERANGE).  Synchronises. */
+/* Current fluid state in ID order (any pointer may be NULL): positions,
+ * velocities, densities and the pressure of the equation of state (Section
+ * 2.2: Tait with the cavitation cutoff for closure 0, eq. eos for closure 1)
+ * at the end of the last step.  xy, vel: cap x 2; rho, p: cap.  cap must be
+ * >= n_fluid (else HR_ERANGE).  Synchronises. */
 int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_t cap);
 
 /* Closure 1 only: specific internal energy e [J/kg] and its rate De [W/kg]
@@ -287,7 +298,10 @@ int hr_tangent_outputs(hr_case *c, double *out, int n);
  * copies them to host_counts (caller-owned, cap >= number of points).
  *
  * Limit: HR_STATIC_NEIGHBOR_MAX points (fluid + ghosts); larger cases are
- * rejected with HR_ERANGE before any device work.  The fixed array (4 bytes
+ * rejected with HR_ERANGE before any device work.  The case's device (the one
+ * current at hr_init_case) must be the current device: the array's address
+ * differs between devices, and a call made with another device current
+ * returns HR_EINVAL.  The fixed array (4 bytes
  * per point, 8 MiB) is resident on every device that loads the library until
  * the process exits.  The first call on a device looks up the array's device
  * address for that device (cudaGetSymbolAddress); make that first call before

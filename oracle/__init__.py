@@ -26,7 +26,8 @@ _lib = None
 N_PROBE_MAX = 16
 
 MUT = dict(ghost_printed_sign=1, drop_pj=2, kernel_norm=4, av_sign=8, dt_no_ghosts=16,
-           grad_sign=32, ghost_vel=64, energy_half=128, sum_no_self=256)
+           grad_sign=32, ghost_vel=64, energy_half=128, sum_no_self=256, xsph_gradw=512,
+           xsph_rhoj=1024, lam_half=2048, av_const_c=4096)
 
 DIAG_FIELDS = ("mass", "px", "py", "KE", "PE", "E_el", "rho_min", "rho_max", "p_min",
                "p_max", "vmax_fluid", "n_in", "penetrated", "t", "dt", "W_boundary",
@@ -60,10 +61,13 @@ class OracleParams(C.Structure):
 
 
 def _build() -> None:
+    # a per-process temporary name: processes that build at the same time
+    # each write their own file, and the rename is atomic
+    tmp = "%s.%d.tmp" % (_LIB, os.getpid())
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(_LIB + ".tmp", _LIB)
+    os.replace(tmp, _LIB)
 
 
 def build() -> str:

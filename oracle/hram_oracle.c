@@ -51,7 +51,11 @@ enum {
     MUT_GRAD_SIGN = 32,          /* grad W pointing the wrong way */
     MUT_GHOST_VEL = 64,          /* v_g = v_w + <v>  instead of 2 v_w - <v> */
     MUT_ENERGY_HALF = 128,       /* energy equation without its factor 1/2 */
-    MUT_SUM_NO_SELF = 256        /* summation density without the particle itself */
+    MUT_SUM_NO_SELF = 256,       /* summation density without the particle itself */
+    MUT_XSPH_GRADW = 512,        /* XSPH weighted by |dW/dr| instead of W */
+    MUT_XSPH_RHOJ = 1024,        /* XSPH with m_j / rho_j instead of m_j / rhobar_ij */
+    MUT_LAM_HALF = 2048,         /* laminar term with 2 nu instead of 4 nu */
+    MUT_AV_CONST_C = 4096        /* artificial viscosity with c0 instead of cbar_ij */
 };
 
 typedef struct {
@@ -635,7 +639,8 @@ static void interaction_operator(orc_case *c)
             int compress = (c->P.mutation & MUT_AV_SIGN) ? vr > 0.0 : vr < 0.0;
             if (compress) {
                 double mu = h * vr / (r2 + eh2);
-                double cbar = 0.5 * (ci + sound_speed(c, rhoj));
+                double cbar = (c->P.mutation & MUT_AV_CONST_C)
+                                  ? c->P.c0 : 0.5 * (ci + sound_speed(c, rhoj));
                 double rhobar = 0.5 * (rhoi + rhoj);
                 Pij = -c->P.alpha * cbar * mu / rhobar;
             }
@@ -646,7 +651,8 @@ static void interaction_operator(orc_case *c)
             double fx = -mj * (Pi_ + Pj + Pij) * F * rx;
             double fy = -mj * (Pi_ + Pj + Pij) * F * ry;
             /* laminar viscosity */
-            double lam = mj * 4.0 * c->nu * (F * r2) / ((rhoi + rhoj) * (r2 + eh2));
+            double lam = mj * ((c->P.mutation & MUT_LAM_HALF) ? 2.0 : 4.0) * c->nu * (F * r2) /
+                         ((rhoi + rhoj) * (r2 + eh2));
             fx += lam * vx;
             fy += lam * vy;
             ax += fx;
@@ -654,8 +660,8 @@ static void interaction_operator(orc_case *c)
             avx += -mj * Pij * F * rx;
             avy += -mj * Pij * F * ry;
             if (!ghost) {
-                double wij = kernel_W(c, r);
-                double rhobar = 0.5 * (rhoi + rhoj);
+                double wij = (c->P.mutation & MUT_XSPH_GRADW) ? -F * r : kernel_W(c, r);
+                double rhobar = (c->P.mutation & MUT_XSPH_RHOJ) ? rhoj : 0.5 * (rhoi + rhoj);
                 Xx += (mj / rhobar) * (vxj - c->vhx[i]) * wij;
                 Xy += (mj / rhobar) * (vyj - c->vhy[i]) * wij;
             } else if (c->gkind[g] == KIND_DISK) {

@@ -4,6 +4,7 @@ Run as ``python -m paper_2609_05494_b300.build`` or call :func:`build`.
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -11,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hram_capi.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "hram_device.cuh"), os.path.join(ROOT, "include", "hram.h")]
+DEPS = SRC + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [os.path.join(ROOT, "include", "hram.h")]
 LIB = os.path.join(HERE, "libhram.so")
 
 NVCC_FLAGS = [

@@ -15,6 +15,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -275,21 +277,29 @@ __global__ void k_neighbor_counts_static(Consts K, Bufs B, int *counts)
 }
 
 constexpr int kMaxDevices = 64;
-int *g_static_counts_ptr[kMaxDevices] = {};
+std::atomic<int *> g_static_counts_ptr[kMaxDevices] = {};
+std::mutex g_static_counts_mutex;
 
-// Device address of g_static_neighbor_counts on the current device, looked up
-// once per device.
-int static_counts_address(int **out)
+// Device address of g_static_neighbor_counts on device dev (which must be
+// the current device), looked up once per device.  Two host threads making
+// their first call at the same time serialise on the mutex; later calls read
+// the published address without locking.
+int static_counts_address(int dev, int **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HR_ECUDA;
-    if (!g_static_counts_ptr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_neighbor_counts) != cudaSuccess || !ptr)
-            return HR_ECUDA;
-        g_static_counts_ptr[dev] = static_cast<int *>(ptr);
+    if (dev < 0 || dev >= kMaxDevices) return HR_ECUDA;
+    int *p = g_static_counts_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_static_counts_mutex);
+        p = g_static_counts_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_static_neighbor_counts) != cudaSuccess || !ptr)
+                return HR_ECUDA;
+            p = static_cast<int *>(ptr);
+            g_static_counts_ptr[dev].store(p, std::memory_order_release);
+        }
     }
-    *out = g_static_counts_ptr[dev];
+    *out = p;
     return HR_OK;
 }
 
@@ -379,6 +389,7 @@ struct hr_case {
     Consts K;
     Bufs B;
     long long nf = 0, nw = 0, ng = 0;
+    int device = -1;  // the CUDA device current at hr_init_case
     int n_tiles = 0, pass_blocks = 0, ghost_blocks = 0, drift_blocks = 0, diag_blocks = 0;
     cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -950,6 +961,10 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
     hr_case *c = new hr_case();
     c->P = *p;
     c->nf = n_fluid;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return HR_ECUDA;
+    }
     const Geometry G = make_walls(*p);
     c->nw = (long long)G.wx.size();
     c->ng = p->Ng;
@@ -1440,8 +1455,12 @@ int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
     const long long npts = c->nf + c->nw + c->ng;
     if (npts > HR_STATIC_NEIGHBOR_MAX) return HR_ERANGE;
     if (cap < npts) return HR_ERANGE;
+    // the array's address is per device: the case's device must be current
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HR_ECUDA;
+    if (dev != c->device) return HR_EINVAL;
     int *counts = nullptr;
-    const int rc = static_counts_address(&counts);
+    const int rc = static_counts_address(dev, &counts);
     if (rc != HR_OK) return rc;
     const int blocks = (int)((npts + 255) / 256);
     k_neighbor_counts_static<<<blocks, 256, 0, c->stream>>>(c->K, c->B, counts);

@@ -31,12 +31,15 @@ def _run(theta: np.ndarray, params: dict, xy, n_steps: int, vel=None, rho=None, 
 def jacobian(theta, params: dict, xy, n_steps: int, vel=None, rho=None, stream=None):
     """(outputs [peak, impulse], J) with J[i, k] = d output_i / d theta_k."""
     th = np.asarray(theta, dtype=np.float64)
+    if np.any(th == 0.0):
+        # the library differentiates along theta_k d/dtheta_k; at theta_k = 0
+        # that direction is zero and the absolute derivative is not recoverable
+        raise ValueError("jacobian: every parameter (alpha, c0, tau) must be nonzero, got %s"
+                         % (th.tolist(),))
     o = _run(th, params, xy, n_steps, vel, rho, stream)
     rel = np.stack([o["dpeak"], o["dimpulse"]])
-    # relative derivatives theta_k d/dtheta_k -> absolute; a zero parameter
-    # (tau = 0: no decay) has no relative direction and keeps derivative 0
-    J = np.divide(rel, th, out=np.zeros_like(rel), where=th != 0.0)
-    return np.array([o["peak"], o["impulse"]]), J
+    # relative derivatives theta_k d/dtheta_k -> absolute
+    return np.array([o["peak"], o["impulse"]]), rel / th
 
 
 def _function():

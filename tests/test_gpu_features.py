@@ -10,7 +10,7 @@ import pytest
 
 import casegen
 import oracle
-from helpers import as64, csr_equal, impact_case, p_scale, perturbed, rel_l2
+from helpers import as64, assert_p_close, csr_equal, impact_case, perturbed, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def test_diagnostics_match_oracle():
         assert dg[k] == pytest.approx(do[k], rel=1e-3), k
     scale = math.hypot(do["px"], do["py"])
     assert abs(dg["px"] - do["px"]) <= 1e-3 * scale and abs(dg["py"] - do["py"]) <= 1e-3 * scale
-    assert dg["wall_impulse"] == pytest.approx(do["wall_impulse"], rel=1e-2, abs=1e-9)
+    assert dg["wall_impulse"] == pytest.approx(do["wall_impulse"], rel=1e-3, abs=1e-9)
     assert dg["p_max"] == pytest.approx(do["p_max"], rel=1e-4)
     assert dg["rho_max"] == pytest.approx(do["rho_max"], rel=1e-5)
     sg, so = g.scalars(), o.scalars()
@@ -211,13 +211,14 @@ def test_full_size_one_step_against_oracle():
     p, xy = impact_case(p)
     vel, rho = perturbed(p, xy, seed=3, v_amp=10.0, rho_rel=0.005)
     g, o = both(p, xy, vel, rho)
+    dt = o.scalars()["dt"]
     g.step()
     o.step()
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["rho"] / fo["rho"] - 1).max() <= 1e-5
-    # float32 positions at |x| ~ 0.3 m carry 3e-8 m rounding (6e-5 of 2h), which
-    # bounds the pressure agreement by the EOS-stiffness scale, not max |p|
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    # float32 positions at |x| ~ 0.3 m carry 3e-8 m rounding (6e-5 of 2h): the
+    # per-particle rounding floor of the gate grows with |x| / h
+    assert_p_close("full_size_1.125M", p, sg["p"], fo, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     assert g.scalars()["dt"] == pytest.approx(o.scalars()["dt"], rel=1e-6)
 

@@ -10,7 +10,7 @@ import pytest
 
 import casegen
 import oracle
-from helpers import as64, impact_case, p_scale, perturbed, rel_l2
+from helpers import as64, assert_p_close, impact_case, perturbed, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -31,10 +31,10 @@ def both(p, xy32, vel=None, rho=None, **kw):
     return Case(p, xy32, vel, rho, **kw), oracle.OracleCase(p, as64(xy32), as64(vel), as64(rho))
 
 
-def compare_state(p, g, o, dens_rel=1e-5, e_rel=1e-4):
+def compare_state(p, g, o, dt, name, dens_rel=1e-5, e_rel=1e-4):
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= dens_rel
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert_p_close(name, p, sg["p"], fo, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     vscale = max(np.abs(fo["vel"]).max(), 1.0)
     assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
@@ -51,7 +51,7 @@ def test_prime_summation_density_and_pressure():
     sg, fo = g.get_state(), o.fluid()
     # the summed density replaces the given one, on both sides
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-6
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert_p_close("paper_prime", p, sg["p"], fo, o.scalars()["dt"])
     assert np.all(g.energy()["e"] == 0.0)
 
 
@@ -62,9 +62,10 @@ def test_one_step(state):
     if state == "perturbed":
         vel, _ = perturbed(p, xy)
     g, o = both(p, xy, vel)
+    dt = o.scalars()["dt"]
     g.step()
     o.step()
-    compare_state(p, g, o)
+    compare_state(p, g, o, dt, "paper_one_step " + state)
     assert abs(g.scalars()["dt"] / o.scalars()["dt"] - 1.0) <= 1e-6
 
 
@@ -167,14 +168,14 @@ def test_hard_reflection_wall_matches_oracle():
     # the paper's baseline wall: no ghost layers, reflection at |y| = W/2
     p, xy = paper_case(wall_layers=0, wall_reflect=1)
     g, o = both(p, xy)
+    dt = o.scalars()["dt"]
     g.run(3)
     o.run(3)
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
-    # a summed density turns float32 position rounding into pressure (about
-    # 1e-4 in d per micrometre at this spacing), so a few steps in the gate
-    # is 1e-4 of the pressure scale
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-4 * p_scale(p, fo["p"])
+    # a summed density turns float32 position rounding into pressure: the
+    # floor of three steps
+    assert_p_close("paper_hard_wall 3 steps", p, sg["p"], fo, dt, steps=3)
     g.run(40)
     assert np.all(np.abs(g.get_state()["xy"][:, 1]) <= 0.5 * p["W"])
     assert g.scalars()["wall_impulse"] == 0.0

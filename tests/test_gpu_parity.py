@@ -9,7 +9,7 @@ import pytest
 
 import casegen
 import oracle
-from helpers import as64, csr_equal, impact_case, p_scale, perturbed, rel_l2
+from helpers import as64, assert_p_close, csr_equal, impact_case, perturbed, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -95,11 +95,12 @@ def test_one_step_around_the_disk_ring(ng, R, closure):
     inside = centre + np.array([[0.0, 0.0], [0.3, 0.1], [-0.5, 0.4], [0.2, -0.7], [0.8, 0.0]]) * R
     xy = np.vstack([xy, inside.astype(np.float32)])
     g, o = both(p, xy)
+    dt = o.scalars()["dt"]
     g.step()
     o.step()
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert_p_close("disk_ring ng=%d closure=%d" % (ng, closure), p, sg["p"], fo, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     vscale = max(np.abs(fo["vel"]).max(), 1.0)
     assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
@@ -158,14 +159,38 @@ def test_probe_history_parity_window():
     tg, to = g.probe_times(), o.probes()[1]
     assert pg.shape == po.shape == (n, len(p["probes"]))
     assert np.abs(tg / to - 1.0).max() <= 1e-5
+    gated = 0
     for k in range(po.shape[1]):
         peak = np.abs(po[:, k]).max()
+        print("PROBE250 %d peak %.3g Pa rel-L2 %.3g" % (k, peak, rel_l2(pg[:, k], po[:, k])))
+        # within 250 steps (41 us) the front reaches only the first wall probe
+        # (x = 30 mm); the others hold a gravity-settling signal of a few kPa
+        # and are gated over the longer window of the next test, which they
+        # see the front in
         if peak > 1e6:
             assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
-        else:
-            # below 1 MPa the wall probes hold only the gravity settling
-            # signal; the float32 state resolves it to a few hundred Pa
-            assert np.abs(pg[:, k] - po[:, k]).max() <= 2e3, k
+            gated += 1
+    assert gated >= 4
+
+
+def test_probe_history_parity_window_all_wall_probes():
+    # 500 steps (88 us): the impact front has passed all four wall probes
+    # (x = 30, 60, 90, 120 mm on the upper wall; peaks 0.43-0.62 GPa), so
+    # every one of them is held to 1e-3 relative L2 over the window
+    p, xy = impact_case()
+    n = 500
+    g, o = both(p, xy)
+    g.run(n)
+    o.run(n)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    assert pg.shape == po.shape == (n, 4)
+    assert np.abs(g.probe_times() / o.probes()[1] - 1.0).max() <= 1e-5
+    for k in range(4):
+        peak = np.abs(po[:, k]).max()
+        err = rel_l2(pg[:, k], po[:, k])
+        print("PROBE500 %d peak %.3g Pa rel-L2 %.3g" % (k, peak, err))
+        assert peak > 1e8, k
+        assert err <= 1e-3, k
 
 
 def test_run_is_deterministic():
@@ -198,11 +223,12 @@ def test_dense_rows_over_32_candidates(closure):
     assert csr_equal(off_g, ids_g, off_o, ids_o)
     counts = np.diff(off_o)[:xy.shape[0]]
     assert counts.max() > 60
+    dt = o.scalars()["dt"]
     g.step()
     o.step()
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
-    assert np.abs(sg["p"] - fo["p"]).max() <= 1e-5 * p_scale(p, fo["p"])
+    assert_p_close("dense_rows closure=%d" % closure, p, sg["p"], fo, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     vscale = max(np.abs(fo["vel"]).max(), 1.0)
     assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale

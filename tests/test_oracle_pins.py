@@ -370,3 +370,139 @@ def test_hydrostatic_ratio_and_suction_values():
     assert abs(h["rho0"] * h["C"] ** 2 / (h["rho0"] * 9.81 * h["H"]) - h["ratio"]) < 0.05e6
     s = g["suction_peak"]
     assert abs(s["rho0"] * s["U"] ** 2 * (0.5 - 2.0) - s["p"]) < 1e-6 * abs(s["p"])
+
+
+# ------------------------------------------- XSPH, laminar and AV moments
+#
+# Each pair sum is evaluated on an unjittered lattice with a velocity (and
+# density) field whose Taylor series stops at second order, so the lattice
+# sum reduces to a few even kernel moments that a continuum integral
+# computes independently of the oracle's pair loop.  h = 4 dx keeps the
+# lattice error of those moments at 1e-5 (XSPH) to 1e-3 (the eta^2 h^2
+# terms), which sets each tolerance.
+
+H_OVER_DX = 4.0
+DX_M = 1e-3
+N_SIDE = 40
+
+
+def _moment_patch(**kw):
+    p = fluid_only(Lx=N_SIDE * DX_M, W=N_SIDE * DX_M, dx=DX_M, h_over_dx=H_OVER_DX,
+                   eps_xsph=0.0, mu_lam=0.0)
+    p.update(kw)
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], 0.0, 1)
+    h = H_OVER_DX * DX_M
+    inner = ((xy[:, 0] > 2 * h + DX_M) & (xy[:, 0] < p["Lx"] - 2 * h - DX_M) &
+             (np.abs(xy[:, 1]) < 0.5 * p["W"] - 2 * h - DX_M))
+    return p, xy, inner, h
+
+
+def _polar_quad(f, h, n_r=48, n_t=96):
+    """Integral of f(r, theta) r dr dtheta over the disk r < 2h: Gauss-Legendre
+    in r (the Wendland kernel is a polynomial in r there), trapezoid in theta
+    (periodic, so spectrally accurate)."""
+    xg, wg = np.polynomial.legendre.leggauss(n_r)
+    r = h * (xg + 1.0)            # [0, 2h]
+    wr = h * wg
+    th = 2.0 * math.pi * np.arange(n_t) / n_t
+    R, T = np.meshgrid(r, th, indexing="ij")
+    return float((f(R, T) * R * wr[:, None]).sum() * (2.0 * math.pi / n_t))
+
+
+def _W(r, h):
+    return np.vectorize(lambda x: oracle.kernel_W(float(x), h))(r)
+
+
+def _F(r, h):
+    return np.vectorize(lambda x: oracle.kernel_F(float(x), h))(r)
+
+
+def _xsph_error(mutation=0, kappa=2.0, A=1e3):
+    # v = (A y^2, 0), rho = rho0 (1 + kappa y): X_x(y_i) = A int (2 y_i eta +
+    # eta^2) W / (1 + kappa (y_i + eta / 2)) dA  (m_j / rhobar_ij with m = rho0 dx^2,
+    # eta = y_j - y_i), X_y = 0
+    p, xy, inner, h = _moment_patch()
+    vel = np.zeros_like(xy)
+    vel[:, 0] = A * xy[:, 1] ** 2
+    rho = p["rho0"] * (1.0 + kappa * xy[:, 1])
+    X = oracle.OracleCase(p, xy, vel, rho, mutation=mutation).fluid()["X"]
+    scale = A * _polar_quad(lambda r, t: (r * np.sin(t)) ** 2 * _W(r, h), h)
+    err = 0.0
+    for yi in np.unique(np.round(xy[inner, 1], 12)):
+        sel = inner & (np.abs(xy[:, 1] - yi) < 1e-9)
+        want = A * _polar_quad(
+            lambda r, t: (2 * yi * r * np.sin(t) + (r * np.sin(t)) ** 2) * _W(r, h)
+            / (1.0 + kappa * (yi + 0.5 * r * np.sin(t))), h)
+        err = max(err, np.abs(X[sel, 0] - want).max() / scale, np.abs(X[sel, 1]).max() / scale)
+    return err
+
+
+def test_xsph_sum_matches_its_continuum_moment():
+    # eq. xsph with rhobar_ij = (rho_i + rho_j) / 2 (reading R9)
+    assert _xsph_error() < 2e-4
+
+
+@pytest.mark.parametrize("mutation", ["xsph_gradw", "xsph_rhoj"])
+def test_planted_xsph_mistakes_fail(mutation):
+    assert _xsph_error(oracle.MUT[mutation]) > 5e-3
+
+
+def _laminar_error(mutation=0, A=1e3, mu=1.0):
+    # v = (A y^2, 0) at rho0 (p = 0), no artificial viscosity or gravity: the
+    # laminar term (reading R7) is the Morris / Lo & Shao estimate of
+    # nu laplacian(v), here a_x = -2 nu A int F r^2 / (r^2 + eta^2 h^2) eta^2 dA
+    # (= 2 nu A = nu d2v/dy2 when eta -> 0), a_y = 0
+    p, xy, inner, h = _moment_patch(alpha=0.0, mu_lam=mu)
+    vel = np.zeros_like(xy)
+    vel[:, 0] = A * xy[:, 1] ** 2
+    a = oracle.OracleCase(p, xy, vel, None, mutation=mutation).fluid()["acc"]
+    nu = mu / p["rho0"]
+    eh2 = p["eta2"] * h * h
+    mom = _polar_quad(lambda r, t: _F(r, h) * r * r / (r * r + eh2) * (r * np.sin(t)) ** 2, h)
+    want = -2.0 * nu * A * mom
+    assert 0.97 < want / (2.0 * nu * A) < 1.0   # the eta^2 h^2 regulariser costs ~2 %
+    return max(np.abs(a[inner, 0] - want).max(), np.abs(a[inner, 1]).max()) / abs(want)
+
+
+def test_laminar_term_is_nu_laplacian():
+    assert _laminar_error() < 2e-3
+
+
+def test_planted_laminar_factor_fails():
+    assert _laminar_error(oracle.MUT["lam_half"]) > 0.4
+
+
+def _av_accel(rho_rel, alpha, mutation=0, beta=100.0, gam=1e3):
+    p, xy, inner, h = _moment_patch(alpha=alpha)
+    xt = xy[:, 0] - 0.5 * p["Lx"]
+    vel = np.stack([-beta * xt + gam * xt ** 2, -beta * xy[:, 1]], axis=1)
+    rho = np.full(xy.shape[0], rho_rel * p["rho0"])
+    return oracle.OracleCase(p, xy, vel, rho, mutation=mutation).fluid()["acc"], inner, p, h
+
+
+def _av_error(rho_rel, mutation=0, alpha=0.1, gam=1e3):
+    # v = (-beta x + gam x^2, -beta y) about the patch centre: every pair
+    # approaches (v_ij . r_ij < 0 for beta > gam (2 |x_i| + 2h)), so the
+    # switched Pi_ij of eq. artificial-viscosity is on everywhere and linear.
+    # At uniform rho the lattice sum leaves a_x = -alpha cbar h gam (rho0 / rho)
+    # int F x^4 / (r^2 + eta^2 h^2) dA, a_y = 0, with cbar = c0 (rho/rho0)^3
+    # (reading R5).  a(alpha) - a(0) removes the pressure terms.
+    a1, inner, p, h = _av_accel(rho_rel, alpha, mutation)
+    a0, _, _, _ = _av_accel(rho_rel, 0.0, mutation)
+    av = a1 - a0
+    eh2 = p["eta2"] * h * h
+    mom = _polar_quad(lambda r, t: _F(r, h) * (r * np.cos(t)) ** 4 / (r * r + eh2), h)
+    cbar = p["c0"] * rho_rel ** (0.5 * (p["gamma"] - 1.0))
+    want = -alpha * cbar * h * gam * mom / rho_rel
+    return max(np.abs(av[inner, 0] - want).max(), np.abs(av[inner, 1]).max()) / abs(want)
+
+
+@pytest.mark.parametrize("rho_rel", [1.0, 1.1])
+def test_artificial_viscosity_moment_and_sound_speed(rho_rel):
+    assert _av_error(rho_rel) < 5e-3
+
+
+def test_planted_constant_sound_speed_fails():
+    # at rho0 the two readings coincide; at 1.1 rho0 cbar differs by 1.1^3
+    assert _av_error(1.0, oracle.MUT["av_const_c"]) < 5e-3
+    assert _av_error(1.1, oracle.MUT["av_const_c"]) > 0.1
