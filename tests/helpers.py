@@ -39,17 +39,38 @@ FP32_EPS = 2.0 ** -24
 K_P = 8.0
 
 
-def p_floor(p, fo, dt, steps=1):
+def local_speed(o, fo):
+    """V_i: the largest speed over particle i and its neighbours (fluid and
+    ghosts) in the FP64 reference case o, whose fluid arrays are fo."""
+    off, ids = o.neighbours()
+    nf = fo["vel"].shape[0]
+    speed = np.concatenate([np.hypot(fo["vel"][:, 0], fo["vel"][:, 1]),
+                            np.hypot(*o.ghosts()["vel"].T)])
+    V = speed[:nf].copy()
+    rows = np.diff(off[:nf + 1])
+    nz = rows > 0
+    if ids.size:
+        m = np.maximum.reduceat(speed[ids], off[:nf][nz])
+        V[nz] = np.maximum(V[nz], m)
+    return V
+
+
+def p_floor(p, fo, dt, steps=1, V=None):
     """Per-particle pressure resolution of a float32 state after `steps`
     steps, against an FP64 reference state fo (oracle fluid arrays).
 
     A position r carries a rounding of 2^-24 |r| (|r| up to the particle's
     own coordinate plus the support 2h), which moves kernel values and
     gradients by 2^-24 |r| / h relative.  With the continuity equation
-    (closure 0) the density deviation then moves by dt |D rho| / rho0 times
-    that in a step; with the summed density (closure 1) by that relative
-    amount itself.  The pressure moves by dp/drho = c^2 times the density:
-    c0^2 (rho / rho0)^(gamma - 1) for Tait, C^2 for Mie-Grueneisen near rho0."""
+    (closure 0) each term m_j v_ij . grad W_ij of the density rate moves by
+    that relative amount; the terms add up to at most (7/3) (2 V_i) / h in
+    units of the density deviation per second (sum_j (m_j / rho0) |grad W_ij|
+    is the kernel's integral of |dW/dr|, 7 / (3 h) for Wendland C2, and
+    |v_ij| <= 2 V_i with V_i the largest speed in the support), so the
+    density deviation moves by dt times that in a step.  With the summed
+    density (closure 1) the density moves by the relative amount itself.
+    The pressure moves by dp/drho = c^2 times the density: c0^2 (rho /
+    rho0)^(gamma - 1) for Tait, C^2 for Mie-Grueneisen near rho0."""
     h = p["h_over_dx"] * p["dx"]
     reach = (np.abs(fo["xy"]).max(axis=1) + 2.0 * h) / h
     dens = np.maximum(fo["rho"] / p["rho0"], 1.0)
@@ -58,16 +79,19 @@ def p_floor(p, fo, dt, steps=1):
         moved = 1.0
     else:
         stiff = p["rho0"] * p["c0"] ** 2 * dens ** (p["gamma"] - 1.0)
-        moved = dt * np.abs(fo["drho"]) / p["rho0"]
+        moved = dt * (7.0 / 3.0) * 2.0 * V / h
     return steps * stiff * FP32_EPS * reach * moved
 
 
-def assert_p_close(name, p, p_gpu, fo, dt, steps=1, rel=1e-5):
-    """The one-step pressure gate: |p_gpu - p_ref| <= rel max|p_ref| plus
-    K_P times the per-particle rounding floor of p_floor (reading R26)."""
+def assert_p_close(name, p, p_gpu, o, dt, steps=1, rel=1e-5):
+    """The one-step pressure gate against the FP64 reference case o:
+    |p_gpu - p_ref| <= rel max|p_ref| plus K_P times the per-particle
+    rounding floor of p_floor (reading R26)."""
+    fo = o.fluid()
     err = np.abs(np.asarray(p_gpu, float) - fo["p"])
     base = rel * np.abs(fo["p"]).max()
-    floor = p_floor(p, fo, dt, steps)
+    V = None if p.get("closure", 0) == 1 else local_speed(o, fo)
+    floor = p_floor(p, fo, dt, steps, V)
     ratio = float((err / (base + floor)).max())
     print("GATE %s: max|dp| %.3g Pa, rel part %.3g Pa, max floor %.3g Pa, err/(rel+floor) %.3g"
           % (name, err.max(), base, floor.max(), ratio))

