@@ -284,6 +284,38 @@ void hr_batch_destroy(hr_batch *b);
  * and hr_load_state refuses them (a loaded state has no derivatives). */
 int hr_tangent_outputs(hr_case *c, double *out, int n);
 
+/* Reverse-mode (adjoint) derivatives of the same two outputs as
+ * hr_tangent_outputs (the peak probe-0 pressure P and the wall impulse J)
+ * with respect to theta = (alpha, c0, tau), for a case with closure 0,
+ * dt_mode 1 and motion 0-2 (not created with HR_FLAG_TANGENT).  This is the
+ * sensitivity study of Section 4.5 (the alpha sweep and Table
+ * tab:alpha-sweep) as a gradient: the adjoint of the interaction pass
+ * (Section 2.2), the ghost operator (eqs. adami-p / adami-v), the equation of
+ * state and the time integrator (Section 2.5), swept backwards through the
+ * run with the step's own neighbour sets, cell order and clamp / cutoff /
+ * switch / reflection decisions, as the forward run took them.
+ *
+ * hr_adjoint_forward runs n_steps steps from the case's uploaded state (the
+ * case must be at step 0: fresh from hr_init_case or hr_set_state), keeping a
+ * checkpoint of the state every checkpoint_every steps.  out (n >= 3
+ * doubles): [P, J, row of the peak in the probe history].  n_steps must not
+ * exceed probe_capacity, and the case needs at least one probe.  The
+ * library allocates the checkpoints, the records of one segment of
+ * checkpoint_every steps and the adjoint buffers (about
+ * (48 n_steps / checkpoint_every + 84 checkpoint_every + 300) bytes per fluid
+ * particle) and keeps them until the next hr_adjoint_forward or
+ * hr_destroy.  Afterwards the case stands at step n_steps as after hr_run.
+ *
+ * hr_adjoint_backward sweeps the run backwards: for each segment, last
+ * first, it recomputes the segment's steps from its checkpoint and carries
+ * the adjoints of the state from the end of each step to its start.  out (n
+ * >= 6 doubles): [dP/d ln alpha, dP/d ln c0, dP/d ln tau, dJ/d ln alpha,
+ * dJ/d ln c0, dJ/d ln tau] (theta_k d/d theta_k, as hr_tangent_outputs).  It
+ * leaves the case's state as hr_adjoint_forward left it, and may be called
+ * again.  HR_EINVAL without a preceding hr_adjoint_forward. */
+int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, double *out, int n);
+int hr_adjoint_backward(hr_case *c, double *out, int n);
+
 /* Neighbour counts of the current state without any device allocation.
  *
  * The paper has no counterpart; this is a library service.  hr_debug_neighbors

@@ -34,6 +34,7 @@ EXPORTS = (
     "hr_probe_times", "hr_diagnostics", "hr_diag_history", "hr_get_state", "hr_set_state",
     "hr_get_energy", "hr_get_ghosts", "hr_get_scalars", "hr_case_info", "hr_debug_neighbors",
     "hr_kernel_times", "hr_save_state", "hr_load_state", "hr_tangent_outputs",
+    "hr_adjoint_forward", "hr_adjoint_backward",
     "hr_neighbor_counts_static", "hr_batch_create", "hr_batch_step", "hr_batch_run",
     "hr_batch_done", "hr_batch_destroy", "hr_destroy", "hr_status_str",
 )
@@ -106,6 +107,8 @@ def lib() -> C.CDLL:
     L.hr_save_state.argtypes = [vp, C.c_char_p]
     L.hr_load_state.argtypes = [vp, C.c_char_p]
     L.hr_tangent_outputs.argtypes = [vp, vp, C.c_int]
+    L.hr_adjoint_forward.argtypes = [vp, i64, C.c_int32, vp, C.c_int]
+    L.hr_adjoint_backward.argtypes = [vp, vp, C.c_int]
     L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
     L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, C.c_int, vp, P(vp)]
     L.hr_batch_step.argtypes = [vp]

@@ -255,6 +255,25 @@ class Case:
         return dict(peak=float(v[0]), dpeak=v[1:4].copy(), impulse=float(v[4]),
                     dimpulse=v[5:8].copy(), peak_row=int(v[8]))
 
+    def adjoint_forward(self, n_steps: int, checkpoint_every: int = 20) -> dict:
+        """Reverse mode, forward half: n_steps steps from the uploaded state
+        with a checkpoint every checkpoint_every steps; the peak probe-0
+        pressure, the wall impulse and the peak's history row."""
+        v = np.empty(3)
+        self.last_status = check(lib().hr_adjoint_forward(self._h, int(n_steps),
+                                                          int(checkpoint_every), _ptr(v), 3),
+                                 "hr_adjoint_forward")
+        return dict(peak=float(v[0]), impulse=float(v[1]), peak_row=int(v[2]))
+
+    def adjoint_backward(self) -> dict:
+        """Reverse mode, backward half: the derivatives of the peak and the
+        impulse along ln alpha, ln c0, ln tau by the reverse sweep with
+        recomputation from the checkpoints."""
+        v = np.empty(6)
+        self.last_status = check(lib().hr_adjoint_backward(self._h, _ptr(v), 6),
+                                 "hr_adjoint_backward")
+        return dict(dpeak=v[0:3].copy(), dimpulse=v[3:6].copy())
+
     def save(self, path: str) -> None:
         check(lib().hr_save_state(self._h, str(path).encode()), "hr_save_state")
 

@@ -8,6 +8,7 @@
 // stream; hr_step replays that graph on the caller's stream.
 #include "hram_device.cuh"
 #include "hram_tangent.cuh"
+#include "hram_adjoint.cuh"
 #include "hram.h"
 
 #include <cmath>
@@ -411,6 +412,8 @@ struct hr_case {
     float *io = nullptr;  // nf x 6 floats for state transfers
     long long host_step = 0;
     int sticky = 0;
+    // reverse mode (hr_adjoint_forward / hr_adjoint_backward)
+    struct AdjCtx *adj = nullptr;
     // tangent mode (HR_FLAG_TANGENT)
     bool tangent = false;
     TBufs T{};
@@ -925,6 +928,276 @@ int build_walls(hr_case *c, const Geometry &G)
     CK(cudaMemcpy(c->B.gw_kind, skind.data(), nw * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.gw_id, sid.data(), nw * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.wall_start, start.data(), start.size() * 4, cudaMemcpyHostToDevice));
+    return HR_OK;
+}
+
+// ------------------------------------------------------ reverse mode
+
+}  // namespace
+
+// The checkpoint store, the tape of one segment of L steps and the adjoint
+// buffers of a case (one device block owned by the case).
+struct AdjCtx {
+    int L = 0;                    // steps between checkpoints
+    long long n_steps = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    std::vector<Slot> tape;       // L slots: the segment being swept
+    Slot prime_slot{}, upload{};  // the priming pass and its input (fluid-ID order)
+    std::vector<Slot> ckpt;       // ckpt[k]: the state after step k L (ckpt[0] = prime_slot)
+    Scalars *S_final = nullptr;   // the scalars after the forward run
+    ABufs A{};
+    LState ls[2]{};
+    int ep_blocks = 0, bk_blocks = 0, gh_blocks = 0;
+    bool forward_done = false;
+    double peak = 0.0, impulse = 0.0;
+    long long peak_row = -1;
+};
+
+namespace {
+
+void adj_free(hr_case *c)
+{
+    if (!c->adj) return;
+    if (c->adj->mem) cudaFree(c->adj->mem);
+    delete c->adj;
+    c->adj = nullptr;
+}
+
+// Carves the reverse-mode buffers of a run of n_steps steps with a
+// checkpoint every L steps.
+int adj_alloc(hr_case *c, long long n_steps, int L)
+{
+    adj_free(c);
+    AdjCtx *a = new AdjCtx();
+    c->adj = a;
+    a->L = L;
+    a->n_steps = n_steps;
+    const size_t n = (size_t)c->nf, ngh = (size_t)(c->nw + c->ng), nc = (size_t)c->K.ncell;
+    const size_t ng = (size_t)c->ng;
+    const long long n_ck = (n_steps + L - 1) / L;   // checkpoints 1 .. n_ck - 1 (0 is the prime)
+    Layout Lo;
+    struct SlotOff {
+        size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_a, st_D, st_X, perm, cs, gd, gv,
+            ga, S;
+    };
+    auto full = [&]() {
+        SlotOff o;
+        o.s_pos = Lo.add((n + kPosPad) * 8);
+        o.s_vel = Lo.add(n * 8);
+        o.s_aux = Lo.add(n * 16);
+        o.s_rd = Lo.add(n * 8);
+        o.s_id = Lo.add(n * 4);
+        o.st_vel = Lo.add(n * 8);
+        o.st_rho = Lo.add(n * 4);
+        o.st_a = Lo.add(n * 8);
+        o.st_D = Lo.add(n * 8);
+        o.st_X = Lo.add(n * 8);
+        o.perm = Lo.add(n * 4);
+        o.cs = Lo.add((nc + 2) * 4);
+        o.gd = Lo.add(std::max<size_t>(ng, 1) * 8);
+        o.gv = Lo.add(std::max<size_t>(ngh, 1) * 8);
+        o.ga = Lo.add(std::max<size_t>(ngh, 1) * 16);
+        o.S = Lo.add(sizeof(Scalars));
+        return o;
+    };
+    auto state = [&]() {   // a checkpoint: the state a step starts from
+        SlotOff o{};
+        o.s_pos = Lo.add((n + kPosPad) * 8);
+        o.s_id = Lo.add(n * 4);
+        o.st_vel = Lo.add(n * 8);
+        o.st_rho = Lo.add(n * 4);
+        o.st_a = Lo.add(n * 8);
+        o.st_D = Lo.add(n * 8);
+        o.st_X = Lo.add(n * 8);
+        o.S = Lo.add(sizeof(Scalars));
+        return o;
+    };
+    std::vector<SlotOff> tape_o;
+    for (long long k = 0; k < std::min<long long>(L, n_steps); ++k) tape_o.push_back(full());
+    const SlotOff prime_o = full();
+    const SlotOff up_o = state();
+    std::vector<SlotOff> ck_o;
+    for (long long k = 1; k < n_ck; ++k) ck_o.push_back(state());
+    const size_t sfin = Lo.add(sizeof(Scalars));
+    const size_t nq = n * kOut, gq = std::max<size_t>(ngh, 1) * kOut;
+    size_t ls_o[2][7];
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 4; ++k) ls_o[b][k] = Lo.add(nq * 8);
+        for (int k = 4; k < 7; ++k) ls_o[b][k] = Lo.add(nq * 4);
+    }
+    a->ep_blocks = (int)((n + kAThreads - 1) / kAThreads);
+    a->bk_blocks = a->ep_blocks;
+    a->gh_blocks = (int)std::max<size_t>(1, (ngh + kAGhostWarps - 1) / kAGhostWarps);
+    const size_t wA = Lo.add(nq * 8), wX = Lo.add(nq * 8), wDr = Lo.add(nq * 4);
+    const size_t lpos = Lo.add(nq * 8), lvh = Lo.add(nq * 8), lrec = Lo.add(nq * 16),
+                 lrd = Lo.add(nq * 8);
+    const size_t gS1 = Lo.add(gq * 16), gS2 = Lo.add(gq * 8), gpar = Lo.add(gq * 16),
+                 grg = Lo.add(gq * 8);
+    const size_t ep = Lo.add((size_t)a->ep_blocks * kOut * 4);
+    const size_t bk = Lo.add((size_t)a->bk_blocks * kOut * 16);
+    const size_t sc = Lo.add(ASC_N * 8);
+    a->bytes = Lo.total;
+    if (cudaMalloc(&a->mem, a->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        a->mem = nullptr;
+        adj_free(c);
+        return HR_ENOMEM;
+    }
+    void *w = a->mem;
+    auto mk = [&](const SlotOff &o, bool isfull) {
+        Slot sl{};
+        sl.s_pos = at<float2>(w, o.s_pos);
+        sl.s_id = at<int>(w, o.s_id);
+        sl.st_vel = at<float2>(w, o.st_vel);
+        sl.st_rho = at<float>(w, o.st_rho);
+        sl.st_a = at<float2>(w, o.st_a);
+        sl.st_D = at<float2>(w, o.st_D);
+        sl.st_X = at<float2>(w, o.st_X);
+        sl.S = at<Scalars>(w, o.S);
+        if (isfull) {
+            sl.s_vel = at<float2>(w, o.s_vel);
+            sl.s_aux = at<float4>(w, o.s_aux);
+            sl.s_rd = at<float2>(w, o.s_rd);
+            sl.perm_dst = at<int>(w, o.perm);
+            sl.cell_start = at<int>(w, o.cs);
+            sl.gd_pos = at<float2>(w, o.gd);
+            sl.g_vel = at<float2>(w, o.gv);
+            sl.g_aux = at<float4>(w, o.ga);
+        }
+        return sl;
+    };
+    for (auto &o : tape_o) a->tape.push_back(mk(o, true));
+    a->prime_slot = mk(prime_o, true);
+    a->upload = mk(up_o, false);
+    a->ckpt.push_back(a->prime_slot);
+    for (auto &o : ck_o) a->ckpt.push_back(mk(o, false));
+    a->S_final = at<Scalars>(w, sfin);
+    for (int b = 0; b < 2; ++b) {
+        LState &l = a->ls[b];
+        l.r = at<float2>(w, ls_o[b][0]);
+        l.v = at<float2>(w, ls_o[b][1]);
+        l.a = at<float2>(w, ls_o[b][2]);
+        l.X = at<float2>(w, ls_o[b][3]);
+        l.d = at<float>(w, ls_o[b][4]);
+        l.D = at<float>(w, ls_o[b][5]);
+        l.E = at<float>(w, ls_o[b][6]);
+    }
+    ABufs &A = a->A;
+    A.wA = at<float2>(w, wA);
+    A.wX = at<float2>(w, wX);
+    A.wDr = at<float>(w, wDr);
+    A.lpos = at<float2>(w, lpos);
+    A.lvh = at<float2>(w, lvh);
+    A.lrec = at<float4>(w, lrec);
+    A.lrd = at<float2>(w, lrd);
+    A.gS1 = at<float4>(w, gS1);
+    A.gS2 = at<float2>(w, gS2);
+    A.gpar = at<float4>(w, gpar);
+    A.grg = at<float2>(w, grg);
+    A.ep_part = at<float>(w, ep);
+    A.bk_part = at<float4>(w, bk);
+    A.sc = at<double>(w, sc);
+    return HR_OK;
+}
+
+// The case's buffers with the per-step arrays of slot sl (S: the slot's
+// scalars when with_S, else the live ones).
+Bufs slot_bufs(const hr_case *c, const Slot &sl, bool with_S)
+{
+    Bufs B = c->B;
+    B.s_pos = sl.s_pos;
+    B.s_vel = sl.s_vel;
+    B.s_aux = sl.s_aux;
+    B.s_rd = sl.s_rd;
+    B.s_id = sl.s_id;
+    B.st_vel = sl.st_vel;
+    B.st_rho = sl.st_rho;
+    B.st_a = sl.st_a;
+    B.st_D = sl.st_D;
+    B.st_X = sl.st_X;
+    B.perm_dst = sl.perm_dst;
+    B.cell_start = sl.cell_start;
+    B.gd_pos = sl.gd_pos;
+    B.g_vel = sl.g_vel;
+    B.g_aux = sl.g_aux;
+    if (with_S) B.S = sl.S;
+    return B;
+}
+
+// One forward step recorded into slot cur from the state in prev (the
+// step's kernels, closure 0, each given the arrays it reads and writes), then
+// the scalars snapshot.  The live scalars c->B.S advance as in a plain step.
+int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, int prime)
+{
+    const Consts &K = c->K;
+    Bufs Bk = c->B;
+    Bk.gd_pos = cur.gd_pos;
+    Bufs Bd = c->B;   // the drift reads the previous state
+    Bd.s_pos = prev.s_pos;
+    Bd.s_id = prev.s_id;
+    Bd.st_vel = prev.st_vel;
+    Bd.st_a = prev.st_a;
+    Bd.st_X = prev.st_X;
+    Bufs Bs = c->B;   // scan and provisional slots write this step's cell starts
+    Bs.cell_start = cur.cell_start;
+    Bufs Br = slot_bufs(c, cur, false);   // the reorder writes this step's arrays
+    Br.st_rho = prev.st_rho;             // ... from the previous density and rates
+    Br.st_D = prev.st_D;
+    const Bufs Bc = slot_bufs(c, cur, false);
+    k_kinematics<<<1, 128, 0, s>>>(K, Bk, prime);
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
+    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs);
+    k_slot<<<c->drift_blocks, 256, 0, s>>>(K, Bs);
+    k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
+    k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);
+    k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, Bc, prime);
+    k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(cur.S, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+    return HR_OK;
+}
+
+// Copies the case's current state (what the next step starts from) into a
+// checkpoint.
+int save_ckpt(hr_case *c, const Slot &k, cudaStream_t s)
+{
+    const size_t n = (size_t)c->nf;
+    CK(cudaMemcpyAsync(k.s_pos, c->B.s_pos, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.s_id, c->B.s_id, n * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.st_vel, c->B.st_vel, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.st_rho, c->B.st_rho, n * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.st_a, c->B.st_a, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.st_D, c->B.st_D, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.st_X, c->B.st_X, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(k.S, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+    return HR_OK;
+}
+
+// The reverse sweep of one step: slot cur holds the step's record, prev the
+// state it started from.  The end-of-step adjoints are in A.cur; the
+// adjoints of the start state land in A.prv.
+int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, int prime,
+                 bool seed_peak)
+{
+    AdjCtx *a = c->adj;
+    const Consts &K = c->K;
+    const Bufs Bc = slot_bufs(c, cur, true);
+    Bufs Bp = c->B;
+    Bp.s_pos = prev.s_pos;
+    Bp.st_vel = prev.st_vel;
+    Bp.st_rho = prev.st_rho;
+    Bp.st_a = prev.st_a;
+    Bp.st_D = prev.st_D;
+    Bp.st_X = prev.st_X;
+    if (seed_peak && K.n_probes > 0) ka_probe<<<1, 32, 0, s>>>(K, Bc, a->A);
+    ka_epilogue<<<a->ep_blocks, kAThreads, 0, s>>>(K, Bc, a->A, prime);
+    ka_ghost<<<a->gh_blocks, kAGhostWarps * 32, 0, s>>>(K, Bc, a->A, prime);
+    ka_pass<<<a->ep_blocks, kAThreads, 0, s>>>(K, Bc, a->A, prime);
+    ka_back<<<a->bk_blocks, kAThreads, 0, s>>>(K, Bc, Bp, a->A, prime);
+    ka_close<<<1, kACloseThreads, 0, s>>>(K, Bc, a->A, prime, a->ep_blocks, a->bk_blocks);
+    CK(cudaGetLastError());
+    std::swap(a->A.cur, a->A.prv);
     return HR_OK;
 }
 
@@ -1449,6 +1722,111 @@ int hr_tangent_outputs(hr_case *c, double *out, int n)
     return st;
 }
 
+int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, double *out, int n)
+{
+    if (!c || !out || n < 3 || n_steps < 1 || checkpoint_every < 1) return HR_EINVAL;
+    if (c->P.closure != 0 || c->P.dt_mode != 1 || c->P.motion < 0 || c->P.motion > 2 || c->tangent)
+        return HR_EINVAL;
+    if (c->K.n_probes < 1 || n_steps > c->K.probe_cap) return HR_EINVAL;
+    int st = device_status(c);
+    if (st < 0) return st;
+    Scalars S0;
+    CK(cudaMemcpy(&S0, c->B.S, sizeof S0, cudaMemcpyDeviceToHost));
+    if (S0.step != 0) return HR_EINVAL;   // from the uploaded state only
+    int rc = adj_alloc(c, n_steps, checkpoint_every);
+    if (rc != HR_OK) return rc;
+    AdjCtx *a = c->adj;
+    cudaStream_t s = c->stream;
+    // the uploaded state, and the priming pass recorded from it: checkpoint 0
+    ka_to_id_order<<<c->drift_blocks, 256, 0, s>>>(c->K, c->B, a->upload);
+    CK(cudaGetLastError());
+    if ((rc = launch_tape_step(c, s, a->prime_slot, a->upload, 1)) != HR_OK) return rc;
+    // the forward run on the case's own step graph, a checkpoint every L steps
+    long long done = 0;
+    while (done < n_steps) {
+        const long long k = std::min<long long>(a->L, n_steps - done);
+        if ((rc = run_steps(c, k)) != HR_OK) return rc;
+        done += k;
+        if (done < n_steps && (rc = save_ckpt(c, a->ckpt[done / a->L], s)) != HR_OK) return rc;
+    }
+    CK(cudaMemcpyAsync(a->S_final, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+    st = device_status(c);
+    if (st < 0) return st;
+    // the peak of probe 0 over the run and its row (the first of equal maxima)
+    const int np = c->K.n_probes;
+    std::vector<float> hist((size_t)n_steps * (size_t)np);
+    CK(cudaMemcpy(hist.data(), c->B.probe_hist, hist.size() * 4, cudaMemcpyDeviceToHost));
+    double peak = -HUGE_VAL;
+    long long row = -1;
+    for (long long k = 0; k < n_steps; ++k)
+        if ((double)hist[(size_t)k * np] > peak) {
+            peak = hist[(size_t)k * np];
+            row = k;
+        }
+    Scalars Sf;
+    CK(cudaMemcpy(&Sf, c->B.S, sizeof Sf, cudaMemcpyDeviceToHost));
+    a->peak = peak;
+    a->peak_row = row;
+    a->impulse = Sf.impulse;
+    a->forward_done = true;
+    out[0] = peak;
+    out[1] = Sf.impulse;
+    out[2] = (double)row;
+    return st;
+}
+
+int hr_adjoint_backward(hr_case *c, double *out, int n)
+{
+    if (!c || !out || n < 6 || !c->adj || !c->adj->forward_done) return HR_EINVAL;
+    if (c->sticky < 0) return c->sticky;
+    AdjCtx *a = c->adj;
+    cudaStream_t s = c->stream;
+    const size_t nq = (size_t)c->nf * kOut;
+    a->A.cur = a->ls[0];
+    a->A.prv = a->ls[1];
+    const LState &z = a->A.cur;
+    for (float2 *p : {z.r, z.v, z.a, z.X}) CK(cudaMemsetAsync(p, 0, nq * 8, s));
+    for (float *p : {z.d, z.D, z.E}) CK(cudaMemsetAsync(p, 0, nq * 4, s));
+    CK(cudaMemsetAsync(a->A.sc, 0, ASC_N * 8, s));
+    const long long N = a->n_steps;
+    const int L = a->L;
+    int rc;
+    for (long long seg = (N + L - 1) / L - 1; seg >= 0; --seg) {
+        const long long base = seg * L, end = std::min<long long>(N, base + L);
+        const Slot &start = a->ckpt[(size_t)seg];
+        // recompute the segment's records from its checkpoint
+        CK(cudaMemcpyAsync(c->B.S, start.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+        for (long long k = base; k < end; ++k) {
+            const Slot &prev = k == base ? start : a->tape[(size_t)(k - base - 1)];
+            if ((rc = launch_tape_step(c, s, a->tape[(size_t)(k - base)], prev, 0)) != HR_OK)
+                return rc;
+        }
+        // and sweep it backwards
+        for (long long k = end - 1; k >= base; --k) {
+            const Slot &prev = k == base ? start : a->tape[(size_t)(k - base - 1)];
+            if ((rc = adjoint_step(c, s, a->tape[(size_t)(k - base)], prev, 0, k == a->peak_row)) !=
+                HR_OK)
+                return rc;
+        }
+    }
+    // the priming pass (a0, D0, X0 of the uploaded state)
+    if ((rc = adjoint_step(c, s, a->prime_slot, a->upload, 1, false)) != HR_OK) return rc;
+    // the case goes on from the end of the forward run
+    CK(cudaMemcpyAsync(c->B.S, a->S_final, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+    const int st = device_status(c);
+    if (st < 0) return st;
+    double sc[ASC_N];
+    CK(cudaMemcpy(sc, a->A.sc, sizeof sc, cudaMemcpyDeviceToHost));
+    // every step's dt = C h / (c0 + v0): d dt / d ln c0 = -dt c0 / (c0 + v0)
+    const double dtdc = -c->K.dt_fixed * c->P.c0 / (c->P.c0 + c->P.v0);
+    for (int q = 0; q < kOut; ++q) {
+        out[3 * q + 0] = sc[ASC_ALPHA + q];
+        out[3 * q + 1] = sc[ASC_C0 + q] + sc[ASC_DT + q] * dtdc;
+        out[3 * q + 2] = sc[ASC_TAU + q];
+    }
+    return st;
+}
+
 int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
 {
     if (!c || !host_counts) return HR_EINVAL;
@@ -1709,6 +2087,7 @@ void hr_destroy(hr_case *c)
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
     if (c->own_ws && c->ws) cudaFree(c->ws);
+    adj_free(c);
     delete c;
 }
 

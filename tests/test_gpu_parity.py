@@ -183,14 +183,21 @@ def test_probe_history_parity_window_all_wall_probes():
     g.run(n)
     o.run(n)
     pg, po = g.probe_pressure(), o.probes()[0]
+    tg, to = g.probe_times(), o.probes()[1]
     assert pg.shape == po.shape == (n, 4)
-    dts = np.abs(g.probe_times() / o.probes()[1] - 1.0).max()
+    # the CFL gate's v_max comes from the splash, whose float32 trajectory
+    # drifts from the FP64 one: after 500 steps the times differ by up to
+    # 7.5e-5 relative (6 ns), so the histories are compared on the oracle's
+    # time axis (the float32 history interpolated linearly onto it)
+    dts = np.abs(tg / to - 1.0).max()
     print("PROBE500 time rel diff %.3g" % dts)
     errs = []
     for k in range(4):
         peak = np.abs(po[:, k]).max()
-        errs.append(rel_l2(pg[:, k], po[:, k]))
-        print("PROBE500 %d peak %.3g Pa rel-L2 %.3g" % (k, peak, errs[-1]))
+        on_t = np.interp(to, tg, pg[:, k])
+        errs.append(rel_l2(on_t, po[:, k]))
+        print("PROBE500 %d peak %.3g Pa rel-L2 %.3g (step-indexed %.3g)"
+              % (k, peak, errs[-1], rel_l2(pg[:, k], po[:, k])))
         assert peak > 1e8, k
     assert max(errs) <= 1e-3
     assert dts <= 1e-4
