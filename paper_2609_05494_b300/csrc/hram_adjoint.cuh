@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(kAThreads) ka_epilogue(Consts K, Bufs B, ABufs
             A.lrd[q] = make_float2(lrdx, lrdy);
         }
     }
+    // the priming pass runs with the constant dt = 0, not with the case's dt
+    if (prime) dtp[0] = dtp[1] = 0.0f;
 #pragma unroll
     for (int c = 0; c < kOut; ++c) {
         const float s = lane_sum(dtp[c]);
@@ -795,6 +797,7 @@ __global__ void __launch_bounds__(kAThreads) ka_back(Consts K, Bufs Bc, Bufs Bp,
             A.prv.E[o] = lE;
         }
     }
+    if (prime) part[0][2] = part[1][2] = 0.0f;   // dt = 0 is a constant there
 #pragma unroll
     for (int c = 0; c < kOut; ++c)
 #pragma unroll
