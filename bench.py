@@ -270,6 +270,58 @@ def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
     return res
 
 
+def adjoint_benchmark(stream, big_xy=None, big_p=None, big_steps=20, every=20):
+    """Cost of the reverse mode (hr_adjoint_forward + hr_adjoint_backward: the
+    run with a checkpoint every `every` steps, then the reverse sweep that
+    recomputes each segment) against the plain run of the same steps, on the
+    22,500-particle fixed-dt workload (400 steps) and on a few steps of the
+    1.125M-particle workload.  CUDA events on the case's stream."""
+    import torch
+    from paper_2609_05494_b300 import Case
+
+    def timed(p, xy, steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            plain = Case(p, xy, stream=stream, probe_capacity=steps + 8)
+            adj = Case(p, xy, stream=stream, probe_capacity=steps + 8)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        plain.run(steps)
+        ev[1].record(stream)
+        plain.sync()
+        ev[2].record(stream)
+        y = adj.adjoint_forward(steps, every)
+        g = adj.adjoint_backward()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        f_ms, a_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        plain.close()
+        adj.close()
+        return f_ms, a_ms, y, g
+
+    p = casegen.config_adjoint()
+    xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                               disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+    steps = int(p["n_steps"])
+    timed(p, xy, 40)   # warm-up of the code paths
+    f_ms, a_ms, y, g = timed(p, xy, steps)
+    res = {"workload": "150 x 150 mm, dx = 1 mm, %d particles, %d steps, fixed dt, a checkpoint "
+                       "every %d steps" % (xy.shape[0], steps, every),
+           "forward_ms_per_step": f_ms / steps, "adjoint_ms_per_step": a_ms / steps,
+           "adjoint_over_forward": a_ms / f_ms, "gradients_per_s": 1e3 / a_ms,
+           "peak_Pa": y["peak"], "dpeak_dln": g["dpeak"].tolist(),
+           "impulse": y["impulse"], "dimpulse_dln": g["dimpulse"].tolist()}
+    if big_xy is not None:
+        q = dict(big_p)
+        q["dt_mode"] = 1
+        f_ms, a_ms, _, _ = timed(q, big_xy, big_steps)
+        res["large"] = {"particles": int(big_xy.shape[0]), "steps": big_steps,
+                        "forward_ms_per_step": f_ms / big_steps,
+                        "adjoint_ms_per_step": a_ms / big_steps,
+                        "adjoint_over_forward": a_ms / f_ms}
+    return res
+
+
 def scaling_benchmark(stream, flush, dxs=(1e-3, 5e-4, 2.5e-4, 2e-4, 1e-4), steps=30, warmup=5):
     """The scaling sweep of the same channel at spacing dx (45,000 to 4.5M
     particles): ms per step (L2 flushed between steps, graph without timing
@@ -540,6 +592,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tangent", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-scaling", action="store_true")
     ap.add_argument("--no-production", action="store_true")
@@ -645,6 +698,7 @@ def main():
     clk.__exit__(None, None, None)
     sweep = None if args.no_sweep else sweep_benchmark(stream, rank, world, dist)
     tangent = None if args.no_tangent else tangent_benchmark(stream, xy, p)
+    adjoint = None if args.no_adjoint else adjoint_benchmark(stream, xy, p)
     paper = None if args.no_paper else paper_event_benchmark(stream)
     scaling = None if args.no_scaling else scaling_benchmark(stream, flush)
     production = None if args.no_production else production_benchmark(stream)
@@ -688,6 +742,7 @@ def main():
         "kernel_groups_ms": groups,
         "batched_sweep": sweep,
         "tangent": tangent,
+        "adjoint": adjoint,
         "paper_event": paper,
         "size_sweep": scaling,
         "production": production,

@@ -50,6 +50,10 @@ extern "C" {
 #define HR_EDT (-5)       /* time step underflow (dt < 1e-14 s) */
 #define HR_ERANGE (-7)    /* caller buffer too small */
 #define HR_EIO (-8)       /* file error in save / load */
+#define HR_ECHECK (-9)    /* an index check failed; only the bounds-checked build
+                            (libhram_checked.so, compiled with -DHRAM_CHECKED)
+                            checks every cell-list, sorted-array and ghost index
+                            before use, skips the access and reports it here */
 /* warning bits (positive) */
 #define HR_WPENETRATION 1 /* fluid particles inside the disk circle */
 #define HR_WOUTSIDE 2     /* particles left the computational box and were frozen */

@@ -11,7 +11,11 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhram.so")
+# HRAM_CHECKED=1 selects the bounds-checked build of the same library (every
+# cell-list, sorted-array and ghost index checked before use; HR_ECHECK on a
+# failure); it computes the same step
+CHECKED = os.environ.get("HRAM_CHECKED", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libhram_checked.so" if CHECKED else "libhram.so")
 MAX_PROBES = 16
 
 # status codes (hram.h)
@@ -23,6 +27,7 @@ HR_ENAN = -4
 HR_EDT = -5
 HR_ERANGE = -7
 HR_EIO = -8
+HR_ECHECK = -9
 HR_WPENETRATION = 1
 HR_WOUTSIDE = 2
 HR_WPROBEFULL = 4

@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hram_capi.cu")]
 DEPS = SRC + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [os.path.join(ROOT, "include", "hram.h")]
 LIB = os.path.join(HERE, "libhram.so")
+# the bounds-checked build of the same source (-DHRAM_CHECKED)
+LIB_CHECKED = os.path.join(HERE, "libhram_checked.so")
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -28,21 +30,29 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if it is missing or older than its sources."""
-    if force or stale():
-        cmd = [nvcc()] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp"] + SRC
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
-        os.replace(LIB + ".tmp", LIB)
+def _compile(lib: str, extra: list, verbose: bool) -> None:
+    tmp = "%s.%d.tmp" % (lib, os.getpid())
+    cmd = [nvcc()] + NVCC_FLAGS + extra + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + SRC
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.check_call(cmd)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = True) -> str:
+    """Compile the library (and its bounds-checked build) if missing or older
+    than the sources."""
+    if force or stale(LIB):
+        _compile(LIB, [], verbose)
+    if checked and (force or stale(LIB_CHECKED)):
+        _compile(LIB_CHECKED, ["-DHRAM_CHECKED"], verbose)
     return LIB
 
 

@@ -75,8 +75,9 @@ enum {
 
 struct ABufs {
     LState cur, prv;         // end-of-step adjoints: this step's order / the previous step's
-    float2 *wA, *wX;         // pair weights lambda_A, lambda_X of the pass sums
-    float *wDr;              // pair weight of the continuity sum
+    float4 *wA, *wX;         // pair weights lambda_A, lambda_X of the pass sums, both
+                             // components in one vector {x0, y0, x1, y1} per particle
+    float2 *wDr;             // pair weights of the continuity sum {c0, c1}
     float2 *lpos, *lvh;      // adjoints of the pass inputs r', vh
     float4 *lrec;            // adjoints of the EOS record {d~ (density), P~, C~, p~}
     float2 *lrd;             // adjoints of {d, D} carried through the sort
@@ -87,6 +88,7 @@ struct ABufs {
     float *ep_part;          // per epilogue block: dt partial [kOut]
     float4 *bk_part;         // per back block: {alpha, c0, dt, 0} [kOut]
     double *sc;              // ASC_* accumulators
+    int *status;             // the case's status word (bounds-checked build)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -117,10 +119,12 @@ __device__ __forceinline__ float tait_slope(const Consts &K, float d)
 }
 
 // Forward intermediates of one pair as pair_terms forms them, side I = the
-// particle whose sums receive the pair (fluid), side J = its neighbour.
+// particle whose sums receive the pair (fluid), side J = its neighbour, and
+// the local partial derivatives the reverse sweep needs (formed once, shared
+// by the adjoint components).
 struct PairFwd {
-    float dx, dy, vx, vy, r2, r, t, mjFc, F, vr, e, S, inv, Csum, mvr, Q, lam, wx;
-    bool tpos, comp;
+    float dx, dy, vx, vy, vr, F, Q, lam, wx;
+    float kFr2, kLamR2, kLamInv, kC, kVr, kInv, kWxT, kWxR, kWxS, kInvR2, kInvS, kFt, kTr, kRr2;
 };
 
 __device__ __forceinline__ void pair_fwd(const Consts &K, float2 ri, float2 vi, float rhoi, float Pi,
@@ -129,26 +133,46 @@ __device__ __forceinline__ void pair_fwd(const Consts &K, float2 ri, float2 vi, 
 {
     q.dx = ri.x - rj.x;
     q.dy = ri.y - rj.y;
-    q.r2 = fmaf(q.dx, q.dx, q.dy * q.dy);
-    q.r = sqrtf(q.r2);
-    const float t = fmaf(-q.r, K.half_inv_h, 1.0f);
-    q.tpos = t > 0.0f;
-    q.t = fmaxf(t, 0.0f);
-    const float t3 = q.t * q.t * q.t;
-    q.mjFc = mj * K.Fc;
-    q.F = q.mjFc * t3;
+    const float r2 = fmaf(q.dx, q.dx, q.dy * q.dy);
+    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+    const float r = r2 * rinv;
+    const float t0 = fmaf(-r, K.half_inv_h, 1.0f);
+    const float t = fmaxf(t0, 0.0f);
+    const float t2 = t * t, t3 = t2 * t;
+    const float mjFc = mj * K.Fc;
+    q.F = mjFc * t3;
     q.vx = vi.x - vj.x;
     q.vy = vi.y - vj.y;
     q.vr = fmaf(q.vx, q.dx, q.vy * q.dy);
-    q.e = q.r2 + K.eh2;
-    q.S = rhoi + rhoj;
-    q.inv = 1.0f / (q.e * q.S);
-    q.Csum = Ci + Cj;
-    q.comp = q.vr < 0.0f;
-    q.mvr = fminf(q.vr, 0.0f);
-    q.Q = Pi + Pj + q.Csum * q.mvr * q.inv;
-    q.lam = K.nu4 * q.F * q.r2 * q.inv;
-    q.wx = xsph ? K.m2Wc * t3 * q.t * fmaf(q.r, K.two_inv_h, 1.0f) / q.S : 0.0f;
+    const float e = r2 + K.eh2;
+    const float S = rhoi + rhoj;
+    const float ie = __fdividef(1.0f, e), iS = __fdividef(1.0f, S);
+    const float inv = ie * iS;
+    const float Csum = Ci + Cj;
+    const float mvr = fminf(q.vr, 0.0f);
+    q.Q = Pi + Pj + Csum * mvr * inv;
+    q.lam = K.nu4 * q.F * r2 * inv;
+    // the partials of the reverse sweep
+    q.kFr2 = K.nu4 * r2 * inv;          // d lam / dF
+    q.kLamR2 = K.nu4 * q.F * inv;       // d lam / d r2 (at fixed inv)
+    q.kLamInv = K.nu4 * q.F * r2;       // d lam / d inv
+    q.kC = mvr * inv;                   // d Pi / d Csum
+    q.kVr = q.vr < 0.0f ? Csum * inv : 0.0f;   // d Pi / d vr (the switch)
+    q.kInv = Csum * mvr;                // d Pi / d inv
+    if (xsph) {
+        const float poly = fmaf(r, K.two_inv_h, 1.0f);
+        q.wx = K.m2Wc * t3 * t * poly * iS;
+        q.kWxT = K.m2Wc * 4.0f * t3 * poly * iS;
+        q.kWxR = K.m2Wc * t3 * t * K.two_inv_h * iS;
+        q.kWxS = -q.wx * iS;
+    } else {
+        q.wx = q.kWxT = q.kWxR = q.kWxS = 0.0f;
+    }
+    q.kInvR2 = -inv * ie;               // d inv / d r2
+    q.kInvS = -inv * iS;                // d inv / d S
+    q.kFt = 3.0f * mjFc * t2;           // dF / dt
+    q.kTr = t0 > 0.0f ? -K.half_inv_h : 0.0f;   // dt / dr
+    q.kRr2 = r2 > 0.0f ? 0.5f * rinv : 0.0f;    // dr / d r2
 }
 
 // Adjoint of one pair for the weights (wA on the acceleration sum, wDr on the
@@ -160,8 +184,8 @@ struct PairAdj {
     float gdx, gdy, gvx, gvy, gS, gQ, gC;
 };
 
-__device__ __forceinline__ PairAdj pair_rev(const Consts &K, const PairFwd &q, float wAx, float wAy,
-                                            float wDr, float wXx, float wXy)
+__device__ __forceinline__ PairAdj pair_rev(const PairFwd &q, float wAx, float wAy, float wDr,
+                                            float wXx, float wXy)
 {
     const float PF = q.Q * q.F;
     // f = -PF d + lam v,  Dr = F vr,  X = wx v
@@ -170,44 +194,28 @@ __device__ __forceinline__ PairAdj pair_rev(const Consts &K, const PairFwd &q, f
     const float gwx = fmaf(wXx, q.vx, wXy * q.vy);
     float gdx = -PF * wAx, gdy = -PF * wAy;
     float gvx = fmaf(q.lam, wAx, q.wx * wXx), gvy = fmaf(q.lam, wAy, q.wx * wXy);
-    float gvr = wDr * q.F;
-    float gF = wDr * q.vr;
-    // PF = Q F
+    // PF = Q F; lam = nu4 F r2 inv
     const float gQ = gPF * q.F;
-    gF = fmaf(gPF, q.Q, gF);
-    // lam = nu4 F r2 inv
-    gF = fmaf(glam, K.nu4 * q.r2 * q.inv, gF);
-    float gr2 = glam * K.nu4 * q.F * q.inv;
-    float ginv = glam * K.nu4 * q.F * q.r2;
-    // Pi_ij = Csum min(vr, 0) inv, inside Q
-    const float gC = gQ * q.mvr * q.inv;
-    if (q.comp) gvr = fmaf(gQ, q.Csum * q.inv, gvr);
-    ginv = fmaf(gQ, q.Csum * q.mvr, ginv);
-    // wx = m2Wc t^4 (1 + 2 r / h) / S
-    float gt = 0.0f, gr = 0.0f, gS = 0.0f;
-    if (q.wx != 0.0f) {
-        const float t3 = q.t * q.t * q.t;
-        const float poly = fmaf(q.r, K.two_inv_h, 1.0f);
-        gt = gwx * K.m2Wc * 4.0f * t3 * poly / q.S;
-        gr = gwx * K.m2Wc * t3 * q.t * K.two_inv_h / q.S;
-        gS = -gwx * q.wx / q.S;
-    }
-    // inv = 1 / (e S), e = r2 + eta^2 h^2
-    gr2 = fmaf(-ginv, q.inv / q.e, gr2);
-    gS = fmaf(-ginv, q.inv / q.S, gS);
-    // F = mj Fc t^3
-    gt = fmaf(gF, 3.0f * q.mjFc * q.t * q.t, gt);
-    // t = max(1 - r / 2h, 0)
-    if (q.tpos) gr = fmaf(-K.half_inv_h, gt, gr);
-    // r = sqrt(r2)
-    if (q.r > 0.0f) gr2 = fmaf(gr, 0.5f / q.r, gr2);
+    float gF = fmaf(wDr, q.vr, fmaf(gPF, q.Q, glam * q.kFr2));
+    float gr2 = glam * q.kLamR2;
+    float ginv = fmaf(gQ, q.kInv, glam * q.kLamInv);
+    // Pi_ij = Csum min(vr, 0) inv inside Q; Dr = F vr
+    const float gC = gQ * q.kC;
+    const float gvr = fmaf(gQ, q.kVr, wDr * q.F);
+    // wx = m2Wc t^4 (1 + 2 r / h) / S; inv = 1 / (e S)
+    float gt = gwx * q.kWxT;
+    float gr = gwx * q.kWxR;
+    const float gS = fmaf(gwx, q.kWxS, ginv * q.kInvS);
+    gr2 = fmaf(ginv, q.kInvR2, gr2);
+    // F = mj Fc t^3, t = max(1 - r / 2h, 0), r = sqrt(r2)
+    gt = fmaf(gF, q.kFt, gt);
+    gr = fmaf(gt, q.kTr, gr);
+    gr2 = fmaf(gr, q.kRr2, gr2);
     // vr = v . d,  r2 = d . d
     gvx = fmaf(gvr, q.dx, gvx);
     gvy = fmaf(gvr, q.dy, gvy);
-    gdx = fmaf(gvr, q.vx, gdx);
-    gdy = fmaf(gvr, q.vy, gdy);
-    gdx = fmaf(2.0f * gr2, q.dx, gdx);
-    gdy = fmaf(2.0f * gr2, q.dy, gdy);
+    gdx = fmaf(gvr, q.vx, fmaf(2.0f * gr2, q.dx, gdx));
+    gdy = fmaf(gvr, q.vy, fmaf(2.0f * gr2, q.dy, gdy));
     return PairAdj{gdx, gdy, gvx, gvy, gS, gQ, gC};
 }
 
@@ -235,8 +243,10 @@ __device__ __forceinline__ T lane_sum(T v)
 // derivative is added to component 0 of the end-of-step adjoints and of the
 // c0 accumulator (the Tait pressure of each neighbour depends on c0).  One
 // warp; each neighbour is written by one lane.
-__global__ void ka_probe(Consts K, Bufs B, ABufs A)
+__global__ void ka_probe(Consts K, Bufs B, ABufs A, long long peak_row)
 {
+    // the record's scalars count the step it closes: seed only the peak's step
+    if (B.S->step - 1 != peak_row) return;
     const int lane = threadIdx.x & 31;
     const float px = K.probe_x[0], py = K.probe_y[0];
     if (outside_box(K, px, py)) return;
@@ -244,7 +254,9 @@ __global__ void ka_probe(Consts K, Bufs B, ABufs A)
     float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
     for (int dy = -1; dy <= 1; ++dy) {
         const int row = c + dy * K.ncx;
+        if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, A.status)) continue;
         const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+        if (kChecked && !row_ok(K, row, a, b, K.nf, A.status)) continue;
         for (int j = a + lane; j < b; j += 32) {
             const float2 rj = B.s_pos[j];
             if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
@@ -270,7 +282,9 @@ __global__ void ka_probe(Consts K, Bufs B, ABufs A)
     float c0bar = 0.0f;
     for (int dy = -1; dy <= 1; ++dy) {
         const int row = c + dy * K.ncx;
+        if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, A.status)) continue;
         const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+        if (kChecked && !row_ok(K, row, a, b, K.nf, A.status)) continue;
         for (int j = a + lane; j < b; j += 32) {
             const float2 rj = B.s_pos[j];
             if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
@@ -318,6 +332,8 @@ __global__ void __launch_bounds__(kAThreads) ka_epilogue(Consts K, Bufs B, ABufs
         const float2 a1 = B.st_a[i];
         const float Dd = B.st_D[i].x;
         const bool clamp = dn <= K.d_lo || dn >= K.d_hi;
+        float2 wAc[kOut], wXc[kOut];
+        float wDc[kOut];
 #pragma unroll
         for (int c = 0; c < kOut; ++c) {
             const int q = i * kOut + c;
@@ -347,12 +363,15 @@ __global__ void __launch_bounds__(kAThreads) ka_epilogue(Consts K, Bufs B, ABufs
                 wDr = K.m_over_rho0 * lDd;
                 wX = make_float2(K.m * lX.x, K.m * lX.y);
             }
-            A.wA[q] = wA;
-            A.wX[q] = wX;
-            A.wDr[q] = wDr;
+            wAc[c] = wA;
+            wXc[c] = wX;
+            wDc[c] = wDr;
             A.lvh[q] = lv;
             A.lrd[q] = make_float2(lrdx, lrdy);
         }
+        A.wA[i] = make_float4(wAc[0].x, wAc[0].y, wAc[1].x, wAc[1].y);
+        A.wX[i] = make_float4(wXc[0].x, wXc[0].y, wXc[1].x, wXc[1].y);
+        A.wDr[i] = make_float2(wDc[0], wDc[1]);
     }
     // the priming pass runs with the constant dt = 0, not with the case's dt
     if (prime) dtp[0] = dtp[1] = 0.0f;
@@ -410,7 +429,9 @@ __global__ void __launch_bounds__(kAGhostWarps * 32) ka_ghost(Consts K, Bufs B, 
         const int cc = cell_of(K, rg.x, rg.y);
         for (int dy = -1; dy <= 1; ++dy) {
             const int row = cc + dy * K.ncx;
+            if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, A.status)) continue;
             const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, A.status)) continue;
             for (int j = a + lane; j < b; j += 32) {
                 const float2 rj = B.s_pos[j];
                 if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
@@ -428,14 +449,16 @@ __global__ void __launch_bounds__(kAGhostWarps * 32) ka_ghost(Consts K, Bufs B, 
                 PairFwd q;
                 pair_fwd(K, rj, vj, fmaf(K.rho0, aux.x, K.rho0), aux.z, aux.w, rg, vg, rhog, ag.z,
                          ag.w, mjg, false, q);
+                const float4 wa4 = A.wA[j];
+                const float2 wd2 = A.wDr[j];
 #pragma unroll
                 for (int c = 0; c < kOut; ++c) {
-                    float2 wa = A.wA[j * kOut + c];
+                    float2 wa = c == 0 ? make_float2(wa4.x, wa4.y) : make_float2(wa4.z, wa4.w);
                     if (c == 1 && side) {
                         wa.x = fmaf(jw, nrm.x, wa.x);
                         wa.y = fmaf(jw, nrm.y, wa.y);
                     }
-                    const PairAdj p = pair_rev(K, q, wa.x, wa.y, A.wDr[j * kOut + c], 0.f, 0.f);
+                    const PairAdj p = pair_rev(q, wa.x, wa.y, c == 0 ? wd2.x : wd2.y, 0.f, 0.f);
                     gd[c] = fmaf(K.rho0, p.gS, gd[c]);
                     gP[c] += p.gQ;
                     gC[c] += p.gC;
@@ -504,7 +527,9 @@ __global__ void __launch_bounds__(kAGhostWarps * 32) ka_ghost(Consts K, Bufs B, 
                 for (int c = 0; c < kOut; ++c) hs[c] = make_float2(0.f, 0.f);
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int row = cc + dy * K.ncx;
+                    if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, A.status)) continue;
                     const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                    if (kChecked && !row_ok(K, row, a, b, K.nf, A.status)) continue;
                     for (int j = a + lane; j < b; j += 32) {
                         const float2 rj = B.s_pos[j];
                         if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
@@ -594,19 +619,15 @@ __global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, 
         const float2 vk = B.s_vel[k];
         const float4 ak = B.s_aux[k];
         const float rhok = fmaf(K.rho0, ak.x, K.rho0);
-        float2 wAk[kOut], wXk[kOut];
-        float wDk[kOut];
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) {
-            wAk[c] = A.wA[k * kOut + c];
-            wXk[c] = A.wX[k * kOut + c];
-            wDk[c] = A.wDr[k * kOut + c];
-        }
+        const float4 wAk = A.wA[k], wXk = A.wX[k];
+        const float2 wDk = A.wDr[k];
         const int cc = cell_of(K, rk.x, rk.y);
 #pragma unroll 1
         for (int dy = -1; dy <= 1; ++dy) {
             const int row = cc + dy * K.ncx;
+            if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, A.status)) continue;
             const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, A.status)) continue;
 #pragma unroll 1
             for (int base = a; base < b; base += 32) {
                 unsigned m = support_mask(B.s_pos, base, min(32, b - base), rk, K.s2);
@@ -620,12 +641,15 @@ __global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, 
                     PairFwd q;
                     pair_fwd(K, rk, vk, rhok, ak.z, ak.w, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
                              aj.w, 1.0f, true, q);
+                    const float4 wAj = A.wA[j], wXj = A.wX[j];
+                    const float2 wDj = A.wDr[j];
 #pragma unroll
                     for (int c = 0; c < kOut; ++c) {
-                        const float2 wAj = A.wA[j * kOut + c], wXj = A.wX[j * kOut + c];
-                        const float wDj = A.wDr[j * kOut + c];
-                        const PairAdj p = pair_rev(K, q, wAk[c].x - wAj.x, wAk[c].y - wAj.y,
-                                                   wDk[c] + wDj, wXk[c].x - wXj.x, wXk[c].y - wXj.y);
+                        const PairAdj p =
+                            c == 0 ? pair_rev(q, wAk.x - wAj.x, wAk.y - wAj.y, wDk.x + wDj.x,
+                                              wXk.x - wXj.x, wXk.y - wXj.y)
+                                   : pair_rev(q, wAk.z - wAj.z, wAk.w - wAj.w, wDk.y + wDj.y,
+                                              wXk.z - wXj.z, wXk.w - wXj.w);
                         gpos[c].x += p.gdx;
                         gpos[c].y += p.gdy;
                         gvh[c].x += p.gvx;
@@ -647,12 +671,12 @@ __global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, 
             const float2 nrm = side ? B.gw_nrm[g] : make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < kOut; ++c) {
-                float2 wa = wAk[c];
+                float2 wa = c == 0 ? make_float2(wAk.x, wAk.y) : make_float2(wAk.z, wAk.w);
                 if (c == 1 && side) {
                     wa.x = fmaf(jw, nrm.x, wa.x);
                     wa.y = fmaf(jw, nrm.y, wa.y);
                 }
-                const PairAdj p = pair_rev(K, q, wa.x, wa.y, wDk[c], 0.f, 0.f);
+                const PairAdj p = pair_rev(q, wa.x, wa.y, c == 0 ? wDk.x : wDk.y, 0.f, 0.f);
                 gpos[c].x += p.gdx;
                 gpos[c].y += p.gdy;
                 gvh[c].x += p.gvx;
@@ -664,7 +688,7 @@ __global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, 
             shepard_share(K, A, g, rg, rk, vk, ak, gpos, gvh, grec);
         };
         if (K.nw > 0)
-            for_fluid_candidates(K, B.wall_start, cc, [&](int g) {
+            for_fluid_candidates(K, B.wall_start, cc, K.nw, A.status, [&](int g) {
                 const float2 rg = B.gw_pos[g];
                 if (!in_support(rk.x, rk.y, rg.x, rg.y, K.s2)) return;
                 ghost_pair(g, rg, K.wall_over_m, B.gw_kind[g] == KIND_SIDE);
@@ -672,7 +696,7 @@ __global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, 
         if (K.ng > 0) {
             const float xc = B.S->xc_f, yc = B.S->yc_f;
             if (near_disk(K, rk.x, rk.y, xc, yc))
-                for_disk_arc(disk_arc(K, rk.x, rk.y, xc, yc), [&](int kk) {
+                for_disk_arc(K, disk_arc(K, rk.x, rk.y, xc, yc), A.status, [&](int kk) {
                     const float2 rg = B.gd_pos[kk];
                     if (outside_box(K, rg.x, rg.y)) return;
                     if (!in_support(rk.x, rk.y, rg.x, rg.y, K.s2)) return;

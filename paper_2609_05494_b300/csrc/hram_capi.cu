@@ -189,12 +189,12 @@ __global__ void k_neighbors(Consts K, Bufs B, int *count, const long long *off, 
         const float2 ri = B.s_pos[r];
         if (!outside_box(K, ri.x, ri.y)) {
             const int c = cell_of(K, ri.x, ri.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+            for_fluid_candidates(K, B.cell_start, c, K.nf, &B.S->status, [&](int j) {
                 const float2 rj = B.s_pos[j];
                 if (j != r && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) emit(B.s_id[j]);
             });
             if (K.nw > 0)
-                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
                     const float2 rg = B.gw_pos[k];
                     if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) emit(K.nf + B.gw_id[k]);
                 });
@@ -210,7 +210,7 @@ __global__ void k_neighbors(Consts K, Bufs B, int *count, const long long *off, 
         const float2 rg = g < K.nw ? B.gw_pos[g] : B.gd_pos[g - K.nw];
         if (!outside_box(K, rg.x, rg.y)) {
             const int c = cell_of(K, rg.x, rg.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+            for_fluid_candidates(K, B.cell_start, c, K.nf, &B.S->status, [&](int j) {
                 const float2 rj = B.s_pos[j];
                 if (in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) emit(B.s_id[j]);
             });
@@ -246,12 +246,12 @@ __global__ void k_neighbor_counts_static(Consts K, Bufs B, int *counts)
         const float2 ri = B.s_pos[r];
         if (!outside_box(K, ri.x, ri.y)) {
             const int c = cell_of(K, ri.x, ri.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+            for_fluid_candidates(K, B.cell_start, c, K.nf, &B.S->status, [&](int j) {
                 const float2 rj = B.s_pos[j];
                 if (j != r && in_support(ri.x, ri.y, rj.x, rj.y, K.s2)) ++n;
             });
             if (K.nw > 0)
-                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
                     const float2 rg = B.gw_pos[k];
                     if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) ++n;
                 });
@@ -268,7 +268,7 @@ __global__ void k_neighbor_counts_static(Consts K, Bufs B, int *counts)
         const float2 rg = g < K.nw ? B.gw_pos[g] : B.gd_pos[g - K.nw];
         if (!outside_box(K, rg.x, rg.y)) {
             const int c = cell_of(K, rg.x, rg.y);
-            for_fluid_candidates(K, B.cell_start, c, [&](int j) {
+            for_fluid_candidates(K, B.cell_start, c, K.nf, &B.S->status, [&](int j) {
                 const float2 rj = B.s_pos[j];
                 if (in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) ++n;
             });
@@ -835,7 +835,8 @@ int device_status(hr_case *c)
     int st = 0;
     CK(cudaMemcpy(&st, &c->B.S->status, sizeof(int), cudaMemcpyDeviceToHost));
     int rc = st & (HR_WPENETRATION | HR_WOUTSIDE | HR_WPROBEFULL);
-    if (st & ST_NAN) rc = HR_ENAN;
+    if (st & ST_BOUNDS) rc = HR_ECHECK;
+    else if (st & ST_NAN) rc = HR_ENAN;
     else if (st & ST_DT) rc = HR_EDT;
     if (rc < 0) c->sticky = rc;
     return c->sticky < 0 ? c->sticky : rc;
@@ -946,6 +947,9 @@ struct AdjCtx {
     Slot prime_slot{}, upload{};  // the priming pass and its input (fluid-ID order)
     std::vector<Slot> ckpt;       // ckpt[k]: the state after step k L (ckpt[0] = prime_slot)
     Scalars *S_final = nullptr;   // the scalars after the forward run
+    Slot start{};                 // the state a segment starts from (a copy of its checkpoint)
+    cudaGraph_t seg_graph[2] = {nullptr, nullptr};        // one full segment, by the parity
+    cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};     // of the adjoint buffers at its start
     ABufs A{};
     LState ls[2]{};
     int ep_blocks = 0, bk_blocks = 0, gh_blocks = 0;
@@ -959,6 +963,10 @@ namespace {
 void adj_free(hr_case *c)
 {
     if (!c->adj) return;
+    for (int k = 0; k < 2; ++k) {
+        if (c->adj->seg_exec[k]) cudaGraphExecDestroy(c->adj->seg_exec[k]);
+        if (c->adj->seg_graph[k]) cudaGraphDestroy(c->adj->seg_graph[k]);
+    }
     if (c->adj->mem) cudaFree(c->adj->mem);
     delete c->adj;
     c->adj = nullptr;
@@ -1017,6 +1025,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     for (long long k = 0; k < std::min<long long>(L, n_steps); ++k) tape_o.push_back(full());
     const SlotOff prime_o = full();
     const SlotOff up_o = state();
+    const SlotOff start_o = state();
     std::vector<SlotOff> ck_o;
     for (long long k = 1; k < n_ck; ++k) ck_o.push_back(state());
     const size_t sfin = Lo.add(sizeof(Scalars));
@@ -1029,7 +1038,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     a->ep_blocks = (int)((n + kAThreads - 1) / kAThreads);
     a->bk_blocks = a->ep_blocks;
     a->gh_blocks = (int)std::max<size_t>(1, (ngh + kAGhostWarps - 1) / kAGhostWarps);
-    const size_t wA = Lo.add(nq * 8), wX = Lo.add(nq * 8), wDr = Lo.add(nq * 4);
+    const size_t wA = Lo.add(n * 16), wX = Lo.add(n * 16), wDr = Lo.add(n * 8);
     const size_t lpos = Lo.add(nq * 8), lvh = Lo.add(nq * 8), lrec = Lo.add(nq * 16),
                  lrd = Lo.add(nq * 8);
     const size_t gS1 = Lo.add(gq * 16), gS2 = Lo.add(gq * 8), gpar = Lo.add(gq * 16),
@@ -1070,6 +1079,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     for (auto &o : tape_o) a->tape.push_back(mk(o, true));
     a->prime_slot = mk(prime_o, true);
     a->upload = mk(up_o, false);
+    a->start = mk(start_o, false);
     a->ckpt.push_back(a->prime_slot);
     for (auto &o : ck_o) a->ckpt.push_back(mk(o, false));
     a->S_final = at<Scalars>(w, sfin);
@@ -1084,9 +1094,9 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
         l.E = at<float>(w, ls_o[b][6]);
     }
     ABufs &A = a->A;
-    A.wA = at<float2>(w, wA);
-    A.wX = at<float2>(w, wX);
-    A.wDr = at<float>(w, wDr);
+    A.wA = at<float4>(w, wA);
+    A.wX = at<float4>(w, wX);
+    A.wDr = at<float2>(w, wDr);
     A.lpos = at<float2>(w, lpos);
     A.lvh = at<float2>(w, lvh);
     A.lrec = at<float4>(w, lrec);
@@ -1098,6 +1108,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     A.ep_part = at<float>(w, ep);
     A.bk_part = at<float4>(w, bk);
     A.sc = at<double>(w, sc);
+    A.status = &c->B.S->status;
     return HR_OK;
 }
 
@@ -1190,7 +1201,7 @@ int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, 
     Bp.st_a = prev.st_a;
     Bp.st_D = prev.st_D;
     Bp.st_X = prev.st_X;
-    if (seed_peak && K.n_probes > 0) ka_probe<<<1, 32, 0, s>>>(K, Bc, a->A);
+    if (seed_peak && K.n_probes > 0) ka_probe<<<1, 32, 0, s>>>(K, Bc, a->A, a->peak_row);
     ka_epilogue<<<a->ep_blocks, kAThreads, 0, s>>>(K, Bc, a->A, prime);
     ka_ghost<<<a->gh_blocks, kAGhostWarps * 32, 0, s>>>(K, Bc, a->A, prime);
     ka_pass<<<a->ep_blocks, kAThreads, 0, s>>>(K, Bc, a->A, prime);
@@ -1198,6 +1209,66 @@ int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, 
     ka_close<<<1, kACloseThreads, 0, s>>>(K, Bc, a->A, prime, a->ep_blocks, a->bk_blocks);
     CK(cudaGetLastError());
     std::swap(a->A.cur, a->A.prv);
+    return HR_OK;
+}
+
+// Copies checkpoint k into the segment start state (and its scalars into the
+// live ones the recomputation advances).
+int load_start(hr_case *c, const Slot &k, cudaStream_t s)
+{
+    const Slot &d = c->adj->start;
+    const size_t n = (size_t)c->nf;
+    CK(cudaMemcpyAsync(d.s_pos, k.s_pos, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.s_id, k.s_id, n * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.st_vel, k.st_vel, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.st_rho, k.st_rho, n * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.st_a, k.st_a, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.st_D, k.st_D, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d.st_X, k.st_X, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->B.S, k.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+    return HR_OK;
+}
+
+// One segment of len steps from the start state: the records recomputed
+// forwards, then the reverse sweep through them.
+int launch_segment(hr_case *c, cudaStream_t s, long long len)
+{
+    AdjCtx *a = c->adj;
+    int rc;
+    for (long long k = 0; k < len; ++k) {
+        const Slot &prev = k == 0 ? a->start : a->tape[(size_t)(k - 1)];
+        if ((rc = launch_tape_step(c, s, a->tape[(size_t)k], prev, 0)) != HR_OK) return rc;
+    }
+    for (long long k = len - 1; k >= 0; --k) {
+        const Slot &prev = k == 0 ? a->start : a->tape[(size_t)(k - 1)];
+        if ((rc = adjoint_step(c, s, a->tape[(size_t)k], prev, 0, true)) != HR_OK) return rc;
+    }
+    return HR_OK;
+}
+
+// A full segment (L steps) as one graph launch: captured once for each
+// parity of the adjoint buffers it starts from.
+int run_full_segment(hr_case *c, cudaStream_t s)
+{
+    AdjCtx *a = c->adj;
+    const int par = a->A.cur.r == a->ls[0].r ? 0 : 1;
+    if (!a->seg_exec[par]) {
+        const ABufs keep = a->A;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        const int rc = launch_segment(c, c->cap, a->L);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        a->A = keep;
+        if (rc != HR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(e);
+        a->seg_graph[par] = g;
+        CK(cudaGraphInstantiate(&a->seg_exec[par], g, 0));
+    }
+    CK(cudaGraphLaunch(a->seg_exec[par], s));
+    if (a->L & 1) std::swap(a->A.cur, a->A.prv);
     return HR_OK;
 }
 
@@ -1792,22 +1863,12 @@ int hr_adjoint_backward(hr_case *c, double *out, int n)
     const int L = a->L;
     int rc;
     for (long long seg = (N + L - 1) / L - 1; seg >= 0; --seg) {
-        const long long base = seg * L, end = std::min<long long>(N, base + L);
-        const Slot &start = a->ckpt[(size_t)seg];
-        // recompute the segment's records from its checkpoint
-        CK(cudaMemcpyAsync(c->B.S, start.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
-        for (long long k = base; k < end; ++k) {
-            const Slot &prev = k == base ? start : a->tape[(size_t)(k - base - 1)];
-            if ((rc = launch_tape_step(c, s, a->tape[(size_t)(k - base)], prev, 0)) != HR_OK)
-                return rc;
-        }
-        // and sweep it backwards
-        for (long long k = end - 1; k >= base; --k) {
-            const Slot &prev = k == base ? start : a->tape[(size_t)(k - base - 1)];
-            if ((rc = adjoint_step(c, s, a->tape[(size_t)(k - base)], prev, 0, k == a->peak_row)) !=
-                HR_OK)
-                return rc;
-        }
+        const long long base = seg * L, len = std::min<long long>(N, base + L) - base;
+        // the segment's records recomputed from its checkpoint, then swept
+        // backwards (a full segment is one graph launch)
+        if ((rc = load_start(c, a->ckpt[(size_t)seg], s)) != HR_OK) return rc;
+        rc = len == L ? run_full_segment(c, s) : launch_segment(c, s, len);
+        if (rc != HR_OK) return rc;
     }
     // the priming pass (a0, D0, X0 of the uploaded state)
     if ((rc = adjoint_step(c, s, a->prime_slot, a->upload, 1, false)) != HR_OK) return rc;
@@ -2102,6 +2163,7 @@ const char *hr_status_str(int s)
     case HR_EDT: return "time step underflow";
     case HR_ERANGE: return "buffer too small";
     case HR_EIO: return "checkpoint file error";
+    case HR_ECHECK: return "an index check of the bounds-checked build failed";
     default: break;
     }
     if (s > 0) return "warning (see HR_W* bits)";

@@ -157,6 +157,38 @@ struct Bufs {
     Scalars *S;
 };
 
+// ----------------------------------------------- bounds-checked build
+
+// Built with -DHRAM_CHECKED, every index into the cell lists, the sorted
+// arrays and the ghost arrays is checked before it is used: a failed check
+// sets ST_BOUNDS in the case's status word and the access is skipped (the
+// candidate row or the particle is left out).  Nothing traps.  In the normal
+// build the checks compile away.
+#ifdef HRAM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+constexpr int ST_BOUNDS = 1024;
+
+__device__ __forceinline__ bool hr_ok(bool cond, int *status)
+{
+    if constexpr (kChecked) {
+        if (!cond) {
+            atomicOr(status, ST_BOUNDS);
+            return false;
+        }
+    }
+    return true;
+}
+
+// A stencil row's candidate range [a, b) of a start array with entries
+// [0, ncell] at least (cell_start, wall_start), items [0, limit).
+__device__ __forceinline__ bool row_ok(const Consts &K, int row, int a, int b, int limit, int *status)
+{
+    return hr_ok(row - 1 >= 0 && row + 2 <= K.ncell && 0 <= a && a <= b && b <= limit, status);
+}
+
 // ---------------------------------------------------------------- helpers
 
 // Neighbour predicate of the method: FP32, round-to-nearest, no contraction.
@@ -444,12 +476,15 @@ __device__ inline void kinematics(const Consts &K, double t, double *xo, double 
 // contiguous row ranges [start(row, cx-1), start(row, cx+2)) of the sorted
 // arrays.  f(j) is called for every candidate j.
 template <class F>
-__device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c, F &&f)
+__device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c,
+                                                     int limit, int *status, F &&f)
 {
 #pragma unroll 1
     for (int dy = -1; dy <= 1; ++dy) {
         const int row = c + dy * K.ncx;
+        if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, status)) continue;
         const int a = start[row - 1], b = start[row + 2];
+        if (kChecked && !row_ok(K, row, a, b, limit, status)) continue;
         for (int j = a; j < b; ++j) f(j);
     }
 }
@@ -495,8 +530,11 @@ __device__ __forceinline__ DiskArc disk_arc(const Consts &K, float x, float y, f
 
 // f(k) for the ghosts of the arc, in ascending k.
 template <class F>
-__device__ __forceinline__ void for_disk_arc(const DiskArc &A, F &&f)
+__device__ __forceinline__ void for_disk_arc(const Consts &K, const DiskArc &A, int *status, F &&f)
 {
+    if (kChecked && !hr_ok(0 <= A.a0 && A.a0 <= A.a1 && A.a1 <= K.ng && 0 <= A.b0 &&
+                           A.b0 <= A.b1 && A.b1 <= K.ng, status))
+        return;
 #pragma unroll 1
     for (int k = A.a0; k < A.a1; ++k) f(k);
 #pragma unroll 1
@@ -732,7 +770,10 @@ __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int
     }
     const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
-    const int dst = B.cell_start[B.u_key[i]] + B.u_slot[i];
+    const int key = B.u_key[i];
+    if (kChecked && !hr_ok(key >= 0 && key <= K.ncell, &B.S->status)) return;
+    const int dst = B.cell_start[key] + B.u_slot[i];
+    if (kChecked && !hr_ok(dst >= 0 && dst < K.nf, &B.S->status)) return;
     B.perm_tmp[dst] = B.u_id[i];
 }
 
@@ -754,7 +795,9 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     const float2 D = B.st_D[i];
     const float2 up = B.u_pos[i];
     float2 uv = B.u_vel[i];
+    if (kChecked && !hr_ok(key >= 0 && key <= K.ncell, &B.S->status)) return;
     const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
+    if (kChecked && !hr_ok(0 <= cs && cs < ce && ce <= K.nf, &B.S->status)) return;
     float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 a = make_float2(0.f, 0.f);
     if constexpr (CL == 1) {
@@ -777,6 +820,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
 #pragma unroll 4
     for (int k = cs; k < ce; ++k) rank += __ldg(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
+    if (kChecked && !hr_ok(dst < ce, &B.S->status)) return;
     B.s_pos[dst] = up;
     B.s_vel[dst] = uv;
     if constexpr (CL == 1) B.s_ex[dst] = make_float4(a.x, a.y, D.y, D.x);
@@ -846,7 +890,9 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
 #pragma unroll 1
         for (int dy = -1; dy <= 1; ++dy) {
             const int row = c + dy * K.ncx;
+            if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
             const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
 #pragma unroll 1
             for (int base = a; base < b; base += 32) {
                 unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
@@ -861,7 +907,7 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
         }
         if (K.nw > 0) {
             const float mw = K.m_over_rho0 * K.wall_over_m;
-            for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+            for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
                 const float2 rg = __ldg(&B.gw_pos[k]);
                 if (in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) S = fmaf(mw, w_at(rg.x, rg.y), S);
             });
@@ -869,7 +915,7 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
         const float xc = B.S->xc_f, yc = B.S->yc_f;
         if (K.ng > 0 && near_disk(K, ri.x, ri.y, xc, yc)) {
             const float md = K.m_over_rho0 * K.disk_over_m;
-            for_disk_arc(disk_arc(K, ri.x, ri.y, xc, yc), [&](int k) {
+            for_disk_arc(K, disk_arc(K, ri.x, ri.y, xc, yc), &B.S->status, [&](int k) {
                 const float2 rg = B.gd_pos[k];
                 if (outside_box(K, rg.x, rg.y) || !in_support(ri.x, ri.y, rg.x, rg.y, K.s2))
                     return;
@@ -909,7 +955,9 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
 #pragma unroll 1
             for (int dy = -1; dy <= 1; ++dy) {
                 const int row = c + dy * K.ncx;
+                if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
                 const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
                 for (int j = a + lane; j < b; j += 32) {
                     const float2 rj = __ldg(&B.s_pos[j]);
                     if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
@@ -1062,11 +1110,16 @@ __device__ __forceinline__ void pass_fluid(const Consts &K, const Bufs &B, int i
     unsigned m0, m1, m2;
     {
         const int r0 = c - K.ncx, r1 = c, r2 = c + K.ncx;
+        if (kChecked && !hr_ok(r0 - 1 >= 0 && r2 + 2 <= K.ncell, &B.S->status)) return;
         base0 = B.cell_start[r0 - 1];
         base1 = B.cell_start[r1 - 1];
         base2 = B.cell_start[r2 - 1];
         const int e0 = B.cell_start[r0 + 2], e1 = B.cell_start[r1 + 2],
                   e2 = B.cell_start[r2 + 2];
+        if (kChecked && !(row_ok(K, r0, base0, e0, K.nf, &B.S->status) &&
+                          row_ok(K, r1, base1, e1, K.nf, &B.S->status) &&
+                          row_ok(K, r2, base2, e2, K.nf, &B.S->status)))
+            return;
         // rows longer than 32 candidates: chunks evaluated right away
         auto row_mask = [&](int a, int b) -> unsigned {
             if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri, K.s2);
@@ -1114,7 +1167,7 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
 {
     // wall ghosts (static cell list)
     if (K.nw > 0) {
-        for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+        for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
             const float2 rg = __ldg(&B.gw_pos[k]);
             if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
             const float4 ag = B.g_aux[k];
@@ -1132,7 +1185,7 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
     if (K.ng > 0) {
         const float xc = B.S->xc_f, yc = B.S->yc_f;
         if (near_disk(K, ri.x, ri.y, xc, yc)) {
-            for_disk_arc(disk_arc(K, ri.x, ri.y, xc, yc), [&](int k) {
+            for_disk_arc(K, disk_arc(K, ri.x, ri.y, xc, yc), &B.S->status, [&](int k) {
                 const float2 rg = B.gd_pos[k];
                 if (outside_box(K, rg.x, rg.y)) return;
                 if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
@@ -1277,9 +1330,15 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
     float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
     if (!outside_box(K, px, py)) {
         const int c = cell_of(K, px, py);
+        if (kChecked && !hr_ok(c - K.ncx - 1 >= 0 && c + K.ncx + 2 <= K.ncell, &B.S->status))
+            return 0.0f;
         const int a0 = B.cell_start[c - K.ncx - 1], b0 = B.cell_start[c - K.ncx + 2];
         const int a1 = B.cell_start[c - 1], b1 = B.cell_start[c + 2];
         const int a2 = B.cell_start[c + K.ncx - 1], b2 = B.cell_start[c + K.ncx + 2];
+        if (kChecked && !(row_ok(K, c - K.ncx, a0, b0, K.nf, &B.S->status) &&
+                          row_ok(K, c, a1, b1, K.nf, &B.S->status) &&
+                          row_ok(K, c + K.ncx, a2, b2, K.nf, &B.S->status)))
+            return 0.0f;
         const int n0 = b0 - a0, n1 = b1 - a1, n = n0 + n1 + (b2 - a2);
         for (int k = lane; k < n; k += 32) {
             const int j = k < n0 ? a0 + k : (k < n0 + n1 ? a1 + (k - n0) : a2 + (k - n0 - n1));

@@ -563,7 +563,9 @@ __global__ void __launch_bounds__(kGhostWarps * 32) kt_ghost(Consts K, Bufs B, T
         const int c = cell_of(K, rgf.x, rgf.y);
         for (int dy = -1; dy <= 1; ++dy) {
             const int row = c + dy * K.ncx;
+            if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
             const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
             for (int j = a + lane; j < b; j += 32) {
                 const float2 rj = B.s_pos[j];
                 if (!in_support(rgf.x, rgf.y, rj.x, rj.y, K.s2)) continue;
@@ -649,7 +651,9 @@ __global__ void __launch_bounds__(kTPassThreads) kt_pass(Consts K, Bufs B, TBufs
 #pragma unroll 1
             for (int dy = -1; dy <= 1; ++dy) {
                 const int row = c + dy * K.ncx;
+                if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
                 const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
 #pragma unroll 1
                 for (int base = a; base < b; base += 32) {
                     unsigned m = support_mask(B.s_pos, base, min(32, b - base), ri, K.s2);
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(kTPassThreads) kt_pass(Consts K, Bufs B, TBufs
                 }
             }
             if (K.nw > 0)
-                for_fluid_candidates(K, B.wall_start, c, [&](int k) {
+                for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
                     const float2 rg = B.gw_pos[k];
                     if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
                     D3 vgx, vgy, ag[4];
@@ -743,7 +747,9 @@ __global__ void __launch_bounds__(kTFinThreads) kt_finalize(Consts K, Bufs B, TB
             const int c = cell_of(K, px, py);
             for (int dy = -1; dy <= 1; ++dy) {
                 const int row = c + dy * K.ncx;
+                if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
                 const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
                 for (int j = a + lane; j < b; j += 32) {
                     const float2 rj = B.s_pos[j];
                     if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;

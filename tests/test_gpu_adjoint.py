@@ -41,7 +41,10 @@ def tangent(p, xy, n, vel=None):
         return c.tangent_outputs()
 
 
-def agree(a, t, scale, rel=1e-4, floor=1e-7):
+def agree(a, t, scale, rel=1e-4, floor=1e-4):
+    # 1e-4 of the derivative, or of the output itself per unit ln(theta) where
+    # the derivative nearly cancels (the float32 sums behind both modes carry
+    # terms of the output's size)
     return abs(a - t) <= rel * abs(t) + floor * abs(scale)
 
 
