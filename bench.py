@@ -209,15 +209,36 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     t_batch = time.perf_counter() - t0
     same = all(np.array_equal(a.probe_pressure(), g.probe_pressure()) for a, g in
                zip(serial[:4], batched[:4]))
+    # the same sweep as one persistent launch, block counts per case autotuned
+    t0 = time.perf_counter()
+    blocks, ptune = autotune.tune_persistent(specs, t_end, stream=stream)
+    t_ptune = time.perf_counter() - t0
+    persist = [Case(p, xy, stream=stream) for p, xy in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Batch(persist, t_end, stream=stream, persistent=True, case_blocks=blocks) as b:
+        b.run()
+    torch.cuda.synchronize()
+    t_persist = time.perf_counter() - t0
+    same_p = all(np.array_equal(a.probe_pressure(), g.probe_pressure()) and
+                 np.array_equal(a.get_state()["xy"], g.get_state()["xy"])
+                 for a, g in zip(serial, persist))
     particles = sum(xy.shape[0] for _, xy in specs)
     t_serial = max_over_ranks(t_serial * 1e3, dist) * 1e-3
     t_batch = max_over_ranks(t_batch * 1e3, dist) * 1e-3
-    for c in serial + batched:
+    t_persist = max_over_ranks(t_persist * 1e3, dist) * 1e-3
+    for c in serial + batched + persist:
         c.close()
     return {"cases": n_cases, "cases_per_rank": len(specs), "t_end_s": t_end,
             "particles": particles, "serial_s": t_serial, "batched_s": t_batch,
             "speedup": t_serial / t_batch, "case_steps": steps_serial,
             "batched_launch_steps": n_batched_steps, "batched_equals_serial": bool(same),
+            "persistent_s": t_persist, "persistent_speedup": t_serial / t_persist,
+            "persistent_over_batched": t_batch / t_persist,
+            "persistent_equals_serial": bool(same_p),
+            "persistent_blocks": {"min": int(blocks.min()), "max": int(blocks.max()),
+                                  "total": int(blocks.sum())},
+            "persistent_autotune": ptune, "persistent_autotune_s": t_ptune,
             "autotune": tune_report, "autotune_s": t_tune}
 
 

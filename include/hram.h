@@ -48,6 +48,7 @@ extern "C" {
 #define HR_ECUDA (-3)     /* a CUDA call failed */
 #define HR_ENAN (-4)      /* NaN or Inf appeared in the fluid state */
 #define HR_EDT (-5)       /* time step underflow (dt < 1e-14 s) */
+#define HR_ETIMEOUT (-6)  /* a bounded device wait gave up (persistent batch barrier) */
 #define HR_ERANGE (-7)    /* caller buffer too small */
 #define HR_EIO (-8)       /* file error in save / load */
 #define HR_ECHECK (-9)    /* an index check failed; only the bounds-checked build
@@ -253,7 +254,31 @@ typedef struct hr_batch hr_batch;
 int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedule,
                     void *cuda_stream, hr_batch **out);
 
-/* One batched step (graph replay), asynchronous. */
+/* The same sweep as one persistent launch (Section 4.5's sensitivity study
+ * run as a batch): every case is given case_blocks[k] thread blocks of its
+ * own (NULL: in proportion to the particle counts), all blocks stay
+ * resident (a cooperative launch; the total may not exceed
+ * hr_persist_capacity), and a case's blocks take it through the stages of
+ * each step -- drift, cell scan, reorder, ghosts (eqs. adami-p / adami-v),
+ * interaction pass (Section 2.2), closing reduction and CFL gate (eq. cfl)
+ * -- meeting at a barrier of their own between stages, so cases of
+ * different sizes and time steps run at their own pace.  Results are bit
+ * for bit those of each case run alone.  Every barrier wait gives up after
+ * spin_limit polls (<= 0: 2^24, about 2 s), and hr_batch_run /
+ * hr_batch_step then return HR_ETIMEOUT and mark every case with it (the
+ * cases stopped mid-step).  hr_batch_run runs the whole sweep (max_steps
+ * <= 0) or max_steps steps of each case in one launch; hr_batch_step runs
+ * one.  Same ownership and closure rules as hr_batch_create; t_end > 0. */
+int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
+                               const int32_t *case_blocks, int64_t spin_limit, void *cuda_stream,
+                               hr_batch **out);
+
+/* Resident blocks the persistent batch may use on the current device (its
+ * blocks per multiprocessor times the multiprocessor count), for closure 0
+ * or 1. */
+int hr_persist_capacity(int closure, int32_t *max_blocks);
+
+/* One batched step (graph replay, or one step of a persistent batch). */
 int hr_batch_step(hr_batch *b);
 
 /* Steps until every case has reached t_end (or max_steps batched steps when

@@ -25,6 +25,7 @@ HR_ENOMEM = -2
 HR_ECUDA = -3
 HR_ENAN = -4
 HR_EDT = -5
+HR_ETIMEOUT = -6
 HR_ERANGE = -7
 HR_EIO = -8
 HR_ECHECK = -9
@@ -41,7 +42,8 @@ EXPORTS = (
     "hr_kernel_times", "hr_save_state", "hr_load_state", "hr_tangent_outputs",
     "hr_adjoint_forward", "hr_adjoint_backward",
     "hr_neighbor_counts_static", "hr_batch_create", "hr_batch_step", "hr_batch_run",
-    "hr_batch_done", "hr_batch_destroy", "hr_destroy", "hr_status_str",
+    "hr_batch_done", "hr_batch_destroy", "hr_batch_create_persistent", "hr_persist_capacity",
+    "hr_destroy", "hr_status_str",
 )
 HR_STATIC_NEIGHBOR_MAX = 1 << 21
 
@@ -116,6 +118,8 @@ def lib() -> C.CDLL:
     L.hr_adjoint_backward.argtypes = [vp, vp, C.c_int]
     L.hr_neighbor_counts_static.argtypes = [vp, vp, i64]
     L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, C.c_int, vp, P(vp)]
+    L.hr_batch_create_persistent.argtypes = [vp, C.c_int, C.c_double, vp, i64, vp, P(vp)]
+    L.hr_persist_capacity.argtypes = [C.c_int, P(C.c_int32)]
     L.hr_batch_step.argtypes = [vp]
     L.hr_batch_run.argtypes = [vp, i64, P(i64)]
     L.hr_batch_done.argtypes = [vp, P(C.c_int)]

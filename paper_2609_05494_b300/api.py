@@ -288,17 +288,42 @@ class Batch:
 
     SCHEDULES = ("case-major", "round-robin", "largest-first")
 
-    def __init__(self, cases, t_end: float, stream=None, schedule: int = 0):
+    def __init__(self, cases, t_end: float, stream=None, schedule: int = 0,
+                 persistent: bool = False, case_blocks=None, spin_limit: int = 0):
+        """persistent=True: the whole sweep as one persistent launch
+        (hr_batch_create_persistent) with case_blocks[k] resident blocks for
+        case k (None: in proportion to the particle counts) and barrier
+        waits that give up after spin_limit polls (0: the library's default)."""
         L = lib()
         self.cases = list(cases)
         self.schedule = int(schedule)
+        self.persistent = bool(persistent)
         arr = (C.c_void_p * len(self.cases))(*[c._h for c in self.cases])
         h = C.c_void_p()
-        check(L.hr_batch_create(arr, len(self.cases), float(t_end), self.schedule,
-                                _stream_handle(stream) if stream is not None else
-                                self.cases[0]._stream, C.byref(h)), "hr_batch_create")
+        st = _stream_handle(stream) if stream is not None else self.cases[0]._stream
+        if self.persistent:
+            blocks = None
+            if case_blocks is not None:
+                cb = np.ascontiguousarray(case_blocks, dtype=np.int32)
+                if cb.shape != (len(self.cases),):
+                    raise ValueError("case_blocks needs one entry per case")
+                blocks = cb
+            check(L.hr_batch_create_persistent(arr, len(self.cases), float(t_end),
+                                               None if blocks is None else _ptr(blocks),
+                                               int(spin_limit), st, C.byref(h)),
+                  "hr_batch_create_persistent")
+        else:
+            check(L.hr_batch_create(arr, len(self.cases), float(t_end), self.schedule, st,
+                                    C.byref(h)), "hr_batch_create")
         self._h = h
         self.steps = 0
+
+    @staticmethod
+    def capacity(closure: int = 0) -> int:
+        """Resident blocks a persistent batch may use on this device."""
+        n = C.c_int32(0)
+        check(lib().hr_persist_capacity(int(closure), C.byref(n)), "hr_persist_capacity")
+        return n.value
 
     def step(self) -> None:
         check(lib().hr_batch_step(self._h), "hr_batch_step")

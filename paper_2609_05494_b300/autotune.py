@@ -1,13 +1,18 @@
 """Autotuner for single cases and batched sweeps.
 
-Two choices are tuned by timing them on the device, not by a model:
+Three choices are tuned by timing them on the device, not by a model:
 
 * the cell grid of each case: the cell side as a multiple of the support
   2h (``cell_factor``).  Larger cells mean more candidates per particle in
   the interaction pass but fewer cells to scan in the sort;
 * the block schedule of a batch: the order in which the blocks of each
   batched launch visit the cases (case after case, round robin, largest
-  case first).  Results do not depend on either choice: only time does.
+  case first);
+* the block counts of a persistent batch: how many of the resident blocks
+  each case gets.  Candidates share the capacity in proportion to
+  particles^a x (estimated steps)^b; the estimated steps of a case are its
+  stop time over its fixed-speed time step C h / (c0 + v0).
+Results do not depend on any of these choices: only time does.
 
 Tuning runs work on throw-away copies of the cases, so the cases handed back
 start from the same state as untuned ones.
@@ -97,3 +102,53 @@ def tune_sweep(specs, classes: int = 3, stream=None):
     report["schedule_ms_per_step"] = sched_ms
     report["schedule"] = Batch.SCHEDULES[schedule]
     return tuned, schedule, report
+
+
+BLOCK_WEIGHTS = ((1.0, 0.0), (1.0, 1.0), (1.0, 0.5), (0.5, 1.0))
+
+
+def block_counts(specs, capacity: int, a: float, b: float, t_end: float) -> np.ndarray:
+    """Resident blocks per case: the capacity shared in proportion to
+    particles^a x (t_end / dt_estimate)^b, at least one each."""
+    w = []
+    for p, xy in specs:
+        h = p["h_over_dx"] * p["dx"]
+        dt = p["cfl"] * h / (p["c0"] + p["v0"])
+        w.append(float(xy.shape[0]) ** a * (t_end / dt) ** b)
+    w = np.array(w)
+    n = np.maximum(1, np.floor(capacity * w / w.sum())).astype(np.int64)
+    while n.sum() > capacity:
+        n[np.argmax(n)] -= 1
+    return n.astype(np.int32)
+
+
+def tune_persistent(specs, t_end: float, horizon: float = 60e-6, stream=None, weights=BLOCK_WEIGHTS):
+    """Block counts of a persistent batch: each candidate split of the resident
+    blocks (weights (a, b) of block_counts) runs the sweep's first ``horizon``
+    seconds of simulated time on throw-away copies; the fastest split wins.
+    Returns (case_blocks, report)."""
+    import torch
+    closure = int(specs[0][0].get("closure", 0))
+    cap = Batch.capacity(closure)
+    report = {"capacity": cap, "candidates": []}
+    best, best_ms = None, None
+    for a, b in weights:
+        nb = block_counts(specs, cap, a, b, t_end)
+        cases = [Case(p, xy, stream=stream) for p, xy in specs]
+        s = torch.cuda.current_stream() if stream is None else stream
+        with Batch(cases, min(horizon, t_end), stream=stream, persistent=True,
+                   case_blocks=nb) as bt:
+            e0, e1 = _events()
+            e0.record(s)
+            bt.run()
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        for c in cases:
+            c.close()
+        report["candidates"].append({"a": a, "b": b, "ms": ms,
+                                     "blocks_min": int(nb.min()), "blocks_max": int(nb.max())})
+        if best_ms is None or ms < best_ms:
+            best, best_ms = nb, ms
+    report["chosen"] = {"blocks": best.tolist(), "ms": best_ms}
+    return best, report

@@ -11,8 +11,9 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "hram_capi.cu")]
-DEPS = SRC + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [os.path.join(ROOT, "include", "hram.h")]
+SRC = [os.path.join(HERE, "csrc", "hram_capi.cu"), os.path.join(HERE, "csrc", "hram_persist.cu")]
+DEPS = SRC + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
+                    glob.glob(os.path.join(HERE, "csrc", "*.h"))) + [os.path.join(ROOT, "include", "hram.h")]
 LIB = os.path.join(HERE, "libhram.so")
 # the bounds-checked build of the same source (-DHRAM_CHECKED)
 LIB_CHECKED = os.path.join(HERE, "libhram_checked.so")

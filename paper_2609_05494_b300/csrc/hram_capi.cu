@@ -9,6 +9,7 @@
 #include "hram_device.cuh"
 #include "hram_tangent.cuh"
 #include "hram_adjoint.cuh"
+#include "hram_persist.h"
 #include "hram.h"
 
 #include <cmath>
@@ -436,6 +437,15 @@ struct hr_batch {
     int nblocks[10] = {};
     int closure = 0;  // shared by every case of the batch
     long long steps = 0;
+    // the persistent form (hr_batch_create_persistent): one launch, each case
+    // on its own fixed blocks, per-case barriers with bounded waits
+    bool persistent = false;
+    int2 *blk = nullptr;        // per block: (case, rank in the case)
+    int *case_nblk = nullptr;   // per case: blocks
+    int *bar = nullptr;         // per case: barrier counter and generation
+    int *err = nullptr;         // set by a wait that ran past spin_limit
+    int nblk_total = 0;
+    long long spin_limit = 0;
 };
 
 namespace {
@@ -2072,8 +2082,144 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     return HR_OK;
 }
 
+int hr_persist_capacity(int closure, int32_t *max_blocks)
+{
+    if (!max_blocks || closure < 0 || closure > 1) return HR_EINVAL;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *max_blocks = persist_blocks_per_sm(closure) * sms;
+    return *max_blocks > 0 ? HR_OK : HR_ECUDA;
+}
+
+int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
+                               const int32_t *case_blocks, int64_t spin_limit, void *cuda_stream,
+                               hr_batch **out)
+{
+    if (!out || !cases || n_cases <= 0 || !(t_end > 0.0)) return HR_EINVAL;
+    *out = nullptr;
+    hr_batch *b = new hr_batch();
+    auto fail = [&](int code) {
+        hr_batch_destroy(b);
+        return code;
+    };
+    for (int k = 0; k < n_cases; ++k) {
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent ||
+            cases[k]->K.closure != cases[0]->K.closure)
+            return fail(HR_EINVAL);
+        b->cases.push_back(cases[k]);
+    }
+    b->stream = (cudaStream_t)cuda_stream;
+    b->closure = cases[0]->K.closure;
+    b->persistent = true;
+    b->spin_limit = spin_limit > 0 ? spin_limit : (1LL << 24);
+    int32_t cap = 0;
+    int rc = hr_persist_capacity(b->closure, &cap);
+    if (rc != HR_OK) return fail(rc);
+    // blocks per case: as given, else in proportion to the particle counts
+    std::vector<int> nb(n_cases);
+    if (case_blocks) {
+        for (int k = 0; k < n_cases; ++k) nb[k] = case_blocks[k];
+    } else {
+        long long tot = 0;
+        for (hr_case *c : b->cases) tot += c->nf;
+        for (int k = 0; k < n_cases; ++k)
+            nb[k] = std::max(1, (int)((double)cap * (double)cases[k]->nf / (double)tot));
+    }
+    long long total = 0;
+    for (int k = 0; k < n_cases; ++k) {
+        if (nb[k] < 1) return fail(HR_EINVAL);
+        total += nb[k];
+    }
+    if (total > cap) return fail(HR_EINVAL);   // every block must stay resident
+    b->nblk_total = (int)total;
+    std::vector<int2> blk;
+    for (int k = 0; k < n_cases; ++k)
+        for (int r = 0; r < nb[k]; ++r) blk.push_back(make_int2(k, r));
+    const size_t bytes = align256(sizeof(Consts) * n_cases) + align256(sizeof(Bufs) * n_cases) +
+                         align256(blk.size() * sizeof(int2)) + align256(n_cases * 4) +
+                         align256(n_cases * 8) + 256 + 256;
+    if (cudaMalloc(&b->mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b->mem = nullptr;
+        return fail(HR_ENOMEM);
+    }
+    size_t off = 0;
+    b->dK = at<Consts>(b->mem, off);
+    off += align256(sizeof(Consts) * n_cases);
+    b->dB = at<Bufs>(b->mem, off);
+    off += align256(sizeof(Bufs) * n_cases);
+    b->blk = at<int2>(b->mem, off);
+    off += align256(blk.size() * sizeof(int2));
+    b->case_nblk = at<int>(b->mem, off);
+    off += align256(n_cases * 4);
+    b->bar = at<int>(b->mem, off);
+    off += align256(n_cases * 8);
+    b->err = at<int>(b->mem, off);
+    off += 256;
+    b->d_count = at<int>(b->mem, off);
+    std::vector<Consts> hk(n_cases);
+    std::vector<Bufs> hb(n_cases);
+    for (int k = 0; k < n_cases; ++k) {
+        hk[k] = cases[k]->K;
+        hk[k].n_probes = cases[k]->K.n_probes;
+        hb[k] = cases[k]->B;
+    }
+    if (cudaMemcpy(b->dK, hk.data(), sizeof(Consts) * n_cases, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->dB, hb.data(), sizeof(Bufs) * n_cases, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->case_nblk, nb.data(), n_cases * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->bar, 0, n_cases * 8) != cudaSuccess || cudaMemset(b->err, 0, 4) != cudaSuccess)
+        return fail(HR_ECUDA);
+    for (int k = 0; k < n_cases; ++k) {
+        hr_case *c = cases[k];
+        if (device_status(c) < 0) return fail(c->sticky);
+        Scalars S;
+        if (cudaMemcpy(&S, c->B.S, sizeof S, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(HR_ECUDA);
+        S.t_end = t_end;
+        S.done = S.t >= t_end ? 1 : 0;
+        if (cudaMemcpy(c->B.S, &S, sizeof S, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(HR_ECUDA);
+    }
+    *out = b;
+    return HR_OK;
+}
+
+// One persistent launch of up to max_steps steps of every case (<= 0: until
+// every case is done).  A wait that ran past the spin limit leaves the cases
+// mid-step: they are marked HR_ETIMEOUT.
+static int persist_run(hr_batch *b, int64_t max_steps)
+{
+    for (hr_case *c : b->cases)
+        if (c->sticky < 0) return c->sticky;
+    if (cudaMemsetAsync(b->err, 0, 4, b->stream) != cudaSuccess) return HR_ECUDA;
+    if (persist_launch(b->dK, b->dB, b->blk, b->case_nblk, b->nblk_total, b->bar, b->spin_limit,
+                       max_steps > 0 ? max_steps : (1LL << 60), b->err, b->closure, b->stream) != 0) {
+        cudaGetLastError();
+        return HR_ECUDA;
+    }
+    int err = 0;
+    if (cudaMemcpyAsync(&err, b->err, 4, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return HR_ECUDA;
+    if (err) {
+        for (hr_case *c : b->cases) c->sticky = HR_ETIMEOUT;
+        return HR_ETIMEOUT;
+    }
+    return HR_OK;
+}
+
 int hr_batch_step(hr_batch *b)
 {
+    if (b && b->persistent) {
+        const int rc = persist_run(b, 1);
+        if (rc == HR_OK) b->steps++;
+        return rc;
+    }
     if (!b || !b->exec) return HR_EINVAL;
     if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return HR_ECUDA;
     b->steps++;
@@ -2097,6 +2243,31 @@ int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done)
     const int n = (int)b->cases.size();
     int64_t done_steps = 0;
     int rc = HR_OK;
+    if (b->persistent) {
+        // the launch runs every case to its stop time (or max_steps steps)
+        std::vector<long long> before(n);
+        for (int k = 0; k < n; ++k) {
+            Scalars S;
+            CK(cudaMemcpy(&S, b->cases[k]->B.S, sizeof S, cudaMemcpyDeviceToHost));
+            before[k] = S.step;
+        }
+        rc = persist_run(b, max_steps);
+        if (rc != HR_OK) return rc;
+        for (int k = 0; k < n; ++k) {
+            Scalars S;
+            CK(cudaMemcpy(&S, b->cases[k]->B.S, sizeof S, cudaMemcpyDeviceToHost));
+            done_steps = std::max<int64_t>(done_steps, S.step - before[k]);
+        }
+        b->steps += done_steps;
+        if (steps_done) *steps_done = done_steps;
+        int worst = HR_OK;
+        for (hr_case *c : b->cases) {
+            const int st = device_status(c);
+            if (st < 0) return st;
+            worst |= st;
+        }
+        return worst;
+    }
     for (;;) {
         int nd = 0;
         if ((rc = hr_batch_done(b, &nd)) != HR_OK) break;
@@ -2164,6 +2335,7 @@ const char *hr_status_str(int s)
     case HR_ERANGE: return "buffer too small";
     case HR_EIO: return "checkpoint file error";
     case HR_ECHECK: return "an index check of the bounds-checked build failed";
+    case HR_ETIMEOUT: return "a bounded device wait gave up (persistent batch)";
     default: break;
     }
     if (s > 0) return "warning (see HR_W* bits)";

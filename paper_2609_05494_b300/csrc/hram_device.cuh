@@ -26,6 +26,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Loads of the arrays a step rewrites (sorted positions, velocities, EOS
+// records, the provisional permutation).  Kernels that see each array's
+// values of one step only read them through the read-only data path; the
+// persistent batched kernel, which runs many steps in one launch, defines
+// this as a plain load before including the header.
+#ifndef HR_DYNAMIC_LOAD
+#define HR_DYNAMIC_LOAD(p) __ldg(p)
+#endif
+
 namespace hr {
 
 constexpr int kMaxProbes = 16;
@@ -818,7 +827,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     }
     int rank = 0;
 #pragma unroll 4
-    for (int k = cs; k < ce; ++k) rank += __ldg(&B.perm_tmp[k]) < id;
+    for (int k = cs; k < ce; ++k) rank += HR_DYNAMIC_LOAD(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
     if (kChecked && !hr_ok(dst < ce, &B.S->status)) return;
     B.s_pos[dst] = up;
@@ -852,7 +861,7 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
         unsigned sub = 0u;
 #pragma unroll
         for (int u = 0; u < kMaskChunk; ++u)
-            sub |= (unsigned)in_support2(ri, __ldg(pp + k0 + u), s2) << u;
+            sub |= (unsigned)in_support2(ri, HR_DYNAMIC_LOAD(pp + k0 + u), s2) << u;
         const int rem = cnt - k0;
         if (rem < kMaskChunk) sub &= (1u << rem) - 1u;
         m |= sub << k0;
@@ -900,7 +909,7 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
                 while (m) {
                     const int j = base + __ffs(m) - 1;
                     m &= m - 1u;
-                    const float2 rj = __ldg(&B.s_pos[j]);
+                    const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
                     S = fmaf(K.m_over_rho0, w_at(rj.x, rj.y), S);
                 }
             }
@@ -959,12 +968,12 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
                 const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
                 if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
                 for (int j = a + lane; j < b; j += 32) {
-                    const float2 rj = __ldg(&B.s_pos[j]);
+                    const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
                     if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
                     const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
                     const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy2 * dy2)));
-                    const float4 aux = __ldg(&B.s_aux[j]);
-                    const float2 vj = __ldg(&B.s_vel[j]);
+                    const float4 aux = HR_DYNAMIC_LOAD(&B.s_aux[j]);
+                    const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
                     const float rw = (1.0f + aux.x) * W;
                     SW += W;
                     Sp = fmaf(aux.y, W, Sp);
@@ -1100,9 +1109,9 @@ __device__ __forceinline__ void pass_fluid(const Consts &K, const Bufs &B, int i
                                            int c, const Self &I, Acc &A)
 {
     auto fluid_pair = [&](int j) {
-        const float2 rj = __ldg(&B.s_pos[j]);
-        const float2 vj = __ldg(&B.s_vel[j]);
-        const float4 aj = __ldg(&B.s_aux[j]);
+        const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
+        const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
+        const float4 aj = HR_DYNAMIC_LOAD(&B.s_aux[j]);
         pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
                        CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
     };
@@ -1549,6 +1558,10 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
 
 // ------------------------------------------------ kernels (one case)
 
+// (A translation unit that only needs the stage bodies defines
+// HR_NO_STEP_KERNELS, so the kernels below are defined in one unit only.)
+#ifndef HR_NO_STEP_KERNELS
+
 __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
 {
     b_drift_key(K, B, blockIdx.x, gridDim.x, prime);
@@ -1709,5 +1722,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) kb_finalize(const Consts *Ks
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
     b_finalize<CL>(K, B, m.local, m.nlocal, 0);
 }
+
+#endif  // HR_NO_STEP_KERNELS
 
 }  // namespace hr

@@ -138,3 +138,109 @@ def test_autotuned_sweep_runs_and_matches_alone():
     for a, g in zip(alone, cs):
         assert np.array_equal(a.probe_pressure(), g.probe_pressure())
         assert np.array_equal(a.get_state()["xy"], g.get_state()["xy"])
+
+
+# ------------------------------------------------------ persistent batches
+
+def test_persistent_batch_equals_cases_run_alone():
+    # the whole sweep in one persistent launch, each case on its own blocks
+    # with its own barriers: every case ends bit for bit as run alone
+    t_end = 12e-6
+    specs = sweep_cases(6)
+    alone, batched = [], []
+    for p, xy in specs:
+        a = Case(p, xy)
+        a.run(0, t_end)
+        alone.append(a)
+        batched.append(Case(p, xy))
+    with Batch(batched, t_end, persistent=True) as b:
+        b.run()
+        assert b.n_done() == len(batched)
+    for a, g in zip(alone, batched):
+        sa, sg = a.get_state(), g.get_state()
+        for k in sa:
+            assert np.array_equal(sa[k], sg[k]), k
+        assert np.array_equal(a.probe_pressure(), g.probe_pressure())
+        assert a.scalars()["step"] == g.scalars()["step"]
+        assert g.scalars()["t"] >= t_end
+
+
+def test_persistent_batch_uneven_blocks_and_steps():
+    # uneven block counts (one block, several) and one step at a time give
+    # the same results as the lone runs
+    specs = sweep_cases(3)
+    cap = Batch.capacity(0)
+    blocks = [1, 3, min(7, cap - 4)]
+    ref = []
+    for p, xy in specs:
+        a = Case(p, xy)
+        a.run(5)
+        ref.append(a)
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 1.0, persistent=True, case_blocks=blocks) as b:
+        for _ in range(5):
+            b.step()
+    for a, g in zip(ref, cs):
+        assert np.array_equal(a.get_state()["xy"], g.get_state()["xy"])
+        assert np.array_equal(a.get_state()["rho"], g.get_state()["rho"])
+
+
+def test_persistent_batch_paper_closure():
+    specs = []
+    for k, a in enumerate((0.01, 0.06)):
+        p, xy = impact_case(dict(casegen.config_parity(), closure=1, c0=1448.0, alpha=a,
+                                 cfl=0.25, motion=1))
+        specs.append((p, xy))
+    alone = []
+    for p, xy in specs:
+        c = Case(p, xy)
+        c.run(0, 8e-6)
+        alone.append(c)
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 8e-6, persistent=True) as b:
+        b.run()
+    for a, g in zip(alone, cs):
+        assert np.array_equal(a.probe_pressure(), g.probe_pressure())
+        assert np.array_equal(a.get_state()["rho"], g.get_state()["rho"])
+
+
+def test_persistent_barrier_wait_gives_up_with_timeout_status():
+    # a spin limit of one poll: a block that reaches a barrier before the
+    # rest of its case's blocks gives up at once; the launch still ends, the
+    # batch reports HR_ETIMEOUT, the cases carry it, and the device goes on
+    from paper_2609_05494_b300 import HramError, _lib
+    specs = sweep_cases(4)
+    cs = [Case(p, xy) for p, xy in specs]
+    with Batch(cs, 20e-6, persistent=True, case_blocks=[4, 4, 4, 4], spin_limit=1) as b:
+        with pytest.raises(HramError) as e:
+            b.run()
+        assert e.value.code == _lib.HR_ETIMEOUT
+    with pytest.raises(HramError) as e:
+        cs[0].sync()
+    assert e.value.code == _lib.HR_ETIMEOUT
+    p, xy = specs[0]
+    with Case(p, xy) as fresh:
+        assert fresh.run(3) >= 0
+
+
+def test_persistent_batch_refusals():
+    from paper_2609_05494_b300 import HramError
+    specs = sweep_cases(2)
+    cs = [Case(p, xy) for p, xy in specs]
+    cap = Batch.capacity(0)
+    with pytest.raises(HramError):
+        Batch(cs, 1e-5, persistent=True, case_blocks=[cap, 1])   # more than stay resident
+    with pytest.raises(HramError):
+        Batch(cs, 1e-5, persistent=True, case_blocks=[0, 1])
+    q, x = impact_case(dict(specs[0][0], closure=1, c0=1448.0))
+    with Case(q, x) as other:
+        with pytest.raises(HramError):
+            Batch([cs[0], other], 1e-5, persistent=True)
+
+
+def test_persistent_autotuner_block_counts():
+    specs = sweep_cases(4)
+    blocks, report = autotune.tune_persistent(specs, 1e-5, horizon=4e-6)
+    assert len(blocks) == 4 and blocks.min() >= 1
+    assert blocks.sum() <= report["capacity"]
+    assert len(report["candidates"]) == len(autotune.BLOCK_WEIGHTS)
