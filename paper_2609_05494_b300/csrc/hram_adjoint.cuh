@@ -40,6 +40,10 @@ constexpr int kOut = 2;          // adjoint components: 0 peak probe-0 pressure,
 constexpr int kAThreads = 128;   // per-particle adjoint kernels
 constexpr int kAGhostWarps = 4;  // ghost adjoint: one warp per ghost
 constexpr int kACloseThreads = 256;
+#ifndef HR_APASS_MIN_BLOCKS
+#define HR_APASS_MIN_BLOCKS 8
+#endif
+constexpr int kAPassMinBlocks = HR_APASS_MIN_BLOCKS;   // resident ka_pass blocks per SM
 
 // One step's forward record.  s_* and st_* are in the step's cell order;
 // cell_start, gd_pos, g_* belong to the step; S is the scalars after the step.
@@ -603,7 +607,7 @@ __device__ __forceinline__ void shepard_share(const Consts &K, const ABufs &A, i
 // weights), and its share of the ghosts' Shepard sums.  The totals: the
 // adjoint of r' (end-of-step position plus pass input), of vh and of the
 // EOS record.
-__global__ void __launch_bounds__(kAThreads) ka_pass(Consts K, Bufs B, ABufs A, int prime)
+__global__ void __launch_bounds__(kAThreads, kAPassMinBlocks) ka_pass(Consts K, Bufs B, ABufs A, int prime)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K.nf) return;
@@ -843,50 +847,52 @@ __global__ void __launch_bounds__(kAThreads) ka_back(Consts K, Bufs Bc, Bufs Bp,
 }
 
 // Closes the step's reverse sweep (one block): sums the block and ghost
-// partials in a fixed order (FP64), transposes the disk kinematics at t^{n+1}
-// (x_c, v_w, a_w as functions of t and tau, from the tangent's FP64 duals),
-// carries the adjoint of t (t^{n+1} = t^n + dt) and adds the wall impulse's
-// direct dependence on dt (F_wall of the step).
+// partials in a fixed order -- compensated FP32 (two-float) per thread, FP64
+// from the warp sums up (the B300's FP64 pipe is far too slow for the
+// per-block loop) -- transposes the disk kinematics at t^{n+1} (x_c, v_w,
+// a_w as functions of t and tau, from the tangent's FP64 duals), carries the
+// adjoint of t (t^{n+1} = t^n + dt) and adds the wall impulse's direct
+// dependence on dt (F_wall of the step).
 __global__ void __launch_bounds__(kACloseThreads) ka_close(Consts K, Bufs B, ABufs A, int prime,
                                                            int n_ep, int n_bk)
 {
     __shared__ double red[kACloseThreads / 32][kOut][6];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double s[kOut][6];
+    // 0 alpha, 1 c0, 2 dt, 3 x_c, 4 v_w, 5 a_w
+    F2 s[kOut][6];
 #pragma unroll
     for (int c = 0; c < kOut; ++c)
 #pragma unroll
-        for (int e = 0; e < 6; ++e) s[c][e] = 0.0;
-    // 0 alpha, 1 c0, 2 dt, 3 x_c, 4 v_w, 5 a_w
+        for (int e = 0; e < 6; ++e) s[c][e] = F2{0.0f, 0.0f};
     for (int b = threadIdx.x; b < n_ep; b += blockDim.x)
 #pragma unroll
-        for (int c = 0; c < kOut; ++c) s[c][2] += (double)A.ep_part[b * kOut + c];
+        for (int c = 0; c < kOut; ++c) s[c][2] = f2_add(s[c][2], F2{A.ep_part[b * kOut + c], 0.0f});
     for (int b = threadIdx.x; b < n_bk; b += blockDim.x)
 #pragma unroll
         for (int c = 0; c < kOut; ++c) {
             const float4 v = A.bk_part[b * kOut + c];
-            s[c][0] += (double)v.x;
-            s[c][1] += (double)v.y;
-            s[c][2] += (double)v.z;
+            s[c][0] = f2_add(s[c][0], F2{v.x, 0.0f});
+            s[c][1] = f2_add(s[c][1], F2{v.y, 0.0f});
+            s[c][2] = f2_add(s[c][2], F2{v.z, 0.0f});
         }
     for (int g = threadIdx.x; g < K.nw + K.ng; g += blockDim.x)
 #pragma unroll
         for (int c = 0; c < kOut; ++c) {
             const float4 v = A.gpar[g * kOut + c];
-            s[c][0] += (double)v.x;
-            s[c][1] += (double)v.y;
+            s[c][0] = f2_add(s[c][0], F2{v.x, 0.0f});
+            s[c][1] = f2_add(s[c][1], F2{v.y, 0.0f});
             if (g >= K.nw) {
-                s[c][3] += (double)A.grg[g * kOut + c].x;
-                s[c][4] += (double)v.z;
-                s[c][5] += (double)v.w;
+                s[c][3] = f2_add(s[c][3], F2{A.grg[g * kOut + c].x, 0.0f});
+                s[c][4] = f2_add(s[c][4], F2{v.z, 0.0f});
+                s[c][5] = f2_add(s[c][5], F2{v.w, 0.0f});
             }
         }
 #pragma unroll
     for (int c = 0; c < kOut; ++c)
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
-            const double v = lane_sum(s[c][e]);
-            if (lane == 0) red[w][c][e] = v;
+            const F2 v = f2_warp_sum(s[c][e]);
+            if (lane == 0) red[w][c][e] = (double)v.hi + (double)v.lo;
         }
     __syncthreads();
     if (threadIdx.x != 0) return;

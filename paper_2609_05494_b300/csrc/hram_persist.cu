@@ -73,43 +73,47 @@ __device__ __forceinline__ bool case_barrier(int *cnt, int *gen, int nb, long lo
     return *flag != 0;
 }
 
-// Cell starts of the whole case by one block (exclusive scan of the counts,
-// cells in chunks of kPersistThreads x 4), the counts and tile sums reset
-// for the next step.  The same integers as the tiled scan of b_scan_apply.
-__device__ __forceinline__ void scan_case(const Consts &K, const Bufs &B)
+// Cell starts of scan tile bx (kScanTile cells) by one 256-thread block:
+// the sums of the tiles before it (counted by the drift) plus an exclusive
+// scan of its own cells, which it resets for the next step.  The same
+// integers as b_scan_apply (a 1,024-thread block per tile).
+__device__ __forceinline__ void scan_tile(const Consts &K, const Bufs &B, int bx)
 {
+    constexpr int kItems = kScanTile / kPersistThreads;
     __shared__ int wsum[kPersistThreads / 32];
-    __shared__ int carry;
-    constexpr int kItems = 4, kChunk = kPersistThreads * kItems;
-    const int n = K.ncell + 1;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int offset;
+    int o = 0;
+    for (int t = threadIdx.x; t < bx; t += blockDim.x) o += B.tile_sum[t];
+    o = warp_sum(o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = o;
     __syncthreads();
-    for (int base0 = 0; base0 < n; base0 += kChunk) {
-        const int base = base0 + threadIdx.x * kItems;
-        int v[kItems];
-        int s = 0;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            v[k] = base + k < n ? B.cell_count[base + k] : 0;
-            s += v[k];
-        }
-        int total;
-        int ex = block_exclusive_scan(s, wsum, &total) + carry;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            if (base + k < n) {
-                B.cell_start[base + k] = ex;
-                B.cell_count[base + k] = 0;
-            }
-            ex += v[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry += total;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < kPersistThreads / 32; ++k) t += wsum[k];
+        offset = t;
     }
-    if (threadIdx.x == 0) B.cell_start[n] = K.nf;
-    const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
+    __syncthreads();
+    const int n = K.ncell + 1;
+    const int base = bx * kScanTile + threadIdx.x * kItems;
+    int v[kItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, wsum, &total) + offset;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (base + k < n) {
+            B.cell_start[base + k] = ex;
+            B.cell_count[base + k] = 0;
+        }
+        ex += v[k];
+    }
+    if (base <= n && n < base + kItems) B.cell_start[n] = K.nf;
+    __syncthreads();
 }
 
 // Two 128-particle pass blocks (pass block indices 2 q and 2 q + 1) in one
@@ -200,7 +204,8 @@ __global__ void __launch_bounds__(kPersistThreads) kp_batch(const Consts *Ks, co
         if (r == 0) b_kinematics(K, B, 0, 1, 0);
         for (int vb = r; vb < n256; vb += nb) b_drift_key(K, B, vb, n256, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
-        if (r == 0) scan_case(K, B);
+        const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
+        for (int vb = r; vb < n_tiles; vb += nb) scan_tile(K, B, vb);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
         for (int vb = r; vb < n256; vb += nb) b_slot(K, B, vb, n256);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
