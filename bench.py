@@ -36,8 +36,11 @@ METRIC = "particle-steps/s at 1M particles"
 UNIT = "particle-steps/s"
 DX = 2e-4
 ALG_BYTES_PER_PARTICLE = 40      # {x, y, vx, vy, rho} read and written once
-FLOP_PER_PAIR = 58               # pair terms of the interaction pass
-FLOP_PER_CANDIDATE = 6           # float predicate of one candidate
+# algorithmic FP32 work of the interaction pass per particle-step: about 20
+# interacting neighbours x ~70 flop of pair terms plus ~61 candidates x ~6
+# flop of the support predicate (FMA counted as 2)
+FLOP_PER_PARTICLE = 1700
+FLOP_PER_PAIR = 58               # the pair terms alone, as the pass forms them
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_pass_channel300x150_dx0.2mm_traffic.txt")
 
 
@@ -603,6 +606,41 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_only(args):
+    """One leg alone (for profiling): the reverse mode or the tangent mode on
+    the channel at --dx for --steps steps (fixed dt), or the 64-case sweep."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    if args.only == "sweep":
+        out = sweep_benchmark(stream)
+    else:
+        from paper_2609_05494_b300 import Case
+        p, xy = workload(args.dx)
+        p["dt_mode"] = 1
+        with torch.cuda.stream(stream):
+            c = Case(p, xy, stream=stream, probe_capacity=args.steps + 8,
+                     tangent=args.only == "tangent")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        if args.only == "adjoint":
+            y = c.adjoint_forward(args.steps, 20)
+            g = c.adjoint_backward()
+            res = {"peak": y["peak"], "impulse": y["impulse"], "dpeak": g["dpeak"].tolist(),
+                   "dimpulse": g["dimpulse"].tolist()}
+        else:
+            c.run(args.steps)
+            res = {k: (v.tolist() if hasattr(v, "tolist") else v)
+                   for k, v in c.tangent_outputs().items()}
+        b.record(stream)
+        torch.cuda.synchronize()
+        out = {"leg": args.only, "particles": int(xy.shape[0]), "steps": args.steps,
+               "ms_per_step": a.elapsed_time(b) / args.steps, "result": res}
+        c.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,6 +655,9 @@ def main():
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-scaling", action="store_true")
     ap.add_argument("--no-production", action="store_true")
+    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep"),
+                    help="run one leg alone on the channel at --dx for --steps steps "
+                         "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -626,6 +667,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only:
+        return run_only(args)
 
     import torch
     dist = None
@@ -731,7 +774,7 @@ def main():
     pk, src = peaks()
     value = aggregate_value(world, n, args.steps, total_ms)
     t_pass = statistics.mean(pass_ms) * 1e-3
-    flops = pairs_fluid_rows * FLOP_PER_PAIR
+    flops = n * FLOP_PER_PARTICLE
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     alu_peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0), n_sm)
     achieved_tf = flops / t_pass / 1e12
@@ -754,7 +797,11 @@ def main():
                      "traffic": traffic,
                      "peak_source": "FP32 from unit counts: %d SM (as the device reports) x "
                                     "128 lanes x 2 x %.0f MHz" % (n_sm, pk.get("sm_max_mhz", 2032.0)),
-                     "flop_per_launch": flops, "pass_ms": t_pass * 1e3},
+                     "flop_per_launch": flops, "flop_per_particle": FLOP_PER_PARTICLE,
+                     "pair_terms_only": {"pairs": pairs_fluid_rows,
+                                         "flop_per_pair": FLOP_PER_PAIR,
+                                         "tflops": pairs_fluid_rows * FLOP_PER_PAIR / t_pass / 1e12},
+                     "pass_ms": t_pass * 1e3},
         "roofline_hbm": {"kernel": "k_pass", "bound": "hbm", "achieved": hbm_achieved,
                          "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": hbm_achieved / pk["hbm_gbs"],

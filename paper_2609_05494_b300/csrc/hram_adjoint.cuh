@@ -39,11 +39,10 @@ namespace hr {
 constexpr int kOut = 2;          // adjoint components: 0 peak probe-0 pressure, 1 wall impulse
 constexpr int kAThreads = 128;   // per-particle adjoint kernels
 constexpr int kAGhostWarps = 4;  // ghost adjoint: one warp per ghost
-constexpr int kACloseThreads = 256;
-#ifndef HR_APASS_MIN_BLOCKS
-#define HR_APASS_MIN_BLOCKS 8
-#endif
-constexpr int kAPassMinBlocks = HR_APASS_MIN_BLOCKS;   // resident ka_pass blocks per SM
+// resident ka_pass blocks per SM: 6 (80 registers, no spills) measured best
+// against 7 and 8 (spills) and against two neighbours per loop iteration at
+// 4 and 5 (109 and 96 registers): 0.823 against 0.825-0.980 ms per step
+constexpr int kAPassMinBlocks = 6;
 
 // One step's forward record.  s_* and st_* are in the step's cell order;
 // cell_start, gd_pos, g_* belong to the step; S is the scalars after the step.
@@ -91,6 +90,7 @@ struct ABufs {
     float2 *grg;             // disk ghost position adjoints
     float *ep_part;          // per epilogue block: dt partial [kOut]
     float4 *bk_part;         // per back block: {alpha, c0, dt, 0} [kOut]
+    float2 *sums;            // ka_reduce's block sums (two-float) [kAReduceBlocks x kASums]
     double *sc;              // ASC_* accumulators
     int *status;             // the case's status word (bounds-checked build)
 };
@@ -636,17 +636,12 @@ __global__ void __launch_bounds__(kAThreads, kAPassMinBlocks) ka_pass(Consts K, 
             for (int base = a; base < b; base += 32) {
                 unsigned m = support_mask(B.s_pos, base, min(32, b - base), rk, K.s2);
                 if (k >= base && k < base + 32) m &= ~(1u << (k - base));
-#pragma unroll 1
-                while (m) {
-                    const int j = base + __ffs(m) - 1;
-                    m &= m - 1u;
-                    const float2 rj = B.s_pos[j], vj = B.s_vel[j];
-                    const float4 aj = B.s_aux[j];
+                // the pair adjoint of neighbour j (its data loaded by the caller)
+                auto fluid_adj = [&](float2 rj, float2 vj, float4 aj, float4 wAj, float4 wXj,
+                                     float2 wDj) {
                     PairFwd q;
                     pair_fwd(K, rk, vk, rhok, ak.z, ak.w, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
                              aj.w, 1.0f, true, q);
-                    const float4 wAj = A.wA[j], wXj = A.wX[j];
-                    const float2 wDj = A.wDr[j];
 #pragma unroll
                     for (int c = 0; c < kOut; ++c) {
                         const PairAdj p =
@@ -662,6 +657,12 @@ __global__ void __launch_bounds__(kAThreads, kAPassMinBlocks) ka_pass(Consts K, 
                         grec[c].y += p.gQ;
                         grec[c].z += p.gC;
                     }
+                };
+#pragma unroll 1
+                while (m) {
+                    const int j = base + __ffs(m) - 1;
+                    m &= m - 1u;
+                    fluid_adj(B.s_pos[j], B.s_vel[j], B.s_aux[j], A.wA[j], A.wX[j], A.wDr[j]);
                 }
             }
         }
@@ -846,63 +847,94 @@ __global__ void __launch_bounds__(kAThreads) ka_back(Consts K, Bufs Bc, Bufs Bp,
     }
 }
 
-// Closes the step's reverse sweep (one block): sums the block and ghost
-// partials in a fixed order -- compensated FP32 (two-float) per thread, FP64
-// from the warp sums up (the B300's FP64 pipe is far too slow for the
-// per-block loop) -- transposes the disk kinematics at t^{n+1} (x_c, v_w,
-// a_w as functions of t and tau, from the tangent's FP64 duals), carries the
-// adjoint of t (t^{n+1} = t^n + dt) and adds the wall impulse's direct
-// dependence on dt (F_wall of the step).
-__global__ void __launch_bounds__(kACloseThreads) ka_close(Consts K, Bufs B, ABufs A, int prime,
-                                                           int n_ep, int n_bk)
+// Partial sums of the step's block and ghost partials (the parameters' and
+// dt's adjoints, and the disk ghosts' x_c, v_w, a_w adjoints): block r of
+// kAReduceBlocks sums slice r of each array in compensated FP32 (two-float)
+// and writes its 12 sums; ka_close adds the blocks' sums in block order.
+constexpr int kAReduceBlocks = 128;
+constexpr int kAReduceThreads = 256;
+constexpr int kASums = kOut * 6;   // per component: alpha, c0, dt, x_c, v_w, a_w
+
+__device__ __forceinline__ void slice_of(int n, int r, int &lo, int &hi)
 {
-    __shared__ double red[kACloseThreads / 32][kOut][6];
+    const int per = (n + kAReduceBlocks - 1) / kAReduceBlocks;
+    lo = min(n, r * per);
+    hi = min(n, lo + per);
+}
+
+__global__ void __launch_bounds__(kAReduceThreads) ka_reduce(Consts K, ABufs A, int n_ep, int n_bk,
+                                                            float2 *out)
+{
+    __shared__ F2 red[kAReduceThreads / 32][kASums];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // 0 alpha, 1 c0, 2 dt, 3 x_c, 4 v_w, 5 a_w
-    F2 s[kOut][6];
+    F2 s[kASums];
 #pragma unroll
-    for (int c = 0; c < kOut; ++c)
+    for (int e = 0; e < kASums; ++e) s[e] = F2{0.0f, 0.0f};
+    int lo, hi;
+    slice_of(n_ep, blockIdx.x, lo, hi);
+    for (int b = lo + threadIdx.x; b < hi; b += blockDim.x)
 #pragma unroll
-        for (int e = 0; e < 6; ++e) s[c][e] = F2{0.0f, 0.0f};
-    for (int b = threadIdx.x; b < n_ep; b += blockDim.x)
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) s[c][2] = f2_add(s[c][2], F2{A.ep_part[b * kOut + c], 0.0f});
-    for (int b = threadIdx.x; b < n_bk; b += blockDim.x)
+        for (int c = 0; c < kOut; ++c) s[c * 6 + 2] = f2_add(s[c * 6 + 2], F2{A.ep_part[b * kOut + c], 0.0f});
+    slice_of(n_bk, blockIdx.x, lo, hi);
+    for (int b = lo + threadIdx.x; b < hi; b += blockDim.x)
 #pragma unroll
         for (int c = 0; c < kOut; ++c) {
             const float4 v = A.bk_part[b * kOut + c];
-            s[c][0] = f2_add(s[c][0], F2{v.x, 0.0f});
-            s[c][1] = f2_add(s[c][1], F2{v.y, 0.0f});
-            s[c][2] = f2_add(s[c][2], F2{v.z, 0.0f});
+            s[c * 6 + 0] = f2_add(s[c * 6 + 0], F2{v.x, 0.0f});
+            s[c * 6 + 1] = f2_add(s[c * 6 + 1], F2{v.y, 0.0f});
+            s[c * 6 + 2] = f2_add(s[c * 6 + 2], F2{v.z, 0.0f});
         }
-    for (int g = threadIdx.x; g < K.nw + K.ng; g += blockDim.x)
+    slice_of(K.nw + K.ng, blockIdx.x, lo, hi);
+    for (int g = lo + threadIdx.x; g < hi; g += blockDim.x)
 #pragma unroll
         for (int c = 0; c < kOut; ++c) {
             const float4 v = A.gpar[g * kOut + c];
-            s[c][0] = f2_add(s[c][0], F2{v.x, 0.0f});
-            s[c][1] = f2_add(s[c][1], F2{v.y, 0.0f});
+            s[c * 6 + 0] = f2_add(s[c * 6 + 0], F2{v.x, 0.0f});
+            s[c * 6 + 1] = f2_add(s[c * 6 + 1], F2{v.y, 0.0f});
             if (g >= K.nw) {
-                s[c][3] = f2_add(s[c][3], F2{A.grg[g * kOut + c].x, 0.0f});
-                s[c][4] = f2_add(s[c][4], F2{v.z, 0.0f});
-                s[c][5] = f2_add(s[c][5], F2{v.w, 0.0f});
+                s[c * 6 + 3] = f2_add(s[c * 6 + 3], F2{A.grg[g * kOut + c].x, 0.0f});
+                s[c * 6 + 4] = f2_add(s[c * 6 + 4], F2{v.z, 0.0f});
+                s[c * 6 + 5] = f2_add(s[c * 6 + 5], F2{v.w, 0.0f});
             }
         }
 #pragma unroll
-    for (int c = 0; c < kOut; ++c)
+    for (int e = 0; e < kASums; ++e) {
+        const F2 v = f2_warp_sum(s[e]);
+        if (lane == 0) red[w][e] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kASums) {
+        F2 t{0.0f, 0.0f};
+        for (int k = 0; k < kAReduceThreads / 32; ++k) t = f2_add(t, red[k][threadIdx.x]);
+        out[blockIdx.x * kASums + threadIdx.x] = make_float2(t.hi, t.lo);
+    }
+}
+
+// Closes the step's reverse sweep (one block of kAReduceBlocks threads):
+// adds the ka_reduce sums in a fixed order (thread b reads block b's sums;
+// FP64 across the block), transposes the disk kinematics at t^{n+1} (x_c,
+// v_w, a_w as functions of t and tau, from the tangent's FP64 duals),
+// carries the adjoint of t (t^{n+1} = t^n + dt) and adds the wall impulse's
+// direct dependence on dt (F_wall of the step).
+__global__ void __launch_bounds__(kAReduceBlocks) ka_close(Consts K, Bufs B, ABufs A, int prime,
+                                                          const float2 *sums)
+{
+    __shared__ double red[kAReduceBlocks / 32][kASums];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-            const F2 v = f2_warp_sum(s[c][e]);
-            if (lane == 0) red[w][c][e] = (double)v.hi + (double)v.lo;
-        }
+    for (int e = 0; e < kASums; ++e) {
+        const float2 v = sums[threadIdx.x * kASums + e];
+        const double x = lane_sum((double)v.x + (double)v.y);
+        if (lane == 0) red[w][e] = x;
+    }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    double tot[kOut][6];
-    for (int c = 0; c < kOut; ++c)
-        for (int e = 0; e < 6; ++e) {
-            double v = 0.0;
-            for (int k = 0; k < kACloseThreads / 32; ++k) v += red[k][c][e];
-            tot[c][e] = v;
-        }
+    double tot[kASums];
+    for (int e = 0; e < kASums; ++e) {
+        double v = 0.0;
+        for (int k = 0; k < kAReduceBlocks / 32; ++k) v += red[k][e];
+        tot[e] = v;
+    }
     double *sc = A.sc;
     // kinematics at this step's time (t^{n+1}; 0 for the priming pass)
     D3d t = dconst(B.S->t);
@@ -910,10 +942,11 @@ __global__ void __launch_bounds__(kACloseThreads) ka_close(Consts K, Bufs B, ABu
     D3d xk, vk, ak;
     kinematics_T(K, t, &xk, &vk, &ak);
     for (int c = 0; c < kOut; ++c) {
-        sc[ASC_ALPHA + c] += tot[c][0];
-        sc[ASC_C0 + c] += tot[c][1];
-        double dtb = tot[c][2];
-        const double xb = tot[c][3], vb = tot[c][4], ab = tot[c][5];
+        const double *q = tot + c * 6;
+        sc[ASC_ALPHA + c] += q[0];
+        sc[ASC_C0 + c] += q[1];
+        double dtb = q[2];
+        const double xb = q[3], vb = q[4], ab = q[5];
         if (K.ng > 0) sc[ASC_TAU + c] += xb * xk.d[2] + vb * vk.d[2] + ab * ak.d[2];
         if (!prime) {
             if (K.ng > 0) sc[ASC_TBAR + c] += xb * xk.d[0] + vb * vk.d[0] + ab * ak.d[0];

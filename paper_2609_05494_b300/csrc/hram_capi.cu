@@ -1055,6 +1055,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
                  grg = Lo.add(gq * 8);
     const size_t ep = Lo.add((size_t)a->ep_blocks * kOut * 4);
     const size_t bk = Lo.add((size_t)a->bk_blocks * kOut * 16);
+    const size_t sums = Lo.add((size_t)kAReduceBlocks * kASums * 8);
     const size_t sc = Lo.add(ASC_N * 8);
     a->bytes = Lo.total;
     if (cudaMalloc(&a->mem, a->bytes) != cudaSuccess) {
@@ -1117,6 +1118,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     A.grg = at<float2>(w, grg);
     A.ep_part = at<float>(w, ep);
     A.bk_part = at<float4>(w, bk);
+    A.sums = at<float2>(w, sums);
     A.sc = at<double>(w, sc);
     A.status = &c->B.S->status;
     return HR_OK;
@@ -1216,7 +1218,9 @@ int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, 
     ka_ghost<<<a->gh_blocks, kAGhostWarps * 32, 0, s>>>(K, Bc, a->A, prime);
     ka_pass<<<a->ep_blocks, kAThreads, 0, s>>>(K, Bc, a->A, prime);
     ka_back<<<a->bk_blocks, kAThreads, 0, s>>>(K, Bc, Bp, a->A, prime);
-    ka_close<<<1, kACloseThreads, 0, s>>>(K, Bc, a->A, prime, a->ep_blocks, a->bk_blocks);
+    ka_reduce<<<kAReduceBlocks, kAReduceThreads, 0, s>>>(K, a->A, a->ep_blocks, a->bk_blocks,
+                                                          a->A.sums);
+    ka_close<<<1, kAReduceBlocks, 0, s>>>(K, Bc, a->A, prime, a->A.sums);
     CK(cudaGetLastError());
     std::swap(a->A.cur, a->A.prv);
     return HR_OK;
