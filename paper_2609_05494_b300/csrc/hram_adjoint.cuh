@@ -58,6 +58,7 @@ struct Slot {
     float2 *gd_pos, *g_vel;
     float4 *g_aux;
     Scalars *S;
+    double *kin;   // dx_c, dv_w, da_w by t, then by ln tau, at the step's time (reverse mode)
 };
 
 // Adjoints of the state a step hands to the next: r, v, a, X, d, D (the
@@ -910,6 +911,24 @@ __global__ void __launch_bounds__(kAReduceThreads) ka_reduce(Consts K, ABufs A, 
     }
 }
 
+// The disk kinematics' derivatives at the time S->t (x_c, v_w, a_w by t and
+// by ln tau, FP64 duals), for the reverse sweep of the step; one thread, on
+// the recomputed step's side branch beside the drift and the sort.
+__global__ void ka_kin(Consts K, const Scalars *S, double *kin)
+{
+    if (threadIdx.x != 0) return;
+    D3d t = dconst(S->t);
+    t.d[0] = 1.0;   // direction 0: d/dt; direction 2: d/d ln tau (set by kinematics_T)
+    D3d xk, vk, ak;
+    kinematics_T(K, t, &xk, &vk, &ak);
+    kin[0] = xk.d[0];
+    kin[1] = vk.d[0];
+    kin[2] = ak.d[0];
+    kin[3] = xk.d[2];
+    kin[4] = vk.d[2];
+    kin[5] = ak.d[2];
+}
+
 // Closes the step's reverse sweep (one block of kAReduceBlocks threads):
 // adds the ka_reduce sums in a fixed order (thread b reads block b's sums;
 // FP64 across the block), transposes the disk kinematics at t^{n+1} (x_c,
@@ -917,7 +936,7 @@ __global__ void __launch_bounds__(kAReduceThreads) ka_reduce(Consts K, ABufs A, 
 // carries the adjoint of t (t^{n+1} = t^n + dt) and adds the wall impulse's
 // direct dependence on dt (F_wall of the step).
 __global__ void __launch_bounds__(kAReduceBlocks) ka_close(Consts K, Bufs B, ABufs A, int prime,
-                                                          const float2 *sums)
+                                                          const float2 *sums, const double *kin)
 {
     __shared__ double red[kAReduceBlocks / 32][kASums];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -936,20 +955,17 @@ __global__ void __launch_bounds__(kAReduceBlocks) ka_close(Consts K, Bufs B, ABu
         tot[e] = v;
     }
     double *sc = A.sc;
-    // kinematics at this step's time (t^{n+1}; 0 for the priming pass)
-    D3d t = dconst(B.S->t);
-    t.d[0] = 1.0;   // direction 0: d/dt; direction 2: d/d ln tau (set by kinematics_T)
-    D3d xk, vk, ak;
-    kinematics_T(K, t, &xk, &vk, &ak);
+    // kinematics derivatives at this step's time (t^{n+1}; 0 for the priming
+    // pass), formed by ka_kin when the step was recorded
     for (int c = 0; c < kOut; ++c) {
         const double *q = tot + c * 6;
         sc[ASC_ALPHA + c] += q[0];
         sc[ASC_C0 + c] += q[1];
         double dtb = q[2];
         const double xb = q[3], vb = q[4], ab = q[5];
-        if (K.ng > 0) sc[ASC_TAU + c] += xb * xk.d[2] + vb * vk.d[2] + ab * ak.d[2];
+        if (K.ng > 0) sc[ASC_TAU + c] += xb * kin[3] + vb * kin[4] + ab * kin[5];
         if (!prime) {
-            if (K.ng > 0) sc[ASC_TBAR + c] += xb * xk.d[0] + vb * vk.d[0] + ab * ak.d[0];
+            if (K.ng > 0) sc[ASC_TBAR + c] += xb * kin[0] + vb * kin[1] + ab * kin[2];
             dtb += sc[ASC_TBAR + c];
             if (c == 1) dtb += B.S->Fwall;   // J = sum_n dt F_wall^{n+1}
         }

@@ -997,7 +997,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     Layout Lo;
     struct SlotOff {
         size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_a, st_D, st_X, perm, cs, gd, gv,
-            ga, S;
+            ga, S, kin;
     };
     auto full = [&]() {
         SlotOff o;
@@ -1017,6 +1017,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
         o.gv = Lo.add(std::max<size_t>(ngh, 1) * 8);
         o.ga = Lo.add(std::max<size_t>(ngh, 1) * 16);
         o.S = Lo.add(sizeof(Scalars));
+        o.kin = Lo.add(6 * 8);
         return o;
     };
     auto state = [&]() {   // a checkpoint: the state a step starts from
@@ -1084,6 +1085,7 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
             sl.gd_pos = at<float2>(w, o.gd);
             sl.g_vel = at<float2>(w, o.gv);
             sl.g_aux = at<float4>(w, o.ga);
+            sl.kin = at<double>(w, o.kin);
         }
         return sl;
     };
@@ -1168,11 +1170,18 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     Br.st_rho = prev.st_rho;             // ... from the previous density and rates
     Br.st_D = prev.st_D;
     const Bufs Bc = slot_bufs(c, cur, false);
-    k_kinematics<<<1, 128, 0, s>>>(K, Bk, prime);
+    // the kinematics (and their derivatives for the reverse sweep) on a side
+    // branch beside the drift and the sort, as in the step graph
+    CK(cudaEventRecord(c->fork, s));
+    CK(cudaStreamWaitEvent(c->cap2, c->fork, 0));
+    k_kinematics<<<1, 128, 0, c->cap2>>>(K, Bk, prime);
+    ka_kin<<<1, 32, 0, c->cap2>>>(K, c->B.S, cur.kin);
+    CK(cudaEventRecord(c->join, c->cap2));
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs);
     k_slot<<<c->drift_blocks, 256, 0, s>>>(K, Bs);
     k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
+    CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);
     k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, Bc, prime);
     k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime);
@@ -1220,7 +1229,7 @@ int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, 
     ka_back<<<a->bk_blocks, kAThreads, 0, s>>>(K, Bc, Bp, a->A, prime);
     ka_reduce<<<kAReduceBlocks, kAReduceThreads, 0, s>>>(K, a->A, a->ep_blocks, a->bk_blocks,
                                                           a->A.sums);
-    ka_close<<<1, kAReduceBlocks, 0, s>>>(K, Bc, a->A, prime, a->A.sums);
+    ka_close<<<1, kAReduceBlocks, 0, s>>>(K, Bc, a->A, prime, a->A.sums, cur.kin);
     CK(cudaGetLastError());
     std::swap(a->A.cur, a->A.prv);
     return HR_OK;
