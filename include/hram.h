@@ -67,6 +67,14 @@ extern "C" {
 #define HR_FLAG_TANGENT 2 /* carry tangent-linear derivatives along the run
                             (see hr_tangent_outputs); needs dt_mode 1 and
                             motion 0-2 */
+#define HR_FLAG_STAGE_POS 4 /* interaction pass variant: a pass block whose
+                            particles lie in one cell row copies the positions
+                            of its three stencil rows to shared memory once and
+                            tests its candidates there; the results are the
+                            same bit for bit (a measured alternative, slower
+                            or no faster on a B300; single-case steps only) */
+#define HR_FLAG_STAGE_ALL 8 /* as HR_FLAG_STAGE_POS, with the velocities and
+                            EOS records staged too (at most one of the two) */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)
@@ -333,11 +341,15 @@ int hr_tangent_outputs(hr_case *c, double *out, int n);
  * checkpoint_every steps and the adjoint buffers (about
  * (48 n_steps / checkpoint_every + 84 checkpoint_every + 300) bytes per fluid
  * particle) and keeps them until the next hr_adjoint_forward or
- * hr_destroy.  Afterwards the case stands at step n_steps as after hr_run.
+ * hr_destroy.  The last segment's steps run on the records as they go
+ * (unless the case takes periodic diagnostics), so its reverse sweep needs no
+ * recomputation.  Afterwards the case stands at step n_steps as after hr_run,
+ * bit for bit.
  *
  * hr_adjoint_backward sweeps the run backwards: for each segment, last
- * first, it recomputes the segment's steps from its checkpoint and carries
- * the adjoints of the state from the end of each step to its start.  out (n
+ * first, it recomputes the segment's steps from its checkpoint (the last
+ * segment's records are already there) and carries the adjoints of the state
+ * from the end of each step to its start.  out (n
  * >= 6 doubles): [dP/d ln alpha, dP/d ln c0, dP/d ln tau, dJ/d ln alpha,
  * dJ/d ln c0, dJ/d ln tau] (theta_k d/d theta_k, as hr_tangent_outputs).  It
  * leaves the case's state as hr_adjoint_forward left it, and may be called

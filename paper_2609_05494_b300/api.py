@@ -70,12 +70,15 @@ class Case:
     params: dict of parameters (see casegen.base_params); xy: (N, 2) initial
     positions in fluid-ID order; vel (N, 2) / rho (N,) optional.  The device
     workspace is a torch uint8 tensor unless ``torch_workspace`` is False, in
-    which case the library allocates it.
+    which case the library allocates it.  ``stage`` picks the interaction
+    pass variant: 0 reads candidates from global memory, 1 stages the
+    candidates' positions in shared memory, 2 their whole records (the
+    results are identical).
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
                  probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
-                 tangent: bool = False):
+                 tangent: bool = False, stage: int = 0):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -84,6 +87,9 @@ class Case:
         self.n = n
         self.params = dict(params)
         flags = (_lib.HR_FLAG_TIMING if timing else 0) | (_lib.HR_FLAG_TANGENT if tangent else 0)
+        if stage not in (0, 1, 2):
+            raise ValueError("stage must be 0, 1 or 2")
+        flags |= (0, _lib.HR_FLAG_STAGE_POS, _lib.HR_FLAG_STAGE_ALL)[stage]
         self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)

@@ -370,6 +370,7 @@ int validate(const hr_params *P, long long nf)
     if (P->motion == 1 && !(P->drag_M > 0)) return HR_EINVAL;
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
     if (P->cell_factor < 1.0) return HR_EINVAL;
+    if ((P->flags & HR_FLAG_STAGE_POS) && (P->flags & HR_FLAG_STAGE_ALL)) return HR_EINVAL;
     // tangent mode: fixed time step (smooth in c0) and a prescribed motion
     if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
     if (P->closure < 0 || P->closure > 1) return HR_EINVAL;
@@ -417,6 +418,7 @@ struct hr_case {
     struct AdjCtx *adj = nullptr;
     // tangent mode (HR_FLAG_TANGENT)
     bool tangent = false;
+    int stage = 0;                // pass variant: 0 global loads, 1/2 staged candidates
     TBufs T{};
     int tpass_blocks = 0;
     void *t_base = nullptr;
@@ -715,6 +717,7 @@ void bind(hr_case *c, const Offsets &o)
     c->diag_cap = c->P.diag_every > 0 ? 4096 : 1;
     c->io = at<float>(w, o.io);
     c->tangent = (c->P.flags & HR_FLAG_TANGENT) != 0;
+    c->stage = (c->P.flags & HR_FLAG_STAGE_POS) ? 1 : (c->P.flags & HR_FLAG_STAGE_ALL) ? 2 : 0;
     B.s_ex = c->P.closure == 1 ? at<float4>(w, o.s_ex) : nullptr;
     B.perm_dst = nullptr;
     if (c->tangent) {
@@ -791,7 +794,11 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     }
     if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
-    if (paper) k_pass<1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    if (c->stage == 1 && paper) k_pass_staged<1, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->stage == 1) k_pass_staged<0, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->stage == 2 && paper) k_pass_staged<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->stage == 2) k_pass_staged<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (paper) k_pass<1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
@@ -960,6 +967,9 @@ struct AdjCtx {
     Slot start{};                 // the state a segment starts from (a copy of its checkpoint)
     cudaGraph_t seg_graph[2] = {nullptr, nullptr};        // one full segment, by the parity
     cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};     // of the adjoint buffers at its start
+    cudaGraph_t rev_graph[2] = {nullptr, nullptr};        // its reverse half alone (a segment
+    cudaGraphExec_t rev_exec[2] = {nullptr, nullptr};     // whose records are on the tape)
+    bool taped_last = false;      // the forward run recorded the last segment on the tape
     ABufs A{};
     LState ls[2]{};
     int ep_blocks = 0, bk_blocks = 0, gh_blocks = 0;
@@ -976,6 +986,8 @@ void adj_free(hr_case *c)
     for (int k = 0; k < 2; ++k) {
         if (c->adj->seg_exec[k]) cudaGraphExecDestroy(c->adj->seg_exec[k]);
         if (c->adj->seg_graph[k]) cudaGraphDestroy(c->adj->seg_graph[k]);
+        if (c->adj->rev_exec[k]) cudaGraphExecDestroy(c->adj->rev_exec[k]);
+        if (c->adj->rev_graph[k]) cudaGraphDestroy(c->adj->rev_graph[k]);
     }
     if (c->adj->mem) cudaFree(c->adj->mem);
     delete c->adj;
@@ -1253,12 +1265,13 @@ int load_start(hr_case *c, const Slot &k, cudaStream_t s)
 }
 
 // One segment of len steps from the start state: the records recomputed
-// forwards, then the reverse sweep through them.
-int launch_segment(hr_case *c, cudaStream_t s, long long len)
+// forwards (unless they are already on the tape), then the reverse sweep
+// through them.
+int launch_segment(hr_case *c, cudaStream_t s, long long len, bool recompute)
 {
     AdjCtx *a = c->adj;
     int rc;
-    for (long long k = 0; k < len; ++k) {
+    for (long long k = 0; recompute && k < len; ++k) {
         const Slot &prev = k == 0 ? a->start : a->tape[(size_t)(k - 1)];
         if ((rc = launch_tape_step(c, s, a->tape[(size_t)k], prev, 0)) != HR_OK) return rc;
     }
@@ -1270,15 +1283,18 @@ int launch_segment(hr_case *c, cudaStream_t s, long long len)
 }
 
 // A full segment (L steps) as one graph launch: captured once for each
-// parity of the adjoint buffers it starts from.
-int run_full_segment(hr_case *c, cudaStream_t s)
+// parity of the adjoint buffers it starts from, with and without the
+// recomputation.
+int run_full_segment(hr_case *c, cudaStream_t s, bool recompute)
 {
     AdjCtx *a = c->adj;
     const int par = a->A.cur.r == a->ls[0].r ? 0 : 1;
-    if (!a->seg_exec[par]) {
+    cudaGraph_t &graph = recompute ? a->seg_graph[par] : a->rev_graph[par];
+    cudaGraphExec_t &exec = recompute ? a->seg_exec[par] : a->rev_exec[par];
+    if (!exec) {
         const ABufs keep = a->A;
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        const int rc = launch_segment(c, c->cap, a->L);
+        const int rc = launch_segment(c, c->cap, a->L, recompute);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
         a->A = keep;
@@ -1287,11 +1303,38 @@ int run_full_segment(hr_case *c, cudaStream_t s)
             return rc;
         }
         CK(e);
-        a->seg_graph[par] = g;
-        CK(cudaGraphInstantiate(&a->seg_exec[par], g, 0));
+        graph = g;
+        CK(cudaGraphInstantiate(&exec, g, 0));
     }
-    CK(cudaGraphLaunch(a->seg_exec[par], s));
+    CK(cudaGraphLaunch(exec, s));
     if (a->L & 1) std::swap(a->A.cur, a->A.prv);
+    return HR_OK;
+}
+
+// Makes the case's own arrays hold what a plain step would have left in
+// them, from the record of the same step (the forward run's last segment
+// runs on the tape; the next plain step reads these arrays).
+int tape_to_live(hr_case *c, const Slot &sl, cudaStream_t s)
+{
+    const size_t n = (size_t)c->nf, ngh = (size_t)(c->nw + c->ng), nc = (size_t)c->K.ncell;
+    const Bufs &B = c->B;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+    };
+    CK(cp(B.s_pos, sl.s_pos, n * 8));
+    CK(cp(B.s_vel, sl.s_vel, n * 8));
+    CK(cp(B.s_aux, sl.s_aux, n * 16));
+    CK(cp(B.s_rd, sl.s_rd, n * 8));
+    CK(cp(B.s_id, sl.s_id, n * 4));
+    CK(cp(B.st_vel, sl.st_vel, n * 8));
+    CK(cp(B.st_rho, sl.st_rho, n * 4));
+    CK(cp(B.st_a, sl.st_a, n * 8));
+    CK(cp(B.st_D, sl.st_D, n * 8));
+    CK(cp(B.st_X, sl.st_X, n * 8));
+    CK(cp(B.cell_start, sl.cell_start, (nc + 2) * 4));
+    CK(cp(B.gd_pos, sl.gd_pos, (size_t)c->ng * 8));
+    CK(cp(B.g_vel, sl.g_vel, ngh * 8));
+    CK(cp(B.g_aux, sl.g_aux, ngh * 16));
     return HR_OK;
 }
 
@@ -1835,13 +1878,29 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
     ka_to_id_order<<<c->drift_blocks, 256, 0, s>>>(c->K, c->B, a->upload);
     CK(cudaGetLastError());
     if ((rc = launch_tape_step(c, s, a->prime_slot, a->upload, 1)) != HR_OK) return rc;
-    // the forward run on the case's own step graph, a checkpoint every L steps
+    // the forward run on the case's own step graph, a checkpoint every L
+    // steps; the last segment is recorded on the tape as it runs, so the
+    // reverse sweep starts without recomputing it (not with periodic
+    // diagnostics, which only the step graph takes)
+    const long long last = ((n_steps - 1) / a->L) * a->L;   // the last segment's first step
+    a->taped_last = c->P.diag_every <= 0;
+    const long long plain_end = a->taped_last ? last : n_steps;
     long long done = 0;
-    while (done < n_steps) {
-        const long long k = std::min<long long>(a->L, n_steps - done);
+    while (done < plain_end) {
+        const long long k = std::min<long long>(a->L, plain_end - done);
         if ((rc = run_steps(c, k)) != HR_OK) return rc;
         done += k;
         if (done < n_steps && (rc = save_ckpt(c, a->ckpt[done / a->L], s)) != HR_OK) return rc;
+    }
+    if (a->taped_last) {
+        const long long len = n_steps - last;
+        if ((rc = load_start(c, a->ckpt[(size_t)(last / a->L)], s)) != HR_OK) return rc;
+        for (long long k = 0; k < len; ++k) {
+            const Slot &prev = k == 0 ? a->start : a->tape[(size_t)(k - 1)];
+            if ((rc = launch_tape_step(c, s, a->tape[(size_t)k], prev, 0)) != HR_OK) return rc;
+        }
+        if ((rc = tape_to_live(c, a->tape[(size_t)(len - 1)], s)) != HR_OK) return rc;
+        c->host_step += len;
     }
     CK(cudaMemcpyAsync(a->S_final, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
     st = device_status(c);
@@ -1889,8 +1948,10 @@ int hr_adjoint_backward(hr_case *c, double *out, int n)
         const long long base = seg * L, len = std::min<long long>(N, base + L) - base;
         // the segment's records recomputed from its checkpoint, then swept
         // backwards (a full segment is one graph launch)
+        const bool recompute = !(a->taped_last && base + len == N);
+        if (recompute) a->taped_last = false;   // the tape is overwritten from here on
         if ((rc = load_start(c, a->ckpt[(size_t)seg], s)) != HR_OK) return rc;
-        rc = len == L ? run_full_segment(c, s) : launch_segment(c, s, len);
+        rc = len == L ? run_full_segment(c, s, recompute) : launch_segment(c, s, len, recompute);
         if (rc != HR_OK) return rc;
     }
     // the priming pass (a0, D0, X0 of the uploaded state)

@@ -851,6 +851,8 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
 #endif
 constexpr int kMaskChunk = HR_MASK_CHUNK;
 constexpr int kPosPad = 32;
+// (SMEM: pos is a shared-memory array, read with plain loads.)
+template <bool SMEM = false>
 __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, int cnt, float2 ri,
                                                  float s2)
 {
@@ -861,7 +863,8 @@ __device__ __forceinline__ unsigned support_mask(const float2 *pos, int base, in
         unsigned sub = 0u;
 #pragma unroll
         for (int u = 0; u < kMaskChunk; ++u)
-            sub |= (unsigned)in_support2(ri, HR_DYNAMIC_LOAD(pp + k0 + u), s2) << u;
+            sub |= (unsigned)in_support2(ri, SMEM ? pp[k0 + u] : HR_DYNAMIC_LOAD(pp + k0 + u), s2)
+                   << u;
         const int rem = cnt - k0;
         if (rem < kMaskChunk) sub &= (1u << rem) - 1u;
         m |= sub << k0;
@@ -1167,6 +1170,153 @@ __device__ __forceinline__ void pass_fluid(const Consts &K, const Bufs &B, int i
     }
 }
 
+// The same phases with the block's candidates staged in shared memory (a
+// measured variant of the pass, HR_FLAG_STAGE_POS / HR_FLAG_STAGE_ALL).
+// When every in-box particle of a pass block lies in one cell row, the three
+// stencil rows of all of them are three contiguous ranges of the sorted
+// arrays, [start(c_min + dy ncx - 1), start(c_max + dy ncx + 2)) for dy =
+// -1, 0, 1 (cell_start is monotone).  The block copies those ranges once --
+// the positions (SV = 1), or the positions, velocities and EOS records
+// (SV = 2) -- and the predicate (and the pair terms) read them there.  A
+// block that spans two cell rows, or whose ranges exceed kStageCap, takes
+// the global path.  The candidates, their order and the arithmetic are
+// those of pass_fluid, so the results are the same bit for bit.
+constexpr int kStageCap = 192;
+template <int SV>
+struct PassStage {
+    int lo[3], n[3];
+    int ok;
+    float2 pos[3][kStageCap + kMaskChunk];
+    float2 vel[SV == 2 ? 3 : 1][SV == 2 ? kStageCap : 1];
+    float4 aux[SV == 2 ? 3 : 1][SV == 2 ? kStageCap : 1];
+};
+
+template <int SV>
+__device__ __forceinline__ void stage_rows(const Consts &K, const Bufs &B, int bx, PassStage<SV> &st)
+{
+    __shared__ int cmin, cmax;
+    if (threadIdx.x == 0) {
+        cmin = 0x7fffffff;
+        cmax = -1;
+    }
+    __syncthreads();
+    const int i = bx * kPassThreads + threadIdx.x;
+    int lo = 0x7fffffff, hi = -1;
+    if (i < K.nf) {
+        const float2 r = B.s_pos[i];
+        if (!outside_box(K, r.x, r.y)) lo = hi = cell_of(K, r.x, r.y);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&cmin, lo);
+        atomicMax(&cmax, hi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = cmax >= 0 && cmin / K.ncx == cmax / K.ncx;
+        for (int r = 0; r < 3 && ok; ++r) {
+            const int a = B.cell_start[cmin + (r - 1) * K.ncx - 1];
+            const int b = B.cell_start[cmax + (r - 1) * K.ncx + 2];
+            if (kChecked && !hr_ok(a >= 0 && a <= b && b <= K.nf, &B.S->status)) ok = 0;
+            st.lo[r] = a;
+            st.n[r] = b - a;
+            ok = ok && b - a <= kStageCap;
+        }
+        st.ok = ok;
+    }
+    __syncthreads();
+    if (!st.ok) return;
+#pragma unroll 1
+    for (int r = 0; r < 3; ++r) {
+        const int a = st.lo[r], n = st.n[r];
+        for (int k = threadIdx.x; k < n + kMaskChunk; k += kPassThreads) {
+            // entries past the range: far away (their bits are masked off too)
+            st.pos[r][k] = k < n ? HR_DYNAMIC_LOAD(&B.s_pos[a + k]) : make_float2(3e38f, 3e38f);
+            if constexpr (SV == 2) {
+                if (k < n) {
+                    st.vel[r][k] = HR_DYNAMIC_LOAD(&B.s_vel[a + k]);
+                    st.aux[r][k] = HR_DYNAMIC_LOAD(&B.s_aux[a + k]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int CL, int SV>
+__device__ __forceinline__ void pass_fluid_staged(const Consts &K, const Bufs &B, int i, float2 ri,
+                                                  int c, const Self &I, Acc &A,
+                                                  const PassStage<SV> &st)
+{
+    auto fluid_pair = [&](int r, int j) {
+        const int k = j - st.lo[r];
+        const float2 rj = st.pos[r][k];
+        float2 vj;
+        float4 aj;
+        if constexpr (SV == 2) {
+            vj = st.vel[r][k];
+            aj = st.aux[r][k];
+        } else {
+            vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
+            aj = HR_DYNAMIC_LOAD(&B.s_aux[j]);
+        }
+        pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                       CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
+    };
+    int base0, base1, base2;
+    unsigned m0, m1, m2;
+    {
+        const int r0 = c - K.ncx, r1 = c, r2 = c + K.ncx;
+        base0 = B.cell_start[r0 - 1];
+        base1 = B.cell_start[r1 - 1];
+        base2 = B.cell_start[r2 - 1];
+        const int e0 = B.cell_start[r0 + 2], e1 = B.cell_start[r1 + 2],
+                  e2 = B.cell_start[r2 + 2];
+        if (kChecked && !(hr_ok(base0 >= st.lo[0] && e0 <= st.lo[0] + st.n[0], &B.S->status) &&
+                          hr_ok(base1 >= st.lo[1] && e1 <= st.lo[1] + st.n[1], &B.S->status) &&
+                          hr_ok(base2 >= st.lo[2] && e2 <= st.lo[2] + st.n[2], &B.S->status)))
+            return;
+        auto row_mask = [&](int r, int a, int b) -> unsigned {
+            if (b - a <= 32) return support_mask<true>(st.pos[r], a - st.lo[r], b - a, ri, K.s2);
+#pragma unroll 1
+            for (int base = a; base < b; base += 32) {
+                unsigned m = support_mask<true>(st.pos[r], base - st.lo[r], min(32, b - base), ri,
+                                                K.s2);
+                if (i >= base && i < base + 32) m &= ~(1u << (i - base));
+                while (m) {
+                    const int j = base + __ffs(m) - 1;
+                    m &= m - 1u;
+                    fluid_pair(r, j);
+                }
+            }
+            return 0u;
+        };
+        m0 = row_mask(0, base0, e0);
+        m1 = row_mask(1, base1, e1);
+        m2 = row_mask(2, base2, e2);
+        if (i >= base1 && i < base1 + 32) m1 &= ~(1u << (i - base1));
+    }
+#pragma unroll 1
+    while ((m0 | m1 | m2) != 0u) {
+        int j, r;
+        if (m0) {
+            j = base0 + __ffs(m0) - 1;
+            m0 &= m0 - 1u;
+            r = 0;
+        } else if (m1) {
+            j = base1 + __ffs(m1) - 1;
+            m1 &= m1 - 1u;
+            r = 1;
+        } else {
+            j = base2 + __ffs(m2) - 1;
+            m2 &= m2 - 1u;
+            r = 2;
+        }
+        fluid_pair(r, j);
+    }
+}
+
 // Ghost neighbours and the epilogue of particle i (inside the box), its
 // fluid sums already in A.
 template <int CL>
@@ -1323,6 +1473,35 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
     const float dt = prime ? 0.0f : B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
     if (i < K.nf) pass_single<CL>(K, B, i, dt, prime, P);
+    pass_block_partials<kPassThreads>(B, bx, P);
+}
+
+// The pass block with staged candidates (see PassStage).
+template <int CL, int SV>
+__device__ __forceinline__ void b_pass_staged(const Consts &K, const Bufs &B, const int bx, int prime)
+{
+    __shared__ PassStage<SV> st;
+    stage_rows<SV>(K, B, bx, st);
+    const int i = bx * kPassThreads + threadIdx.x;
+    const float dt = prime ? 0.0f : B.S->dt_f;
+    PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (i < K.nf) {
+        const float2 ri = B.s_pos[i];
+        const float2 vi = B.s_vel[i];
+        const float4 ai = B.s_aux[i];
+        const float2 rd = B.s_rd[i];
+        if (outside_box(K, ri.x, ri.y)) {
+            pass_frozen<CL>(B, i, vi, rd);
+        } else {
+            const float ci = CL == 1 ? K.c_av : ai.w;
+            const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
+            Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+            const int c = cell_of(K, ri.x, ri.y);
+            if (st.ok) pass_fluid_staged<CL, SV>(K, B, i, ri, c, I, A, st);
+            else pass_fluid<CL>(K, B, i, ri, c, I, A);
+            pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
+        }
+    }
     pass_block_partials<kPassThreads>(B, bx, P);
 }
 
@@ -1606,6 +1785,12 @@ template <int CL>
 __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass(Consts K, Bufs B, int prime)
 {
     b_pass<CL>(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+template <int CL, int SV>
+__global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass_staged(Consts K, Bufs B, int prime)
+{
+    b_pass_staged<CL, SV>(K, B, blockIdx.x, prime);
 }
 
 template <int CL>

@@ -110,6 +110,28 @@ def test_forward_state_is_a_plain_run_and_backward_repeats():
         assert np.array_equal(a.get_state()["xy"], b.get_state()["xy"])
 
 
+@pytest.mark.parametrize("n,every,diag", [(15, 20, 0), (40, 20, 0), (40, 20, 5)])
+def test_taped_last_segment(n, every, diag):
+    # the forward run records its last segment as it goes (not with periodic
+    # diagnostics): the state it leaves, and the derivatives of one or more
+    # backward sweeps, equal those of a plain run and of the recomputing path
+    p, xy = case0()
+    with Case(p, xy) as a, Case(p, xy, diag_every=diag) as b:
+        a.run(n)
+        b.adjoint_forward(n, every)
+        sa, sb = a.get_state(), b.get_state()
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), key
+        assert a.scalars() == b.scalars()
+        d1 = b.adjoint_backward()
+        d2 = b.adjoint_backward()
+        assert np.array_equal(d1["dpeak"], d2["dpeak"])
+        assert np.array_equal(d1["dimpulse"], d2["dimpulse"])
+    ref = adjoint(p, xy, n, every=1)[1]      # every segment recomputed (one step each)
+    assert np.array_equal(d1["dpeak"], ref["dpeak"])
+    assert np.array_equal(d1["dimpulse"], ref["dimpulse"])
+
+
 @pytest.mark.parametrize("motion", [1, 2])
 def test_tau_derivative_exactly_zero_without_decay(motion):
     p, xy = case0(motion=motion, a_const=2e6)
