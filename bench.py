@@ -216,7 +216,10 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     t0 = time.perf_counter()
     blocks, ptune = autotune.tune_persistent(specs, t_end, stream=stream)
     t_ptune = time.perf_counter() - t0
-    persist = [Case(p, xy, stream=stream) for p, xy in specs]
+    # (the persistent kernel takes the 3 x 3 stencil: cases tuned to the 5 x 5
+    # one run on cells of side 2h there, and are not compared bit for bit)
+    pspecs = [(dict(p, cell_factor=max(float(p["cell_factor"]), 1.001)), xy) for p, xy in specs]
+    persist = [Case(p, xy, stream=stream) for p, xy in pspecs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with Batch(persist, t_end, stream=stream, persistent=True, case_blocks=blocks) as b:
@@ -225,7 +228,8 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
     t_persist = time.perf_counter() - t0
     same_p = all(np.array_equal(a.probe_pressure(), g.probe_pressure()) and
                  np.array_equal(a.get_state()["xy"], g.get_state()["xy"])
-                 for a, g in zip(serial, persist))
+                 for a, g, (p, _), (q, _) in zip(serial, persist, specs, pspecs)
+                 if p["cell_factor"] == q["cell_factor"])
     particles = sum(xy.shape[0] for _, xy in specs)
     t_serial = max_over_ranks(t_serial * 1e3, dist) * 1e-3
     t_batch = max_over_ranks(t_batch * 1e3, dist) * 1e-3
@@ -243,6 +247,48 @@ def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3
                                   "total": int(blocks.sum())},
             "persistent_autotune": ptune, "persistent_autotune_s": t_ptune,
             "autotune": tune_report, "autotune_s": t_tune}
+
+
+def pass_variant_benchmark(stream, xy, p, flush, steps=50):
+    """A/B of the interaction pass on the headline workload: candidates read
+    through the read-only path from global memory (the default), their
+    positions staged in shared memory (HR_FLAG_STAGE_POS), their whole
+    records staged (HR_FLAG_STAGE_ALL), and cells of side h with the 5 x 5
+    stencil (cell_factor 0.5).  Each variant: the same flushed-L2 steps from
+    t = 0, the kernel groups timed by the in-graph events.  The staged
+    variants' end states are compared bit for bit with the default's; the
+    5 x 5 stencil sums the same neighbours in another order, so its density
+    is compared to rounding."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    out, ref = {}, None
+    variants = (("global", 0, p), ("stage_pos", 1, p), ("stage_all", 2, p),
+                ("cells_h_5x5", 0, dict(p, cell_factor=0.5)))
+    for name, stage, q in variants:
+        with torch.cuda.stream(stream):
+            c = Case(q, xy, stream=stream, timing=True, stage=stage, probe_capacity=steps + 16)
+        c.run(5)
+        c.sync()
+        gs = {}
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                c.step()
+            stream.synchronize()
+            for g, v in c.kernel_times().items():
+                gs.setdefault(g, []).append(v)
+        st = c.get_state()
+        c.close()
+        out[name] = {g + "_us": 1e3 * statistics.mean(v) for g, v in gs.items()}
+        out[name]["step_us"] = sum(out[name].values())
+        if ref is None:
+            ref = st
+        elif stage:
+            out[name]["bitwise_equal"] = all(np.array_equal(ref[k], st[k]) for k in ref)
+        else:
+            out[name]["rho_max_rel_diff"] = float(np.abs(st["rho"] / ref["rho"] - 1.0).max())
+    out["steps"] = steps
+    return out
 
 
 def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
@@ -614,6 +660,10 @@ def run_only(args):
     stream = torch.cuda.Stream()
     if args.only == "sweep":
         out = sweep_benchmark(stream)
+    elif args.only == "passvar":
+        p, xy = workload(args.dx)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = pass_variant_benchmark(stream, xy, p, flush, steps=args.steps)
     else:
         from paper_2609_05494_b300 import Case
         p, xy = workload(args.dx)
@@ -655,7 +705,8 @@ def main():
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-scaling", action="store_true")
     ap.add_argument("--no-production", action="store_true")
-    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep"),
+    ap.add_argument("--no-passvar", action="store_true")
+    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar"),
                     help="run one leg alone on the channel at --dx for --steps steps "
                          "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
@@ -766,6 +817,7 @@ def main():
     paper = None if args.no_paper else paper_event_benchmark(stream)
     scaling = None if args.no_scaling else scaling_benchmark(stream, flush)
     production = None if args.no_production else production_benchmark(stream)
+    passvar = None if args.no_passvar else pass_variant_benchmark(stream, xy, p, flush)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -814,6 +866,7 @@ def main():
         "paper_event": paper,
         "size_sweep": scaling,
         "production": production,
+        "pass_variants": passvar,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

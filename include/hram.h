@@ -96,7 +96,12 @@ extern "C" {
  *  dt_mode         0 adaptive dt, 1 fixed dt = cfl h / (c0 + v0)
  *  rho_lo, rho_hi  density band as fractions of rho0 (0.5, 1.5)
  *  box_pad         computational-box padding (<= 0: default)
- *  cell_factor     cell side / 2h (>= 1.001)
+ *  cell_factor     cell side / 2h: >= 1 gives cells of side max(f, 1.001) 2h
+ *                  and the 3 x 3 cell stencil; [0.5, 1) cells of side
+ *                  max(f, 0.5005) 2h and the 5 x 5 stencil (smaller cells,
+ *                  fewer candidates per particle, more cells to scan; not with
+ *                  HR_FLAG_TANGENT, the staged pass variants, the reverse mode
+ *                  or a persistent batch)
  *  probe_xy        wall probe points, n_probes of them
  *  probe_capacity  probe history rows kept on the device
  *  diag_every      record FP64 diagnostics every k steps (0 = never)
@@ -276,7 +281,8 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
  * hr_batch_step then return HR_ETIMEOUT and mark every case with it (the
  * cases stopped mid-step).  hr_batch_run runs the whole sweep (max_steps
  * <= 0) or max_steps steps of each case in one launch; hr_batch_step runs
- * one.  Same ownership and closure rules as hr_batch_create; t_end > 0. */
+ * one.  Same ownership and closure rules as hr_batch_create; t_end > 0;
+ * every case takes the 3 x 3 stencil (cell_factor >= 1), else HR_EINVAL. */
 int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
                                const int32_t *case_blocks, int64_t spin_limit, void *cuda_stream,
                                hr_batch **out);

@@ -4,7 +4,9 @@ Three choices are tuned by timing them on the device, not by a model:
 
 * the cell grid of each case: the cell side as a multiple of the support
   2h (``cell_factor``).  Larger cells mean more candidates per particle in
-  the interaction pass but fewer cells to scan in the sort;
+  the interaction pass but fewer cells to scan in the sort; a factor of 0.5
+  gives cells of side h and the 5 x 5 stencil (25 h^2 of candidates against
+  at least 36 h^2);
 * the block schedule of a batch: the order in which the blocks of each
   batched launch visit the cases (case after case, round robin, largest
   case first);
@@ -23,7 +25,7 @@ import numpy as np
 
 from .api import Batch, Case
 
-CELL_FACTORS = (1.001, 1.1, 1.25)
+CELL_FACTORS = (0.5, 1.001, 1.1, 1.25)
 
 
 def _events():
@@ -126,10 +128,14 @@ def tune_persistent(specs, t_end: float, horizon: float = 60e-6, stream=None, we
     """Block counts of a persistent batch: each candidate split of the resident
     blocks (weights (a, b) of block_counts) runs the sweep's first ``horizon``
     seconds of simulated time on throw-away copies; the fastest split wins.
+    Cases tuned to the 5 x 5 stencil run on cells of side 2h here.
     Returns (case_blocks, report)."""
     import torch
     closure = int(specs[0][0].get("closure", 0))
     cap = Batch.capacity(closure)
+    # the persistent kernel takes the 3 x 3 stencil only
+    specs = [(dict(p, cell_factor=max(float(p.get("cell_factor", 1.001)), 1.001)), xy)
+             for p, xy in specs]
     report = {"capacity": cap, "candidates": []}
     best, best_ms = None, None
     for a, b in weights:

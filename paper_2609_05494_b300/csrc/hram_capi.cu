@@ -369,8 +369,12 @@ int validate(const hr_params *P, long long nf)
     if (P->motion == 3 && !(P->disk_density > 0)) return HR_EINVAL;
     if (P->motion == 1 && !(P->drag_M > 0)) return HR_EINVAL;
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
-    if (P->cell_factor < 1.0) return HR_EINVAL;
+    if (!(P->cell_factor >= 0.5)) return HR_EINVAL;
     if ((P->flags & HR_FLAG_STAGE_POS) && (P->flags & HR_FLAG_STAGE_ALL)) return HR_EINVAL;
+    // cells of side < 2h (5 x 5 stencil): the plain and batched steps only
+    if (P->cell_factor < 1.0 &&
+        (P->flags & (HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL)))
+        return HR_EINVAL;
     // tangent mode: fixed time step (smooth in c0) and a prescribed motion
     if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
     if (P->closure < 0 || P->closure > 1) return HR_EINVAL;
@@ -460,7 +464,10 @@ void make_consts(hr_case *c)
     std::memset(&K, 0, sizeof K);
     const double h = P.h_over_dx * P.dx;
     const double s = 2.0 * h;
-    const double dc = s * (P.cell_factor > 1.001 ? P.cell_factor : 1.001);
+    // cells of side >= 2h take the 3 x 3 stencil; side in [h, 2h) the 5 x 5
+    K.sr = P.cell_factor < 1.0 ? 2 : 1;
+    const double dc = K.sr == 2 ? s * std::max(P.cell_factor, 0.5005)
+                                : s * std::max(P.cell_factor, 1.001);
     double padx, pady;
     if (P.box_pad > 0.0) {
         padx = pady = P.box_pad;
@@ -470,11 +477,12 @@ void make_consts(hr_case *c)
         if (P.end_walls && P.wall_layers > 0) padx = (P.wall_layers + 2) * P.dx + s;
     }
     const double xlo = -padx, xhi = P.Lx + padx, ylo = -0.5 * P.W - pady, yhi = 0.5 * P.W + pady;
-    K.x0 = (float)(xlo - dc);
-    K.y0 = (float)(ylo - dc);
+    // sr cells of margin on every side, so a stencil never leaves the grid
+    K.x0 = (float)(xlo - K.sr * dc);
+    K.y0 = (float)(ylo - K.sr * dc);
     K.inv_dc = (float)(1.0 / dc);
-    K.ncx = (int)std::floor((xhi - xlo) / dc) + 3;
-    K.ncy = (int)std::floor((yhi - ylo) / dc) + 3;
+    K.ncx = (int)std::floor((xhi - xlo) / dc) + 1 + 2 * K.sr;
+    K.ncy = (int)std::floor((yhi - ylo) / dc) + 1 + 2 * K.sr;
     K.ncell = K.ncx * K.ncy;
     K.xlo = (float)xlo;
     K.xhi = (float)xhi;
@@ -798,6 +806,8 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     else if (c->stage == 1) k_pass_staged<0, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 2 && paper) k_pass_staged<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 2) k_pass_staged<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (K.sr == 2 && paper) k_pass<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (K.sr == 2) k_pass<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (paper) k_pass<1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
@@ -1864,6 +1874,7 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
     if (!c || !out || n < 3 || n_steps < 1 || checkpoint_every < 1) return HR_EINVAL;
     if (c->P.closure != 0 || c->P.dt_mode != 1 || c->P.motion < 0 || c->P.motion > 2 || c->tangent)
         return HR_EINVAL;
+    if (c->K.sr != 1) return HR_EINVAL;   // the reverse kernels take the 3 x 3 stencil
     if (c->K.n_probes < 1 || n_steps > c->K.probe_cap) return HR_EINVAL;
     int st = device_status(c);
     if (st < 0) return st;
@@ -2179,7 +2190,7 @@ int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
     };
     for (int k = 0; k < n_cases; ++k) {
         if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent ||
-            cases[k]->K.closure != cases[0]->K.closure)
+            cases[k]->K.closure != cases[0]->K.closure || cases[k]->K.sr != 1)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }

@@ -60,6 +60,7 @@ struct Consts {
     // grid and box
     float x0, y0, inv_dc;
     int ncx, ncy, ncell;
+    int sr;   // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
     float xlo, xhi, ylo, yhi;
     float W2, Lx;
     int side_walls, end_walls;
@@ -266,8 +267,8 @@ __device__ __forceinline__ int cell_of(const Consts &K, float x, float y)
 {
     int cx = __float2int_rd(__fmul_rn(__fsub_rn(x, K.x0), K.inv_dc));
     int cy = __float2int_rd(__fmul_rn(__fsub_rn(y, K.y0), K.inv_dc));
-    cx = min(max(cx, 1), K.ncx - 2);
-    cy = min(max(cy, 1), K.ncy - 2);
+    cx = min(max(cx, K.sr), K.ncx - 1 - K.sr);
+    cy = min(max(cy, K.sr), K.ncy - 1 - K.sr);
     return cy * K.ncx + cx;
 }
 
@@ -481,18 +482,20 @@ __device__ inline void kinematics(const Consts &K, double t, double *xo, double 
 }
 
 // Candidate enumeration shared by every gather (ghost pass, interaction pass,
-// probes, debug neighbour lists): the 3x3 cell stencil of cell c is three
-// contiguous row ranges [start(row, cx-1), start(row, cx+2)) of the sorted
-// arrays.  f(j) is called for every candidate j.
+// probes, debug neighbour lists): the (2R+1) x (2R+1) cell stencil of cell c
+// (R = K.sr) is 2R+1 contiguous row ranges [start(row, cx-R),
+// start(row, cx+R+1)) of the sorted arrays.  f(j) is called for every
+// candidate j.
 template <class F>
 __device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c,
                                                      int limit, int *status, F &&f)
 {
+    const int R = K.sr;
 #pragma unroll 1
-    for (int dy = -1; dy <= 1; ++dy) {
+    for (int dy = -R; dy <= R; ++dy) {
         const int row = c + dy * K.ncx;
-        if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, status)) continue;
-        const int a = start[row - 1], b = start[row + 2];
+        if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, status)) continue;
+        const int a = start[row - R], b = start[row + R + 1];
         if (kChecked && !row_ok(K, row, a, b, limit, status)) continue;
         for (int j = a; j < b; ++j) f(j);
     }
@@ -896,14 +899,15 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
         };
         float S = K.self_w - 1.0f;
         const int c = cell_of(K, ri.x, ri.y);
-        // the three stencil rows: predicate masks over blocks of up to 32
+        // the stencil rows: predicate masks over blocks of up to 32
         // candidates (unrolled, independent loads), then the set bits in
         // ascending order
+        const int R = K.sr;
 #pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             const int row = c + dy * K.ncx;
-            if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
-            const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+            if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
+            const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
             if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
 #pragma unroll 1
             for (int base = a; base < b; base += 32) {
@@ -964,11 +968,12 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
         const bool inside = !outside_box(K, rg.x, rg.y);
         if (inside) {
             const int c = cell_of(K, rg.x, rg.y);
+            const int R = K.sr;
 #pragma unroll 1
-            for (int dy = -1; dy <= 1; ++dy) {
+            for (int dy = -R; dy <= R; ++dy) {
                 const int row = c + dy * K.ncx;
-                if (kChecked && !hr_ok(row - 1 >= 0 && row + 2 <= K.ncell, &B.S->status)) continue;
-                const int a = B.cell_start[row - 1], b = B.cell_start[row + 2];
+                if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
+                const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
                 if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
                 for (int j = a + lane; j < b; j += 32) {
                     const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
@@ -1165,6 +1170,70 @@ __device__ __forceinline__ void pass_fluid(const Consts &K, const Bufs &B, int i
         } else {
             j = base2 + __ffs(m2) - 1;
             m2 &= m2 - 1u;
+        }
+        fluid_pair(j);
+    }
+}
+
+// Phases 1 and 2 on cells of side >= h (K.sr = 2): the 5 x 5 stencil as
+// five row ranges of five cells each, in the same order (rows from below,
+// candidates in sorted order within a row).
+template <int CL>
+__device__ __forceinline__ void pass_fluid5(const Consts &K, const Bufs &B, int i, float2 ri,
+                                            int c, const Self &I, Acc &A)
+{
+    auto fluid_pair = [&](int j) {
+        const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
+        const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
+        const float4 aj = HR_DYNAMIC_LOAD(&B.s_aux[j]);
+        pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                       CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
+    };
+    int base[5];
+    unsigned m[5];
+    auto row_mask = [&](int a, int b) -> unsigned {
+        if (b - a <= 32) return support_mask(B.s_pos, a, b - a, ri, K.s2);
+#pragma unroll 1
+        for (int bs = a; bs < b; bs += 32) {
+            unsigned mm = support_mask(B.s_pos, bs, min(32, b - bs), ri, K.s2);
+            if (i >= bs && i < bs + 32) mm &= ~(1u << (i - bs));
+            while (mm) {
+                const int j = bs + __ffs(mm) - 1;
+                mm &= mm - 1u;
+                fluid_pair(j);
+            }
+        }
+        return 0u;
+    };
+    if (kChecked && !hr_ok(c - 2 * K.ncx - 2 >= 0 && c + 2 * K.ncx + 3 <= K.ncell, &B.S->status))
+        return;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int row = c + (r - 2) * K.ncx;
+        base[r] = B.cell_start[row - 2];
+        const int e = B.cell_start[row + 3];
+        if (kChecked && !row_ok(K, row, base[r], e, K.nf, &B.S->status)) return;
+        m[r] = row_mask(base[r], e);
+    }
+    if (i >= base[2] && i < base[2] + 32) m[2] &= ~(1u << (i - base[2]));
+#pragma unroll 1
+    while ((m[0] | m[1] | m[2] | m[3] | m[4]) != 0u) {
+        int j;
+        if (m[0]) {
+            j = base[0] + __ffs(m[0]) - 1;
+            m[0] &= m[0] - 1u;
+        } else if (m[1]) {
+            j = base[1] + __ffs(m[1]) - 1;
+            m[1] &= m[1] - 1u;
+        } else if (m[2]) {
+            j = base[2] + __ffs(m[2]) - 1;
+            m[2] &= m[2] - 1u;
+        } else if (m[3]) {
+            j = base[3] + __ffs(m[3]) - 1;
+            m[3] &= m[3] - 1u;
+        } else {
+            j = base[4] + __ffs(m[4]) - 1;
+            m[4] &= m[4] - 1u;
         }
         fluid_pair(j);
     }
@@ -1402,7 +1471,9 @@ __device__ __forceinline__ void pass_frozen(const Bufs &B, int i, float2 vi, flo
     B.st_X[i] = make_float2(0.f, 0.f);
 }
 
-template <int CL>
+// R: the stencil reach (1 or 2), or 0 to take it from K.sr (batched and
+// persistent kernels, whose cases may differ).
+template <int CL, int R = 0>
 __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int i, float dt,
                                             int prime, PassPart &P)
 {
@@ -1418,7 +1489,8 @@ __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int 
     const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
     Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
     const int c = cell_of(K, ri.x, ri.y);
-    pass_fluid<CL>(K, B, i, ri, c, I, A);
+    if (R == 2 || (R == 0 && K.sr == 2)) pass_fluid5<CL>(K, B, i, ri, c, I, A);
+    else pass_fluid<CL>(K, B, i, ri, c, I, A);
     pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
 }
 
@@ -1466,13 +1538,13 @@ __device__ __forceinline__ void pass_block_partials(const Bufs &B, const int bx,
     }
 }
 
-template <int CL>
+template <int CL, int R = 0>
 __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     const int i = bx * blockDim.x + threadIdx.x;
     const float dt = prime ? 0.0f : B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
-    if (i < K.nf) pass_single<CL>(K, B, i, dt, prime, P);
+    if (i < K.nf) pass_single<CL, R>(K, B, i, dt, prime, P);
     pass_block_partials<kPassThreads>(B, bx, P);
 }
 
@@ -1516,7 +1588,31 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 {
     const int lane = threadIdx.x & 31;
     float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f;
-    if (!outside_box(K, px, py)) {
+    auto add = [&](int j) {
+        const float2 rj = B.s_pos[j];
+        const float d = B.st_rho[j];
+        if (!in_support(px, py, rj.x, rj.y, K.s2)) return;
+        const float dx = px - rj.x, dy = py - rj.y;
+        const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy * dy)));
+        const float rw = (1.0f + d) * W;
+        const float pj = CL == 1 ? mg_p(K, d, B.st_D[j].y) : tait_p(K, d);
+        SW += W;
+        Sp = fmaf(pj, W, Sp);
+        Srx = fmaf(rw, dx, Srx);
+        Sry = fmaf(rw, dy, Sry);
+    };
+    if (!outside_box(K, px, py) && K.sr != 1) {
+        // 5 x 5 stencil: the rows one after another
+        const int c = cell_of(K, px, py);
+        const int R = K.sr;
+        for (int dy = -R; dy <= R; ++dy) {
+            const int row = c + dy * K.ncx;
+            if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
+            const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
+            for (int j = a + lane; j < b; j += 32) add(j);
+        }
+    } else if (!outside_box(K, px, py)) {
         const int c = cell_of(K, px, py);
         if (kChecked && !hr_ok(c - K.ncx - 1 >= 0 && c + K.ncx + 2 <= K.ncell, &B.S->status))
             return 0.0f;
@@ -1528,20 +1624,8 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
                           row_ok(K, c + K.ncx, a2, b2, K.nf, &B.S->status)))
             return 0.0f;
         const int n0 = b0 - a0, n1 = b1 - a1, n = n0 + n1 + (b2 - a2);
-        for (int k = lane; k < n; k += 32) {
-            const int j = k < n0 ? a0 + k : (k < n0 + n1 ? a1 + (k - n0) : a2 + (k - n0 - n1));
-            const float2 rj = B.s_pos[j];
-            const float d = B.st_rho[j];
-            if (!in_support(px, py, rj.x, rj.y, K.s2)) continue;
-            const float dx = px - rj.x, dy = py - rj.y;
-            const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy * dy)));
-            const float rw = (1.0f + d) * W;
-            const float pj = CL == 1 ? mg_p(K, d, B.st_D[j].y) : tait_p(K, d);
-            SW += W;
-            Sp = fmaf(pj, W, Sp);
-            Srx = fmaf(rw, dx, Srx);
-            Sry = fmaf(rw, dy, Sry);
-        }
+        for (int k = lane; k < n; k += 32)
+            add(k < n0 ? a0 + k : (k < n0 + n1 ? a1 + (k - n0) : a2 + (k - n0 - n1)));
     }
     SW = warp_sum(SW);
     Sp = warp_sum(Sp);
@@ -1781,10 +1865,10 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
 // 10 resident blocks per SM (48 registers): 40 warps against 36 at the
 // compiler's own 54 registers, 3 % faster on the 1.125M workload, no spills
 constexpr int kPassMinBlocks = 10;
-template <int CL>
+template <int CL, int R = 1>
 __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass(Consts K, Bufs B, int prime)
 {
-    b_pass<CL>(K, B, blockIdx.x, gridDim.x, prime);
+    b_pass<CL, R>(K, B, blockIdx.x, gridDim.x, prime);
 }
 
 template <int CL, int SV>

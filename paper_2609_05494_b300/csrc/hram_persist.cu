@@ -128,7 +128,7 @@ __device__ __forceinline__ void pass_pair(const Consts &K, const Bufs &B, int q)
     const int i = q * kPersistThreads + threadIdx.x;
     const float dt = B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
-    if (i < K.nf) pass_single<CL>(K, B, i, dt, 0, P);
+    if (i < K.nf) pass_single<CL, 1>(K, B, i, dt, 0, P);   // 3 x 3 stencil (cell_factor >= 1)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0)) {
         P.fdx = warp_sum(P.fdx);

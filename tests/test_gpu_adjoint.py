@@ -186,7 +186,8 @@ def test_autograd_reverse_mode():
 
 def test_reverse_mode_refusals():
     p, xy = case0()
-    for kw in (dict(dt_mode=0), dict(motion=3), dict(closure=1, c0=1448.0)):
+    for kw in (dict(dt_mode=0), dict(motion=3), dict(closure=1, c0=1448.0),
+               dict(cell_factor=0.5)):
         with Case(dict(p, **kw), xy) as c:
             with pytest.raises(HramError) as e:
                 c.adjoint_forward(10)

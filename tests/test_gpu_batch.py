@@ -27,9 +27,13 @@ def sweep_cases(n, dx=2e-3):
     return out
 
 
-def test_batch_equals_cases_run_alone():
+@pytest.mark.parametrize("mixed_cells", [False, True])
+def test_batch_equals_cases_run_alone(mixed_cells):
     t_end = 12e-6
     specs = sweep_cases(6)
+    if mixed_cells:
+        # every other case on cells of side h (5 x 5 stencil) in the same batch
+        specs = [(dict(p, cell_factor=0.5) if k % 2 else p, xy) for k, (p, xy) in enumerate(specs)]
     alone, batched = [], []
     for p, xy in specs:
         a = Case(p, xy)
@@ -236,6 +240,10 @@ def test_persistent_batch_refusals():
     with Case(q, x) as other:
         with pytest.raises(HramError):
             Batch([cs[0], other], 1e-5, persistent=True)
+    # the persistent kernel takes the 3 x 3 stencil only
+    with Case(dict(specs[1][0], cell_factor=0.5), specs[1][1]) as fine:
+        with pytest.raises(HramError):
+            Batch([cs[0], fine], 1e-5, persistent=True)
 
 
 def test_persistent_autotuner_block_counts():

@@ -179,11 +179,17 @@ def test_caller_owned_output_buffers():
 
 def test_invalid_parameters_rejected():
     p, xy = impact_case()
-    for bad in (dict(dx=0.0), dict(Ng=5000), dict(cfl=-1.0), dict(rho_hi=0.2)):
+    for bad in (dict(dx=0.0), dict(Ng=5000), dict(cfl=-1.0), dict(rho_hi=0.2),
+                dict(cell_factor=0.4)):
         q = dict(p)
         q.update(bad)
         with pytest.raises(HramError) as e:
             Case(q, xy)
+        assert e.value.code == _lib.HR_EINVAL
+    # the staged pass variants take the 3 x 3 stencil, one variant at a time
+    for kw, stage in ((dict(cell_factor=0.5), 1), (dict(cell_factor=0.5), 2)):
+        with pytest.raises(HramError) as e:
+            Case(dict(p, **kw), xy, stage=stage)
         assert e.value.code == _lib.HR_EINVAL
 
 

@@ -28,15 +28,17 @@ def both(p, xy32, vel=None, rho=None, **kw):
 
 # ------------------------------------------------------------ neighbours
 
+@pytest.mark.parametrize("cf", [1.001, 0.5])
 @pytest.mark.parametrize("kind", ["impact", "perturbed_positions", "closed_box"])
-def test_neighbour_sets_bit_exact(kind):
+def test_neighbour_sets_bit_exact(kind, cf):
+    # cf = 0.5: cells of side h and the 5 x 5 stencil
     if kind == "impact":
-        p, xy = impact_case()
+        p, xy = impact_case(cell_factor=cf)
     elif kind == "perturbed_positions":
-        p, xy = impact_case(jitter=0.3, Lx=0.05, W=0.04)
+        p, xy = impact_case(jitter=0.3, Lx=0.05, W=0.04, cell_factor=cf)
     else:
         p, xy = impact_case(Lx=0.03, W=0.02, dx=1e-3, end_walls=1, Ng=40, R_disk=3e-3,
-                            x_c0=0.012, v0=0.0)
+                            x_c0=0.012, v0=0.0, cell_factor=cf)
     g, o = both(p, xy)
     off_g, ids_g = g.neighbours()
     off_o, ids_o = o.neighbours()
@@ -144,6 +146,37 @@ def test_ghost_state_after_one_step():
     assert np.abs(gg["vel"] - go["vel"]).max() <= 1e-5 * vmax
 
 
+@pytest.mark.parametrize("closure", [0, 1])
+def test_five_by_five_stencil_one_step_and_window(closure):
+    # cells of side h (5 x 5 stencil): the same neighbours in another order,
+    # so the sums agree with the oracle to rounding; one step from a perturbed
+    # state, then 150 steps of the impact with the probes it reaches
+    p, xy = impact_case(cell_factor=0.5, closure=closure)
+    vel, rho = perturbed(p, xy)
+    g, o = both(p, xy, vel, None if closure else rho)
+    dt = o.scalars()["dt"]
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert_p_close("5x5 closure=%d" % closure, p, sg["p"], o, dt)
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+    p2, xy2 = impact_case(cell_factor=0.5, closure=closure)
+    p2["probes"] = list(p2["probes"]) + [(0.030, 0.0), (0.020, 0.030)]
+    g, o = both(p2, xy2)
+    g.run(150)
+    o.run(150)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    gated = 0
+    for k in range(po.shape[1]):
+        if np.abs(po[:, k]).max() > 1e6:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
+            gated += 1
+    assert gated >= 2
+
+
 # ------------------------------------------------------------ probe window
 
 def test_probe_history_parity_window():
@@ -213,6 +246,36 @@ def test_run_is_deterministic():
     for k in sa:
         assert np.array_equal(sa[k], sb[k])
     assert np.array_equal(a.probe_pressure(), b.probe_pressure())
+
+
+@pytest.mark.parametrize("stage", [1, 2])
+@pytest.mark.parametrize("kind", ["impact", "dense", "paper"])
+def test_staged_pass_variants_bitwise(stage, kind):
+    # the pass with its candidates staged in shared memory reads the same
+    # values in the same order: every array equals the global-load pass's
+    if kind == "impact":
+        p, xy = impact_case()
+        vel = None
+    elif kind == "dense":
+        # rows longer than 32 candidates, and blocks beyond the staging capacity
+        p = casegen.base_params()
+        p.update(dx=1e-3, Lx=0.02, W=0.02, Ng=0, wall_layers=3, gy=0.0)
+        xy = casegen.fluid_lattice(0.012, 0.012, 0.5e-3, 0.01, 21, disk=None)
+        xy[:, 0] += 0.004
+        xy = xy.astype(np.float32)
+        vel, _ = perturbed(p, xy, seed=5, v_amp=3.0, rho_rel=0.0)
+    else:
+        p, xy = impact_case(closure=1)
+        vel = None
+    a = Case(p, xy, vel)
+    b = Case(p, xy, vel, stage=stage)
+    a.run(30)
+    b.run(30)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.probe_pressure(), b.probe_pressure())
+    assert a.scalars() == b.scalars()
 
 
 @pytest.mark.parametrize("closure", [0, 1])

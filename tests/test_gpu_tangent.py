@@ -122,7 +122,7 @@ def test_autograd_bridge_returns_library_jacobian():
 
 def test_unsupported_set_ups_are_refused():
     p, xy = tangent_case()
-    for kw in (dict(dt_mode=0), dict(motion=3)):
+    for kw in (dict(dt_mode=0), dict(motion=3), dict(cell_factor=0.5)):
         q = dict(p)
         q.update(kw)
         with pytest.raises(HramError) as e:
