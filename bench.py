@@ -253,20 +253,22 @@ def pass_variant_benchmark(stream, xy, p, flush, steps=50):
     """A/B of the interaction pass on the headline workload: candidates read
     through the read-only path from global memory (the default), their
     positions staged in shared memory (HR_FLAG_STAGE_POS), their whole
-    records staged (HR_FLAG_STAGE_ALL), and cells of side h with the 5 x 5
-    stencil (cell_factor 0.5).  Each variant: the same flushed-L2 steps from
+    records staged (HR_FLAG_STAGE_ALL), cells of side h with the 5 x 5
+    stencil (cell_factor 0.5), and every fluid pair evaluated once
+    (HR_FLAG_NEWTON3).  Each variant: the same flushed-L2 steps from
     t = 0, the kernel groups timed by the in-graph events.  The staged
     variants' end states are compared bit for bit with the default's; the
-    5 x 5 stencil sums the same neighbours in another order, so its density
-    is compared to rounding."""
+    5 x 5 stencil and the Newton-3 pass sum the same neighbours in another
+    order, so their density is compared to rounding."""
     import torch
     from paper_2609_05494_b300 import Case
     out, ref = {}, None
-    variants = (("global", 0, p), ("stage_pos", 1, p), ("stage_all", 2, p),
-                ("cells_h_5x5", 0, dict(p, cell_factor=0.5)))
-    for name, stage, q in variants:
+    variants = (("global", 0, p, False), ("stage_pos", 1, p, False), ("stage_all", 2, p, False),
+                ("cells_h_5x5", 0, dict(p, cell_factor=0.5), False), ("newton3", 0, p, True))
+    for name, stage, q, n3 in variants:
         with torch.cuda.stream(stream):
-            c = Case(q, xy, stream=stream, timing=True, stage=stage, probe_capacity=steps + 16)
+            c = Case(q, xy, stream=stream, timing=True, stage=stage, newton3=n3,
+                     probe_capacity=steps + 16)
         c.run(5)
         c.sync()
         gs = {}

@@ -75,6 +75,15 @@ extern "C" {
                             or no faster on a B300; single-case steps only) */
 #define HR_FLAG_STAGE_ALL 8 /* as HR_FLAG_STAGE_POS, with the velocities and
                             EOS records staged too (at most one of the two) */
+#define HR_FLAG_NEWTON3 16 /* interaction pass variant: every fluid pair is
+                            evaluated once (half stencil) and both particles
+                            take their side of it, summed in a fixed order with
+                            no floating-point atomics; results agree with the
+                            plain pass to rounding and are reproducible.
+                            Closure 0, cell_factor >= 1, single-case steps; not
+                            with the tangent or reverse modes.  A cell denser
+                            than the tiles hold makes the step return
+                            HR_ERANGE */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)

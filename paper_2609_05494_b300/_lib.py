@@ -36,6 +36,7 @@ HR_FLAG_TIMING = 1
 HR_FLAG_TANGENT = 2
 HR_FLAG_STAGE_POS = 4
 HR_FLAG_STAGE_ALL = 8
+HR_FLAG_NEWTON3 = 16
 
 EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",

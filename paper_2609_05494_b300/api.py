@@ -73,12 +73,13 @@ class Case:
     which case the library allocates it.  ``stage`` picks the interaction
     pass variant: 0 reads candidates from global memory, 1 stages the
     candidates' positions in shared memory, 2 their whole records (the
-    results are identical).
+    results are identical).  ``newton3`` evaluates every fluid pair once
+    (results equal to rounding).
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
                  probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
-                 tangent: bool = False, stage: int = 0):
+                 tangent: bool = False, stage: int = 0, newton3: bool = False):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -90,6 +91,8 @@ class Case:
         if stage not in (0, 1, 2):
             raise ValueError("stage must be 0, 1 or 2")
         flags |= (0, _lib.HR_FLAG_STAGE_POS, _lib.HR_FLAG_STAGE_ALL)[stage]
+        if newton3:
+            flags |= _lib.HR_FLAG_NEWTON3
         self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)

@@ -9,6 +9,7 @@
 #include "hram_device.cuh"
 #include "hram_tangent.cuh"
 #include "hram_adjoint.cuh"
+#include "hram_n3.cuh"
 #include "hram_persist.h"
 #include "hram.h"
 
@@ -371,6 +372,11 @@ int validate(const hr_params *P, long long nf)
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
     if (!(P->cell_factor >= 0.5)) return HR_EINVAL;
     if ((P->flags & HR_FLAG_STAGE_POS) && (P->flags & HR_FLAG_STAGE_ALL)) return HR_EINVAL;
+    // the Newton-3 pass: closure 0, the 3 x 3 stencil, no other pass variant
+    if ((P->flags & HR_FLAG_NEWTON3) &&
+        (P->closure != 0 || P->cell_factor < 1.0 ||
+         (P->flags & (HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL))))
+        return HR_EINVAL;
     // cells of side < 2h (5 x 5 stencil): the plain and batched steps only
     if (P->cell_factor < 1.0 &&
         (P->flags & (HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL)))
@@ -423,6 +429,7 @@ struct hr_case {
     // tangent mode (HR_FLAG_TANGENT)
     bool tangent = false;
     int stage = 0;                // pass variant: 0 global loads, 1/2 staged candidates
+    bool n3 = false;              // pass variant: each fluid pair evaluated once
     TBufs T{};
     int tpass_blocks = 0;
     void *t_base = nullptr;
@@ -561,6 +568,12 @@ void make_consts(hr_case *c)
     c->n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
     c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
     c->tpass_blocks = (int)((c->nf + kTPassThreads - 1) / kTPassThreads);
+    K.n3 = (P.flags & HR_FLAG_NEWTON3) ? 1 : 0;
+    if (K.n3) {
+        // row chunks of kN3Threads particles: at most one partial chunk per row
+        c->pass_blocks = (int)((c->nf + kN3Threads - 1) / kN3Threads) + K.ncy + 1;
+        K.n3_tiles_max = c->pass_blocks;
+    }
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
     K.closure = P.closure;
@@ -585,6 +598,7 @@ struct Offsets {
         probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
         fin_part, fin_vmax, fin_npen, fin_ticket;
     size_t s_ex;  // closure 1 only
+    size_t n3_row_base, n3_tile_row, n3_info, n3_flag, n3_ext_a, n3_ext_b, n3_ctl;  // Newton-3 only
     // tangent arrays (zero-sized unless HR_FLAG_TANGENT)
     size_t t_begin, t_s_pos, t_s_vel, t_s_aux, t_s_rd, t_st_vel, t_st_rho, t_st_a, t_st_D, t_st_X,
         t_u_pos, t_u_vel, t_g_vel, t_g_aux, t_perm, t_part, t_sc, t_end;
@@ -644,6 +658,16 @@ Offsets plan(const hr_case *c)
     o.diag_hist = L.add((size_t)dcap * kDiagFields * 8);
     o.io = L.add(n * 6 * 4);
     o.s_ex = L.add(c->P.closure == 1 ? n * 16 : 0);
+    {
+        const size_t nt = K.n3 ? (size_t)K.n3_tiles_max : 0;
+        o.n3_row_base = L.add(K.n3 ? ((size_t)K.ncy + 1) * 4 : 0);
+        o.n3_tile_row = L.add(nt * 4);
+        o.n3_info = L.add(nt * 16);
+        o.n3_flag = L.add(nt * 4);
+        o.n3_ext_a = L.add(nt * kN3ExtCap * 16);
+        o.n3_ext_b = L.add(nt * kN3ExtCap * 4);
+        o.n3_ctl = L.add(K.n3 ? 8 : 0);
+    }
     const size_t tn = (c->P.flags & HR_FLAG_TANGENT) ? n * kDir : 0;
     const size_t tg = (c->P.flags & HR_FLAG_TANGENT) ? ng * kDir : 0;
     const bool tm = (c->P.flags & HR_FLAG_TANGENT) != 0;
@@ -728,6 +752,14 @@ void bind(hr_case *c, const Offsets &o)
     c->stage = (c->P.flags & HR_FLAG_STAGE_POS) ? 1 : (c->P.flags & HR_FLAG_STAGE_ALL) ? 2 : 0;
     B.s_ex = c->P.closure == 1 ? at<float4>(w, o.s_ex) : nullptr;
     B.perm_dst = nullptr;
+    c->n3 = c->K.n3 != 0;
+    B.n3_row_base = c->n3 ? at<int>(w, o.n3_row_base) : nullptr;
+    B.n3_tile_row = c->n3 ? at<int>(w, o.n3_tile_row) : nullptr;
+    B.n3_info = c->n3 ? at<int4>(w, o.n3_info) : nullptr;
+    B.n3_flag = c->n3 ? at<int>(w, o.n3_flag) : nullptr;
+    B.n3_ext_a = c->n3 ? at<float4>(w, o.n3_ext_a) : nullptr;
+    B.n3_ext_b = c->n3 ? at<float>(w, o.n3_ext_b) : nullptr;
+    B.n3_ctl = c->n3 ? at<int>(w, o.n3_ctl) : nullptr;
     if (c->tangent) {
         TBufs &T = c->T;
         T.n = (int)c->nf;
@@ -802,7 +834,8 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     }
     if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
-    if (c->stage == 1 && paper) k_pass_staged<1, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    if (c->n3) k_pass_n3<<<c->pass_blocks, kN3Threads, 0, s>>>(K, B, prime);
+    else if (c->stage == 1 && paper) k_pass_staged<1, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 1) k_pass_staged<0, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 2 && paper) k_pass_staged<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 2) k_pass_staged<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
@@ -863,6 +896,8 @@ int device_status(hr_case *c)
     CK(cudaMemcpy(&st, &c->B.S->status, sizeof(int), cudaMemcpyDeviceToHost));
     int rc = st & (HR_WPENETRATION | HR_WOUTSIDE | HR_WPROBEFULL);
     if (st & ST_BOUNDS) rc = HR_ECHECK;
+    else if (st & ST_N3WAIT) rc = HR_ETIMEOUT;
+    else if (st & ST_N3CAP) rc = HR_ERANGE;
     else if (st & ST_NAN) rc = HR_ENAN;
     else if (st & ST_DT) rc = HR_EDT;
     if (rc < 0) c->sticky = rc;
@@ -890,6 +925,10 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
     CK(cudaMemsetAsync(c->B.tile_sum, 0, (size_t)c->n_tiles * 4, c->stream));
     CK(cudaMemsetAsync(c->B.fin_ticket, 0, 4, c->stream));
     CK(cudaMemsetAsync(c->B.S, 0, sizeof(Scalars), c->stream));
+    if (c->n3) {
+        CK(cudaMemsetAsync(c->B.n3_flag, 0, (size_t)c->K.n3_tiles_max * 4, c->stream));
+        CK(cudaMemsetAsync(c->B.n3_ctl, 0, 8, c->stream));
+    }
     if (c->tangent) {
         // the uploaded state does not depend on the parameters; dt = C h /
         // (c0 + v0) has d dt / d ln c0 = -dt c0 / (c0 + v0)
@@ -1874,7 +1913,7 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
     if (!c || !out || n < 3 || n_steps < 1 || checkpoint_every < 1) return HR_EINVAL;
     if (c->P.closure != 0 || c->P.dt_mode != 1 || c->P.motion < 0 || c->P.motion > 2 || c->tangent)
         return HR_EINVAL;
-    if (c->K.sr != 1) return HR_EINVAL;   // the reverse kernels take the 3 x 3 stencil
+    if (c->K.sr != 1 || c->n3) return HR_EINVAL;   // the reverse kernels take the plain pass
     if (c->K.n_probes < 1 || n_steps > c->K.probe_cap) return HR_EINVAL;
     int st = device_status(c);
     if (st < 0) return st;
@@ -2070,7 +2109,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     };
     for (int k = 0; k < n_cases; ++k) {
         // one closure per batch (the kernels are templated on it); no tangents
-        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent ||
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->n3 ||
             cases[k]->K.closure != cases[0]->K.closure)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
@@ -2189,7 +2228,7 @@ int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
         return code;
     };
     for (int k = 0; k < n_cases; ++k) {
-        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent ||
+        if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->n3 ||
             cases[k]->K.closure != cases[0]->K.closure || cases[k]->K.sr != 1)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);

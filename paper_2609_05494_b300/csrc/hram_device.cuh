@@ -52,6 +52,9 @@ constexpr int ST_OUTSIDE = 2;
 constexpr int ST_PROBEFULL = 4;
 constexpr int ST_NAN = 256;
 constexpr int ST_DT = 512;
+constexpr int ST_N3CAP = 2048;    // a Newton-3 pass tile went past a capacity
+constexpr int ST_N3WAIT = 4096;   // a Newton-3 pass tile gave up waiting for another
+constexpr int kN3Threads = 128;   // particles per Newton-3 pass tile
 
 enum GhostKind { KIND_SIDE = 1, KIND_END = 2, KIND_DISK = 3 };
 
@@ -83,6 +86,7 @@ struct Consts {
     float probe_x[kMaxProbes], probe_y[kMaxProbes];
     long long probe_cap;
     int n_pass_blocks, n_ghost_blocks;
+    int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
     // closure 1 (the paper's): cubic B-spline, summation density,
     // Mie-Grueneisen EOS with the internal-energy equation
     int closure;
@@ -165,6 +169,16 @@ struct Bufs {
     double *probe_t;
     // scalars
     Scalars *S;
+    // the Newton-3 pass variant (null otherwise): tile table (per-row first
+    // tile, row of each tile), per-tile header {end, same-row targets, first
+    // target of the row above, its count}, ready flags, partial slabs, and
+    // {ticket, flag value of this step}
+    int *n3_row_base, *n3_tile_row;
+    int4 *n3_info;
+    int *n3_flag;
+    float4 *n3_ext_a;
+    float *n3_ext_b;
+    int *n3_ctl;
 };
 
 // ----------------------------------------------- bounds-checked build
@@ -772,10 +786,45 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
 }
 
+// The Newton-3 pass's tile table: chunks of kN3Threads particles of each
+// cell row, numbered row by row (the pass takes them in that order from a
+// ticket, reset here with the step's flag value advanced).  One block.
+__device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
+{
+    __shared__ int wsum[32];
+    __shared__ int running;
+    if (threadIdx.x == 0) running = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int r0 = 0; r0 < K.ncy; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        int cnt = 0;
+        if (r < K.ncy) cnt = B.cell_start[(r + 1) * K.ncx] - B.cell_start[r * K.ncx];
+        const int ch = (cnt + kN3Threads - 1) / kN3Threads;
+        int total;
+        const int base = running + block_exclusive_scan(ch, wsum, &total);
+        if (r < K.ncy) {
+            B.n3_row_base[r] = base;
+            for (int k = 0; k < ch; ++k)
+                if (base + k < K.n3_tiles_max) B.n3_tile_row[base + k] = r;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) running += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        B.n3_row_base[K.ncy] = min(running, K.n3_tiles_max);
+        B.n3_ctl[0] = 0;
+        B.n3_ctl[1] = B.n3_ctl[1] + 1;
+    }
+}
+
 // Provisional scatter of the IDs by (cell start + atomic slot).  Block 0
-// also clears the tile sums for the next step's k_drift_key.
+// also clears the tile sums for the next step's k_drift_key (and builds the
+// Newton-3 pass's tile table).
 __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
+    if (bx == 0 && K.n3) n3_table(K, B);
     if (bx == 0) {
         const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
         for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;

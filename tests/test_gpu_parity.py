@@ -185,6 +185,58 @@ def test_five_by_five_stencil_one_step_and_window(closure):
     assert gated >= 1
 
 
+def test_newton3_pass_against_oracle():
+    # every fluid pair evaluated once, both sides summed in a fixed order:
+    # one step from a perturbed state, a 250-step window of the impact, and
+    # two runs bit for bit
+    p, xy = impact_case()
+    vel, rho = perturbed(p, xy)
+    g, o = both(p, xy, vel, rho, newton3=True)
+    dt = o.scalars()["dt"]
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert_p_close("newton3 one step", p, sg["p"], o, dt)
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+    assert abs(g.scalars()["dt"] / o.scalars()["dt"] - 1.0) <= 1e-6
+    p2, xy2 = impact_case()
+    p2["probes"] = list(p2["probes"]) + [(0.030, 0.0), (0.020, 0.030), (0.040, -0.030)]
+    g, o = both(p2, xy2, newton3=True)
+    n = p2["n_steps"]
+    g.run(n)
+    o.run(n)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    gated = 0
+    for k in range(po.shape[1]):
+        if np.abs(po[:, k]).max() > 1e6:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
+            gated += 1
+    assert gated >= 3
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("KE", "E_el", "dissipation"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-3), k
+    b = Case(p2, xy2, newton3=True)
+    b.run(n)
+    assert np.array_equal(g.get_state()["rho"], b.get_state()["rho"])
+    assert np.array_equal(pg, b.probe_pressure())
+
+
+def test_newton3_pass_reports_overfull_tiles():
+    # a cell far denser than the tiles hold: the step says so (HR_ERANGE)
+    from paper_2609_05494_b300 import HramError, _lib
+    p = casegen.base_params()
+    p.update(dx=1e-3, Lx=0.02, W=0.02, Ng=0, wall_layers=3, gy=0.0)
+    xy = casegen.fluid_lattice(0.012, 0.012, 0.25e-3, 0.01, 21, disk=None)
+    xy[:, 0] += 0.004
+    with pytest.raises(HramError) as e:
+        c = Case(p, xy.astype(np.float32), newton3=True)
+        c.run(1)
+    assert e.value.code == _lib.HR_ERANGE
+
+
 # ------------------------------------------------------------ probe window
 
 def test_probe_history_parity_window():
