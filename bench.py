@@ -427,6 +427,61 @@ def scaling_benchmark(stream, flush, dxs=(1e-3, 5e-4, 2.5e-4, 2e-4, 1e-4), steps
     return out
 
 
+def small_case_benchmark(stream, flush, steps=50, warmup=5):
+    """Small, latency-bound cases with the pass split over 1, 2 or 4 lanes
+    per particle (HR_FLAG_PASS_LANES2 / _LANES4): ms per step (graph without
+    timing events, L2 flushed between steps) and the pass's own duration
+    (in-graph events, a second case).  The 1,000-particle patch is this
+    step's floor: eight dependent kernels of one short wave each."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    cases = []
+    p, xy = workload(1e-3)
+    q = dict(p, Lx=0.04, W=0.025)
+    cases.append(("patch 40 x 25 mm, dx = 1 mm", q, casegen.fluid_lattice(
+        q["Lx"], q["W"], q["dx"], q["jitter"], q["seed"],
+        disk=(q["x_c0"], q["y_c0"], q["R_disk"])).astype(np.float32)))
+    q = casegen.config_adjoint()
+    cases.append(("150 x 150 mm, dx = 1 mm", q, casegen.fluid_lattice(
+        q["Lx"], q["W"], q["dx"], q["jitter"], q["seed"],
+        disk=(q["x_c0"], q["y_c0"], q["R_disk"])).astype(np.float32)))
+    cases.append(("300 x 150 mm, dx = 1 mm", p, xy))
+    p5, xy5 = workload(5e-4)
+    cases.append(("300 x 150 mm, dx = 0.5 mm", p5, xy5))
+    out = []
+    for name, q, x in cases:
+        row = {"case": name, "particles": int(x.shape[0])}
+        for lanes in (1, 2, 4):
+            with torch.cuda.stream(stream):
+                c = Case(q, x, stream=stream, lanes=lanes, probe_capacity=steps + warmup + 8)
+                t = Case(q, x, stream=stream, lanes=lanes, timing=True,
+                         probe_capacity=steps + warmup + 8)
+            c.run(warmup)
+            t.run(warmup)
+            c.sync()
+            t.sync()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            pt = []
+            for k in range(steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 0xFF)
+                    ev[k][0].record(stream)
+                    c.step()
+                    ev[k][1].record(stream)
+                    flush.fill_(k & 0xFF)
+                    t.step()
+                stream.synchronize()
+                pt.append(t.kernel_times()["pass"])
+            torch.cuda.synchronize()
+            row["lanes%d_ms_per_step" % lanes] = sum(a.elapsed_time(b) for a, b in ev) / steps
+            row["lanes%d_pass_us" % lanes] = 1e3 * statistics.mean(pt)
+            c.close()
+            t.close()
+        out.append(row)
+    return out
+
+
 def production_benchmark(stream):
     """The production runs: 300 x 150 mm at dx = 0.5 mm (180,000 particles),
     1 ms of simulated time at v0 = 900 and 600 m/s; wall clock of the whole
@@ -662,6 +717,9 @@ def run_only(args):
     stream = torch.cuda.Stream()
     if args.only == "sweep":
         out = sweep_benchmark(stream)
+    elif args.only == "small":
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = small_case_benchmark(stream, flush, steps=args.steps)
     elif args.only == "passvar":
         p, xy = workload(args.dx)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -708,7 +766,8 @@ def main():
     ap.add_argument("--no-scaling", action="store_true")
     ap.add_argument("--no-production", action="store_true")
     ap.add_argument("--no-passvar", action="store_true")
-    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar"),
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small"),
                     help="run one leg alone on the channel at --dx for --steps steps "
                          "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
@@ -820,6 +879,7 @@ def main():
     scaling = None if args.no_scaling else scaling_benchmark(stream, flush)
     production = None if args.no_production else production_benchmark(stream)
     passvar = None if args.no_passvar else pass_variant_benchmark(stream, xy, p, flush)
+    small = None if args.no_small else small_case_benchmark(stream, flush)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -869,6 +929,7 @@ def main():
         "size_sweep": scaling,
         "production": production,
         "pass_variants": passvar,
+        "small_cases": small,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

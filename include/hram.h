@@ -84,6 +84,14 @@ extern "C" {
                             with the tangent or reverse modes.  A cell denser
                             than the tiles hold makes the step return
                             HR_ERANGE */
+#define HR_FLAG_PASS_LANES2 32 /* interaction pass variant: each particle's
+                            candidates, pairs and ghosts split over 2 lanes
+                            (sums combined in a fixed order; results agree with
+                            the plain pass to rounding): a shorter critical
+                            path for small, latency-bound cases.  cell_factor
+                            >= 1, single-case steps; not with the tangent or
+                            reverse modes.  At most one pass-variant flag */
+#define HR_FLAG_PASS_LANES4 64 /* as HR_FLAG_PASS_LANES2 with 4 lanes */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)

@@ -73,13 +73,15 @@ class Case:
     which case the library allocates it.  ``stage`` picks the interaction
     pass variant: 0 reads candidates from global memory, 1 stages the
     candidates' positions in shared memory, 2 their whole records (the
-    results are identical).  ``newton3`` evaluates every fluid pair once
+    results are identical).  ``newton3`` evaluates every fluid pair once,
+    ``lanes`` (2 or 4) splits each particle's pass work over that many lanes
     (results equal to rounding).
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
                  probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
-                 tangent: bool = False, stage: int = 0, newton3: bool = False):
+                 tangent: bool = False, stage: int = 0, newton3: bool = False,
+                 lanes: int = 1):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -93,6 +95,9 @@ class Case:
         flags |= (0, _lib.HR_FLAG_STAGE_POS, _lib.HR_FLAG_STAGE_ALL)[stage]
         if newton3:
             flags |= _lib.HR_FLAG_NEWTON3
+        if lanes not in (1, 2, 4):
+            raise ValueError("lanes must be 1, 2 or 4")
+        flags |= {1: 0, 2: _lib.HR_FLAG_PASS_LANES2, 4: _lib.HR_FLAG_PASS_LANES4}[lanes]
         self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)

@@ -372,6 +372,15 @@ int validate(const hr_params *P, long long nf)
     if (P->Ng > 0 && !(P->R_disk > 0)) return HR_EINVAL;
     if (!(P->cell_factor >= 0.5)) return HR_EINVAL;
     if ((P->flags & HR_FLAG_STAGE_POS) && (P->flags & HR_FLAG_STAGE_ALL)) return HR_EINVAL;
+    // one pass variant at a time
+    {
+        const int v = P->flags & (HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL | HR_FLAG_NEWTON3 |
+                                  HR_FLAG_PASS_LANES2 | HR_FLAG_PASS_LANES4);
+        if (v & (v - 1)) return HR_EINVAL;
+        if ((P->flags & (HR_FLAG_PASS_LANES2 | HR_FLAG_PASS_LANES4)) &&
+            (P->cell_factor < 1.0 || (P->flags & HR_FLAG_TANGENT)))
+            return HR_EINVAL;
+    }
     // the Newton-3 pass: closure 0, the 3 x 3 stencil, no other pass variant
     if ((P->flags & HR_FLAG_NEWTON3) &&
         (P->closure != 0 || P->cell_factor < 1.0 ||
@@ -430,6 +439,7 @@ struct hr_case {
     bool tangent = false;
     int stage = 0;                // pass variant: 0 global loads, 1/2 staged candidates
     bool n3 = false;              // pass variant: each fluid pair evaluated once
+    int lanes = 1;                // pass variant: lanes per particle
     TBufs T{};
     int tpass_blocks = 0;
     void *t_base = nullptr;
@@ -569,6 +579,9 @@ void make_consts(hr_case *c)
     c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
     c->tpass_blocks = (int)((c->nf + kTPassThreads - 1) / kTPassThreads);
     K.n3 = (P.flags & HR_FLAG_NEWTON3) ? 1 : 0;
+    c->lanes = (P.flags & HR_FLAG_PASS_LANES4) ? 4 : (P.flags & HR_FLAG_PASS_LANES2) ? 2 : 1;
+    if (c->lanes > 1)   // kPassThreads / lanes particles per pass block
+        c->pass_blocks = (int)((c->nf * c->lanes + kPassThreads - 1) / kPassThreads);
     if (K.n3) {
         // row chunks of kN3Threads particles: at most one partial chunk per row
         c->pass_blocks = (int)((c->nf + kN3Threads - 1) / kN3Threads) + K.ncy + 1;
@@ -835,6 +848,10 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     if (c->n3) k_pass_n3<<<c->pass_blocks, kN3Threads, 0, s>>>(K, B, prime);
+    else if (c->lanes == 2 && paper) k_pass_lanes<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->lanes == 2) k_pass_lanes<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->lanes == 4 && paper) k_pass_lanes<1, 4><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+    else if (c->lanes == 4) k_pass_lanes<0, 4><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 1 && paper) k_pass_staged<1, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 1) k_pass_staged<0, 1><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->stage == 2 && paper) k_pass_staged<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
@@ -1913,7 +1930,8 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
     if (!c || !out || n < 3 || n_steps < 1 || checkpoint_every < 1) return HR_EINVAL;
     if (c->P.closure != 0 || c->P.dt_mode != 1 || c->P.motion < 0 || c->P.motion > 2 || c->tangent)
         return HR_EINVAL;
-    if (c->K.sr != 1 || c->n3) return HR_EINVAL;   // the reverse kernels take the plain pass
+    if (c->K.sr != 1 || c->n3 || c->lanes != 1)   // the records take the plain pass's sums
+        return HR_EINVAL;
     if (c->K.n_probes < 1 || n_steps > c->K.probe_cap) return HR_EINVAL;
     int st = device_status(c);
     if (st < 0) return st;
@@ -2110,6 +2128,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     for (int k = 0; k < n_cases; ++k) {
         // one closure per batch (the kernels are templated on it); no tangents
         if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->n3 ||
+            cases[k]->lanes != 1 ||
             cases[k]->K.closure != cases[0]->K.closure)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
@@ -2229,6 +2248,7 @@ int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
     };
     for (int k = 0; k < n_cases; ++k) {
         if (!cases[k] || cases[k]->sticky < 0 || cases[k]->tangent || cases[k]->n3 ||
+            cases[k]->lanes != 1 ||
             cases[k]->K.closure != cases[0]->K.closure || cases[k]->K.sr != 1)
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);

@@ -500,9 +500,12 @@ __device__ inline void kinematics(const Consts &K, double t, double *xo, double 
 // (R = K.sr) is 2R+1 contiguous row ranges [start(row, cx-R),
 // start(row, cx+R+1)) of the sorted arrays.  f(j) is called for every
 // candidate j.
+// (lane, lanes: the candidates lane, lane + lanes, ... of each row, for a
+// particle whose work is split over several lanes.)
 template <class F>
 __device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c,
-                                                     int limit, int *status, F &&f)
+                                                     int limit, int *status, F &&f, int lane = 0,
+                                                     int lanes = 1)
 {
     const int R = K.sr;
 #pragma unroll 1
@@ -511,7 +514,7 @@ __device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int 
         if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, status)) continue;
         const int a = start[row - R], b = start[row + R + 1];
         if (kChecked && !row_ok(K, row, a, b, limit, status)) continue;
-        for (int j = a; j < b; ++j) f(j);
+        for (int j = a + lane; j < b; j += lanes) f(j);
     }
 }
 
@@ -556,15 +559,16 @@ __device__ __forceinline__ DiskArc disk_arc(const Consts &K, float x, float y, f
 
 // f(k) for the ghosts of the arc, in ascending k.
 template <class F>
-__device__ __forceinline__ void for_disk_arc(const Consts &K, const DiskArc &A, int *status, F &&f)
+__device__ __forceinline__ void for_disk_arc(const Consts &K, const DiskArc &A, int *status, F &&f,
+                                             int lane = 0, int lanes = 1)
 {
     if (kChecked && !hr_ok(0 <= A.a0 && A.a0 <= A.a1 && A.a1 <= K.ng && 0 <= A.b0 &&
                            A.b0 <= A.b1 && A.b1 <= K.ng, status))
         return;
 #pragma unroll 1
-    for (int k = A.a0; k < A.a1; ++k) f(k);
+    for (int k = A.a0 + lane; k < A.a1; k += lanes) f(k);
 #pragma unroll 1
-    for (int k = A.b0; k < A.b1; ++k) f(k);
+    for (int k = A.b0 + lane; k < A.b1; k += lanes) f(k);
 }
 
 // ----------------------------------------------------- a2: drift and key
@@ -1435,12 +1439,12 @@ __device__ __forceinline__ void pass_fluid_staged(const Consts &K, const Bufs &B
     }
 }
 
-// Ghost neighbours and the epilogue of particle i (inside the box), its
-// fluid sums already in A.
+// The wall and disk ghost neighbours of a particle (inside the box) into A,
+// their forces into the block partials (split over lanes as for_fluid_candidates).
 template <int CL>
-__device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int i, float2 ri,
-                                            float2 vi, float4 ai, float2 rd, int c, float dt,
-                                            int prime, const Self &I, Acc &A, PassPart &P)
+__device__ __forceinline__ void pass_ghosts(const Consts &K, const Bufs &B, float2 ri, int c,
+                                            const Self &I, Acc &A, PassPart &P, int lane = 0,
+                                            int lanes = 1)
 {
     // wall ghosts (static cell list)
     if (K.nw > 0) {
@@ -1456,7 +1460,7 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
                 const float2 e = __ldg(&B.gw_nrm[k]);
                 P.fw -= f.x * e.x + f.y * e.y;
             }
-        });
+        }, lane, lanes);
     }
     // disk ghosts (the ring, only near the disk)
     if (K.ng > 0) {
@@ -1473,11 +1477,19 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
                                                 K.disk_over_m, false, A);
                 P.fdx += f.x;
                 P.fdy += f.y;
-            });
+            }, lane, lanes);
             const float ddx = ri.x - xc, ddy = ri.y - yc;
-            P.npen += ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
+            if (lane == 0) P.npen += ddx * ddx + ddy * ddy < K.R2 ? 1 : 0;
         }
     }
+}
+
+// The epilogue of particle i (inside the box), its sums complete in A.
+template <int CL>
+__device__ __forceinline__ void pass_close(const Consts &K, const Bufs &B, int i, float2 vi,
+                                           float4 ai, float2 rd, float dt, int prime, Acc &A,
+                                           PassPart &P)
+{
     const float ax = fmaf(K.m, A.a.x, K.gx), ay = fmaf(K.m, A.a.y, K.gy);
     float2 vnew;
     if constexpr (CL == 1) {
@@ -1507,6 +1519,17 @@ __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int 
     B.st_X[i] = make_float2(K.m * A.X.x, K.m * A.X.y);
     P.vmax = fmaxf(P.vmax, sqrtf(vnew.x * vnew.x + vnew.y * vnew.y));
     P.diss += -K.m * K.m * (vi.x * A.av.x + vi.y * A.av.y);
+}
+
+// Ghost neighbours and the epilogue of particle i (inside the box), its
+// fluid sums already in A.
+template <int CL>
+__device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int i, float2 ri,
+                                            float2 vi, float4 ai, float2 rd, int c, float dt,
+                                            int prime, const Self &I, Acc &A, PassPart &P)
+{
+    pass_ghosts<CL>(K, B, ri, c, I, A, P);
+    pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
 }
 
 // A frozen particle (outside the box) keeps its state, takes part in nothing.
@@ -1624,6 +1647,96 @@ __device__ __forceinline__ void b_pass_staged(const Consts &K, const Bufs &B, co
         }
     }
     pass_block_partials<kPassThreads>(B, bx, P);
+}
+
+// The pass with each particle's work split over L consecutive lanes (a
+// measured variant for small cases, HR_FLAG_PASS_LANES2 / _LANES4).  The
+// candidates of the three stencil rows, in blocks of kMaskChunk taken in
+// order, go to the lanes in turn (block g to lane g mod L); each lane
+// evaluates the pairs of its blocks, then its share of the wall and disk
+// ghosts, and the L partial sums are combined by a butterfly of shuffles
+// (every lane ends with the same sums); the first lane closes the particle.
+// The candidates and the pair arithmetic are the plain pass's; only the
+// order of the sums differs, so results agree with it to rounding and runs
+// are reproducible.
+template <int L>
+__device__ __forceinline__ float lane_group_sum(float v)
+{
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int CL, int L>
+__global__ void __launch_bounds__(kPassThreads) k_pass_lanes(Consts K, Bufs B, int prime)
+{
+    constexpr int PPB = kPassThreads / L;
+    const int lane = threadIdx.x % L;
+    const int i = blockIdx.x * PPB + threadIdx.x / L;
+    const float dt = prime ? 0.0f : B.S->dt_f;
+    PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+    bool live = false;
+    float2 ri = make_float2(0.f, 0.f), vi = make_float2(0.f, 0.f), rd = make_float2(0.f, 0.f);
+    float4 ai = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < K.nf) {
+        ri = B.s_pos[i];
+        vi = B.s_vel[i];
+        ai = B.s_aux[i];
+        rd = B.s_rd[i];
+        if (outside_box(K, ri.x, ri.y)) {
+            if (lane == 0) pass_frozen<CL>(B, i, vi, rd);
+        } else {
+            live = true;
+        }
+    }
+    if (live) {
+        const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, CL == 1 ? K.c_av : ai.w};
+        const int c = cell_of(K, ri.x, ri.y);
+        auto fluid_pair = [&](int j) {
+            const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
+            const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
+            const float4 aj = HR_DYNAMIC_LOAD(&B.s_aux[j]);
+            pair_terms<CL>(K, I, rj, vj, fmaf(K.rho0, aj.x, K.rho0), aj.z,
+                           CL == 1 ? K.c_av : aj.w, 1.0f, true, A);
+        };
+        const int base0 = B.cell_start[c - K.ncx - 1], base1 = B.cell_start[c - 1],
+                  base2 = B.cell_start[c + K.ncx - 1];
+        const int cnt0 = B.cell_start[c - K.ncx + 2] - base0, cnt1 = B.cell_start[c + 2] - base1,
+                  cnt2 = B.cell_start[c + K.ncx + 2] - base2;
+        bool ok = true;
+        if (kChecked)
+            ok = row_ok(K, c - K.ncx, base0, base0 + cnt0, K.nf, &B.S->status) &&
+                 row_ok(K, c, base1, base1 + cnt1, K.nf, &B.S->status) &&
+                 row_ok(K, c + K.ncx, base2, base2 + cnt2, K.nf, &B.S->status);
+        const int n0 = (cnt0 + kMaskChunk - 1) / kMaskChunk, n1 = (cnt1 + kMaskChunk - 1) / kMaskChunk,
+                  n2 = (cnt2 + kMaskChunk - 1) / kMaskChunk;
+#pragma unroll 1
+        for (int g = lane; ok && g < n0 + n1 + n2; g += L) {
+            const int r = g < n0 ? 0 : (g < n0 + n1 ? 1 : 2);
+            const int k = r == 0 ? g : (r == 1 ? g - n0 : g - n0 - n1);
+            const int bs = r == 0 ? base0 : (r == 1 ? base1 : base2);
+            const int cn = r == 0 ? cnt0 : (r == 1 ? cnt1 : cnt2);
+            const int b0 = bs + k * kMaskChunk;
+            unsigned m = support_mask(B.s_pos, b0, min(cn - k * kMaskChunk, kMaskChunk), ri, K.s2);
+            if (i >= b0 && i < b0 + kMaskChunk) m &= ~(1u << (i - b0));
+            while (m) {
+                const int j = b0 + __ffs(m) - 1;
+                m &= m - 1u;
+                fluid_pair(j);
+            }
+        }
+        pass_ghosts<CL>(K, B, ri, c, I, A, P, lane, L);
+    }
+    A.a.x = lane_group_sum<L>(A.a.x);
+    A.a.y = lane_group_sum<L>(A.a.y);
+    A.av.x = lane_group_sum<L>(A.av.x);
+    A.av.y = lane_group_sum<L>(A.av.y);
+    A.X.x = lane_group_sum<L>(A.X.x);
+    A.X.y = lane_group_sum<L>(A.X.y);
+    A.dr = lane_group_sum<L>(A.dr);
+    if (live && lane == 0) pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
+    pass_block_partials<kPassThreads>(B, blockIdx.x, P);
 }
 
 // ----------------------------------- a6, a7: probes, accumulators, gate

@@ -191,6 +191,15 @@ def test_invalid_parameters_rejected():
         with pytest.raises(HramError) as e:
             Case(dict(p, **kw), xy, stage=stage)
         assert e.value.code == _lib.HR_EINVAL
+    # two pass variants at once; lanes or Newton-3 on cells of side h
+    for kw in (dict(stage=1, newton3=True), dict(lanes=2, newton3=True), dict(stage=2, lanes=4)):
+        with pytest.raises(HramError) as e:
+            Case(p, xy, **kw)
+        assert e.value.code == _lib.HR_EINVAL
+    for kw in (dict(lanes=2), dict(newton3=True)):
+        with pytest.raises(HramError) as e:
+            Case(dict(p, cell_factor=0.5), xy, **kw)
+        assert e.value.code == _lib.HR_EINVAL
 
 
 def test_nan_state_reported():

@@ -185,6 +185,50 @@ def test_five_by_five_stencil_one_step_and_window(closure):
     assert gated >= 1
 
 
+@pytest.mark.parametrize("closure", [0, 1])
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_multi_lane_pass_against_oracle(lanes, closure):
+    # each particle's candidates, pairs and ghosts split over 2 or 4 lanes:
+    # one step from a perturbed state (with the disk ring and the walls), a
+    # 150-step window of the impact, and two runs bit for bit
+    p, xy = impact_case(closure=closure)
+    vel, rho = perturbed(p, xy)
+    g, o = both(p, xy, vel, None if closure else rho, lanes=lanes)
+    dt = o.scalars()["dt"]
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert_p_close("lanes=%d closure=%d" % (lanes, closure), p, sg["p"], o, dt)
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    vscale = max(np.abs(fo["vel"]).max(), 1.0)
+    assert np.abs(sg["vel"] - fo["vel"]).max() <= 1e-4 * vscale
+    p2, xy2 = impact_case(closure=closure)
+    p2["probes"] = list(p2["probes"]) + [(0.030, 0.0), (0.020, 0.030)]
+    g, o = both(p2, xy2, lanes=lanes)
+    g.run(150)
+    o.run(150)
+    pg, po = g.probe_pressure(), o.probes()[0]
+    floor = 1e-5 * p2["rho0"] * p2["c0"] ** 2 if closure else 0.0
+    strong = 1e7 if closure else 1e6
+    gated = 0
+    for k in range(po.shape[1]):
+        err = np.sqrt(np.mean((pg[:, k] - po[:, k]) ** 2))
+        if closure:
+            assert err <= 1e-3 * np.sqrt(np.mean(po[:, k] ** 2)) + floor, k
+        if np.abs(po[:, k]).max() > strong:
+            assert rel_l2(pg[:, k], po[:, k]) <= 1e-3, k
+            gated += 1
+    assert gated >= 1
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("KE", "dissipation", "wall_impulse"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-3, abs=1e-9), k
+    b = Case(p2, xy2, lanes=lanes)
+    b.run(150)
+    assert np.array_equal(g.get_state()["rho"], b.get_state()["rho"])
+    assert np.array_equal(pg, b.probe_pressure())
+
+
 def test_newton3_pass_against_oracle():
     # every fluid pair evaluated once, both sides summed in a fixed order:
     # one step from a perturbed state, a 250-step window of the impact, and
