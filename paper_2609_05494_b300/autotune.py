@@ -1,6 +1,6 @@
 """Autotuner for single cases and batched sweeps.
 
-Three choices are tuned by timing them on the device, not by a model:
+Four choices are tuned by timing them on the device, not by a model:
 
 * the cell grid of each case: the cell side as a multiple of the support
   2h (``cell_factor``).  Larger cells mean more candidates per particle in
@@ -10,6 +10,7 @@ Three choices are tuned by timing them on the device, not by a model:
 * the block schedule of a batch: the order in which the blocks of each
   batched launch visit the cases (case after case, round robin, largest
   case first);
+* the lanes per particle of a single case's interaction pass (1, 2 or 4);
 * the block counts of a persistent batch: how many of the resident blocks
   each case gets.  Candidates share the capacity in proportion to
   particles^a x (estimated steps)^b; the estimated steps of a case are its
@@ -57,6 +58,27 @@ def tune_cell_factor(params: dict, xy, candidates=CELL_FACTORS, steps: int = 20,
         timings[float(f)] = time_case(p, xy, steps=steps, stream=stream)
     best = min(timings, key=timings.get)
     return best, timings
+
+
+def tune_pass_lanes(params: dict, xy, candidates=(1, 2, 4), steps: int = 20,
+                    stream=None) -> tuple[int, dict]:
+    """Lanes per particle of the interaction pass for a single case: the
+    fastest of ``candidates`` and every candidate's ms per step.  More lanes
+    shorten the pass's critical path in small, latency-bound cases and cost
+    instructions in large ones."""
+    import torch
+    timings = {}
+    for lanes in candidates:
+        with Case(params, xy, stream=stream, lanes=lanes) as c:
+            c.run(3)
+            a, b = _events()
+            s = torch.cuda.current_stream() if stream is None else stream
+            a.record(s)
+            c.run(steps)
+            b.record(s)
+            b.synchronize()
+            timings[int(lanes)] = a.elapsed_time(b) / steps
+    return min(timings, key=timings.get), timings
 
 
 def tune_sweep(specs, classes: int = 3, stream=None):

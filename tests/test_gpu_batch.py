@@ -252,3 +252,10 @@ def test_persistent_autotuner_block_counts():
     assert len(blocks) == 4 and blocks.min() >= 1
     assert blocks.sum() <= report["capacity"]
     assert len(report["candidates"]) == len(autotune.BLOCK_WEIGHTS)
+
+
+def test_pass_lanes_autotuner():
+    p, xy = impact_case()
+    best, timings = autotune.tune_pass_lanes(p, xy, steps=5)
+    assert best in (1, 2, 4) and set(timings) == {1, 2, 4}
+    assert all(v > 0 for v in timings.values())
