@@ -23,6 +23,20 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// A named NVTX range over one C-ABI call (a profiler's timeline shows the
+// library's calls; the kernels inside carry their own names).  Without a
+// tool attached the push and pop are no-ops.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+
 using namespace hr;
 
 namespace {
@@ -1429,6 +1443,7 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
                  const float *rho, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
                  hr_case **out)
 {
+    const NvtxRange nvtx_range("hr_init_case");
     if (!out) return HR_EINVAL;
     *out = nullptr;
     if (!xy) return HR_EINVAL;
@@ -1495,6 +1510,7 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
 
 int hr_step(hr_case *c)
 {
+    const NvtxRange nvtx_range("hr_step");
     if (!c || !c->exec) return HR_EINVAL;
     if (c->sticky < 0) return c->sticky;
     if (cudaGraphLaunch(c->exec, c->stream) != cudaSuccess) return c->sticky = HR_ECUDA;
@@ -1538,6 +1554,7 @@ static int run_steps(hr_case *c, int64_t k)
 
 int hr_run(hr_case *c, int64_t n_steps, double t_end)
 {
+    const NvtxRange nvtx_range("hr_run");
     if (!c) return HR_EINVAL;
     if (!c->exec) return HR_EINVAL;
     if (t_end <= 0.0) {
@@ -1626,6 +1643,7 @@ int hr_diag_history(hr_case *c, double *host_out, int64_t cap_rows, int64_t *n_r
 
 int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_t cap)
 {
+    const NvtxRange nvtx_range("hr_get_state");
     if (!c) return HR_EINVAL;
     if (cap < c->nf) return HR_ERANGE;
     const size_t n = (size_t)c->nf;
@@ -1659,6 +1677,7 @@ int hr_get_energy(hr_case *c, float *e, float *de, int64_t cap)
 
 int hr_set_state(hr_case *c, const float *xy, const float *vel, const float *rho, int64_t n)
 {
+    const NvtxRange nvtx_range("hr_set_state");
     if (!c || !xy || n != c->nf) return HR_EINVAL;
     const int s0 = device_status(c);
     if (s0 == HR_ECUDA) return s0;
@@ -1792,6 +1811,7 @@ int hr_kernel_times(hr_case *c, float *ms, int n)
 // Checkpoint file: magic, counts, params, scalars, state in ID order, probes.
 int hr_save_state(hr_case *c, const char *path)
 {
+    const NvtxRange nvtx_range("hr_save_state");
     if (!c || !path) return HR_EINVAL;
     const int st = device_status(c);
     if (st < 0) return st;
@@ -1851,6 +1871,7 @@ int hr_save_state(hr_case *c, const char *path)
 
 int hr_load_state(hr_case *c, const char *path)
 {
+    const NvtxRange nvtx_range("hr_load_state");
     if (!c || !path || c->tangent) return HR_EINVAL;
     device_status(c);
     FILE *f = std::fopen(path, "rb");
@@ -1927,6 +1948,7 @@ int hr_tangent_outputs(hr_case *c, double *out, int n)
 
 int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, double *out, int n)
 {
+    const NvtxRange nvtx_range("hr_adjoint_forward");
     if (!c || !out || n < 3 || n_steps < 1 || checkpoint_every < 1) return HR_EINVAL;
     if (c->P.closure != 0 || c->P.dt_mode != 1 || c->P.motion < 0 || c->P.motion > 2 || c->tangent)
         return HR_EINVAL;
@@ -1998,6 +2020,7 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
 
 int hr_adjoint_backward(hr_case *c, double *out, int n)
 {
+    const NvtxRange nvtx_range("hr_adjoint_backward");
     if (!c || !out || n < 6 || !c->adj || !c->adj->forward_done) return HR_EINVAL;
     if (c->sticky < 0) return c->sticky;
     AdjCtx *a = c->adj;
@@ -2359,6 +2382,7 @@ static int persist_run(hr_batch *b, int64_t max_steps)
 
 int hr_batch_step(hr_batch *b)
 {
+    const NvtxRange nvtx_range("hr_batch_step");
     if (b && b->persistent) {
         const int rc = persist_run(b, 1);
         if (rc == HR_OK) b->steps++;
@@ -2383,6 +2407,7 @@ int hr_batch_done(hr_batch *b, int *n_done)
 
 int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done)
 {
+    const NvtxRange nvtx_range("hr_batch_run");
     if (!b) return HR_EINVAL;
     const int n = (int)b->cases.size();
     int64_t done_steps = 0;
