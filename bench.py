@@ -894,6 +894,8 @@ def main():
     achieved_tf = flops / t_pass / 1e12
     hbm_achieved = ALG_BYTES_PER_PARTICLE * n / t_pass / 1e9
     traffic = read_traffic(kernel_source_hash())
+    from paper_2609_05494_b300 import fp32_rate
+    fma = {"scalar_tflops": fp32_rate(False, stream), "packed_f32x2_tflops": fp32_rate(True, stream)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -911,6 +913,7 @@ def main():
                      "traffic": traffic,
                      "peak_source": "FP32 from unit counts: %d SM (as the device reports) x "
                                     "128 lanes x 2 x %.0f MHz" % (n_sm, pk.get("sm_max_mhz", 2032.0)),
+                     "fp32_fma_measured": fma,
                      "flop_per_launch": flops, "flop_per_particle": FLOP_PER_PARTICLE,
                      "pair_terms_only": {"pairs": pairs_fluid_rows,
                                          "flop_per_pair": FLOP_PER_PAIR,

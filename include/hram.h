@@ -408,6 +408,16 @@ int hr_adjoint_backward(hr_case *c, double *out, int n);
 #define HR_STATIC_NEIGHBOR_MAX (1 << 21)
 int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap);
 
+/* FP32 FMA rate of the current device in TFLOP/s (an FMA counted as two
+ * operations), measured: a kernel of 16 independent FMA chains per thread on
+ * 8 blocks of 256 threads per multiprocessor, as scalar fma.rn.f32 (packed
+ * = 0) or as packed fma.rn.f32x2 (packed = 1), timed with CUDA events on
+ * cuda_stream (NULL: the default stream).  The paper has no counterpart; the
+ * interaction pass (Section 2.2) is an FP32 gather whose roofline is this
+ * rate.  Allocates and frees a small device buffer; synchronises the
+ * stream.  *tflops = 0 and a negative status on failure. */
+int hr_fp32_rate(int packed, void *cuda_stream, double *tflops);
+
 void hr_destroy(hr_case *c);
 const char *hr_status_str(int status);
 

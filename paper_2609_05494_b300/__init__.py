@@ -6,6 +6,6 @@ runs in the CUDA kernels of ``libhram.so`` behind the C-ABI of
 include/hram.h; this package is its Python binding.
 """
 from .api import (Batch, Case, DIAG_FIELDS, KERNEL_GROUPS, SCALAR_FIELDS, TANGENT_PARAMS,  # noqa: F401
-                  make_params)
+                  fp32_rate, make_params)
 from .grad import jacobian, peak_and_impulse  # noqa: F401
 from ._lib import HramError, lib  # noqa: F401

@@ -48,7 +48,7 @@ EXPORTS = (
     "hr_adjoint_forward", "hr_adjoint_backward",
     "hr_neighbor_counts_static", "hr_batch_create", "hr_batch_step", "hr_batch_run",
     "hr_batch_done", "hr_batch_destroy", "hr_batch_create_persistent", "hr_persist_capacity",
-    "hr_destroy", "hr_status_str",
+    "hr_fp32_rate", "hr_destroy", "hr_status_str",
 )
 HR_STATIC_NEIGHBOR_MAX = 1 << 21
 
@@ -125,6 +125,7 @@ def lib() -> C.CDLL:
     L.hr_batch_create.argtypes = [vp, C.c_int, C.c_double, C.c_int, vp, P(vp)]
     L.hr_batch_create_persistent.argtypes = [vp, C.c_int, C.c_double, vp, i64, vp, P(vp)]
     L.hr_persist_capacity.argtypes = [C.c_int, P(C.c_int32)]
+    L.hr_fp32_rate.argtypes = [C.c_int, vp, P(C.c_double)]
     L.hr_batch_step.argtypes = [vp]
     L.hr_batch_run.argtypes = [vp, i64, P(i64)]
     L.hr_batch_done.argtypes = [vp, P(C.c_int)]

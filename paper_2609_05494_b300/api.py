@@ -370,3 +370,12 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def fp32_rate(packed: bool = False, stream=None) -> float:
+    """Measured FP32 FMA rate of the current device, TFLOP/s (FMA = 2): the
+    ALU roof of the interaction pass (scalar or packed f32x2 FMAs)."""
+    out = C.c_double(0.0)
+    check(lib().hr_fp32_rate(1 if packed else 0, _stream_handle(stream), C.byref(out)),
+          "hr_fp32_rate")
+    return out.value

@@ -247,6 +247,41 @@ __global__ void k_wall_keys(Consts K, const float2 *pos, int n, int *key)
 // directly; it uses the per-device address from cudaGetSymbolAddress.
 __device__ __align__(256) int g_static_neighbor_counts[HR_STATIC_NEIGHBOR_MAX];
 
+// FP32 FMA rate of the device (hr_fp32_rate): every thread runs 16
+// independent FMA chains for iters iterations, as scalar fma.rn.f32 or as
+// eight packed fma.rn.f32x2 pairs; the chains' sums are stored so none of it
+// is dead code.
+constexpr int kFmaChains = 16;
+__global__ void __launch_bounds__(256) k_fma_rate(float *out, int iters, int packed)
+{
+    float v[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) v[k] = threadIdx.x * 1e-6f + k * 1e-3f;
+    const float b = 0.999999f, c = 1e-7f;
+    if (packed) {
+#pragma unroll 4
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < kFmaChains; k += 2) {
+                const float2 r = p2_fma(make_float2(v[k], v[k + 1]), make_float2(b, b),
+                                        make_float2(c, c));
+                v[k] = r.x;
+                v[k + 1] = r.y;
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < kFmaChains; ++k) v[k] = fmaf(v[k], b, c);
+        }
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) sum += v[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 // Count-only variant of k_neighbors that writes by global point index (fluid
 // ID, then wall-ghost ID, then disk ghost), so no host-side reordering is
 // needed.  Same candidate loops and predicate.
@@ -2061,6 +2096,45 @@ int hr_adjoint_backward(hr_case *c, double *out, int n)
         out[3 * q + 2] = sc[ASC_TAU + q];
     }
     return st;
+}
+
+int hr_fp32_rate(int packed, void *cuda_stream, double *tflops)
+{
+    if (!tflops) return HR_EINVAL;
+    *tflops = 0.0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HR_ECUDA;
+    const int threads = 256, blocks = sms * 8, iters = 1 << 14;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = HR_OK;
+    if (cudaMalloc(&out, (size_t)blocks * threads * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return HR_ENOMEM;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = HR_ECUDA;
+    } else {
+        k_fma_rate<<<blocks, threads, 0, s>>>(out, iters / 16, packed ? 1 : 0);   // warm-up
+        cudaEventRecord(e0, s);
+        k_fma_rate<<<blocks, threads, 0, s>>>(out, iters, packed ? 1 : 0);
+        cudaEventRecord(e1, s);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.0f)) {
+            rc = HR_ECUDA;
+        } else {
+            const double flop = 2.0 * kFmaChains * (double)iters * blocks * threads;
+            *tflops = flop / (ms * 1e-3) / 1e12;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    return rc;
 }
 
 int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)

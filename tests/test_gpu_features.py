@@ -249,3 +249,15 @@ def test_two_way_coupling_matches_oracle():
         assert sg[k] == pytest.approx(so[k], rel=1e-5), k
     assert sg["aproj"] == pytest.approx(so["aproj"], rel=1e-3)
     assert np.abs(g.get_state()["rho"] / o.fluid()["rho"] - 1).max() <= 1e-4
+
+
+def test_fp32_rate_measurement():
+    # the measured FMA rate is positive and within the unit-count bound
+    # (SMs x 128 lanes x 2 x the maximum clock, with a margin for the
+    # packed form, whose rate the measurement settles)
+    from paper_2609_05494_b300 import fp32_rate
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    bound = sms * 128 * 2 * 2.2e9 / 1e12
+    for packed in (False, True):
+        r = fp32_rate(packed)
+        assert 0.05 * bound < r < 2.2 * bound, (packed, r, bound)
