@@ -2163,8 +2163,10 @@ int hr_neighbor_counts_static(hr_case *c, int32_t *host_counts, int64_t cap)
 
 namespace {
 
-enum BatchKernel { BK_KIN, BK_DRIFT, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN, BK_DENS };
-constexpr int kBatchKernels = 9;
+// BK_PASS maps the cases on the 3 x 3 stencil, BK_PASS5 those on the 5 x 5
+enum BatchKernel { BK_KIN, BK_DRIFT, BK_APPLY, BK_SLOT, BK_RANK, BK_GHOST, BK_PASS, BK_FIN, BK_DENS,
+                   BK_PASS5 };
+constexpr int kBatchKernels = 10;
 
 __global__ void k_batch_count_done(const Bufs *Bs, int n, int *out)
 {
@@ -2197,13 +2199,19 @@ int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
         CK(cudaStreamWaitEvent(s, b->join, 0));
         kb_density<<<b->nblocks[BK_DENS], 256, 0, s>>>(K, B, b->map[BK_DENS]);
         kb_ghost<1><<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
-        kb_pass<1><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        if (b->nblocks[BK_PASS])
+            kb_pass<1, 1><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        if (b->nblocks[BK_PASS5])
+            kb_pass<1, 2><<<b->nblocks[BK_PASS5], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS5]);
         kb_finalize<1><<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
     } else {
         kb_rank_scatter<0><<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
         CK(cudaStreamWaitEvent(s, b->join, 0));
         kb_ghost<0><<<b->nblocks[BK_GHOST], kGhostWarps * 32, 0, s>>>(K, B, b->map[BK_GHOST]);
-        kb_pass<0><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        if (b->nblocks[BK_PASS])
+            kb_pass<0, 1><<<b->nblocks[BK_PASS], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS]);
+        if (b->nblocks[BK_PASS5])
+            kb_pass<0, 2><<<b->nblocks[BK_PASS5], kPassThreads, 0, s>>>(K, B, b->map[BK_PASS5]);
         kb_finalize<0><<<b->nblocks[BK_FIN], kFinalizeThreads, 0, s>>>(K, B, b->map[BK_FIN]);
     }
     CK(cudaGetLastError());
@@ -2244,9 +2252,10 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     auto nblk = [&](int k, int q) {
         const hr_case *c = cases[k];
         const int fin = 4 + c->K.n_probes;  // four reduction blocks, one per probe
+        const int p3 = c->K.sr == 1 ? c->pass_blocks : 0, p5 = c->K.sr == 2 ? c->pass_blocks : 0;
         const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->drift_blocks,
-                                       c->drift_blocks, c->ghost_blocks, c->pass_blocks, fin,
-                                       c->drift_blocks};
+                                       c->drift_blocks, c->ghost_blocks, p3, fin,
+                                       c->drift_blocks, p5};
         return nb[q];
     };
     for (int q = 0; q < kBatchKernels; ++q) {

@@ -277,12 +277,16 @@ __device__ __forceinline__ bool in_support2(float2 ri, float2 rj, float s2)
     return __fadd_rn(q.x, q.y) < s2;
 }
 
+// The cell of a point, clamped to keep its stencil inside the grid.  R: the
+// stencil reach when the caller knows it at compile time, 0 to read K.sr.
+template <int R = 0>
 __device__ __forceinline__ int cell_of(const Consts &K, float x, float y)
 {
+    const int r = R ? R : K.sr;
     int cx = __float2int_rd(__fmul_rn(__fsub_rn(x, K.x0), K.inv_dc));
     int cy = __float2int_rd(__fmul_rn(__fsub_rn(y, K.y0), K.inv_dc));
-    cx = min(max(cx, K.sr), K.ncx - 1 - K.sr);
-    cy = min(max(cy, K.sr), K.ncy - 1 - K.sr);
+    cx = min(max(cx, r), K.ncx - 1 - r);
+    cy = min(max(cy, r), K.ncy - 1 - r);
     return cy * K.ncx + cx;
 }
 
@@ -501,13 +505,14 @@ __device__ inline void kinematics(const Consts &K, double t, double *xo, double 
 // start(row, cx+R+1)) of the sorted arrays.  f(j) is called for every
 // candidate j.
 // (lane, lanes: the candidates lane, lane + lanes, ... of each row, for a
-// particle whose work is split over several lanes.)
-template <class F>
+// particle whose work is split over several lanes.  RC: the reach when known
+// at compile time, else 0.)
+template <int RC = 0, class F>
 __device__ __forceinline__ void for_fluid_candidates(const Consts &K, const int *start, int c,
                                                      int limit, int *status, F &&f, int lane = 0,
                                                      int lanes = 1)
 {
-    const int R = K.sr;
+    const int R = RC ? RC : K.sr;
 #pragma unroll 1
     for (int dy = -R; dy <= R; ++dy) {
         const int row = c + dy * K.ncx;
@@ -1441,14 +1446,14 @@ __device__ __forceinline__ void pass_fluid_staged(const Consts &K, const Bufs &B
 
 // The wall and disk ghost neighbours of a particle (inside the box) into A,
 // their forces into the block partials (split over lanes as for_fluid_candidates).
-template <int CL>
+template <int CL, int R = 0>
 __device__ __forceinline__ void pass_ghosts(const Consts &K, const Bufs &B, float2 ri, int c,
                                             const Self &I, Acc &A, PassPart &P, int lane = 0,
                                             int lanes = 1)
 {
     // wall ghosts (static cell list)
     if (K.nw > 0) {
-        for_fluid_candidates(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
+        for_fluid_candidates<R>(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
             const float2 rg = __ldg(&B.gw_pos[k]);
             if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
             const float4 ag = B.g_aux[k];
@@ -1523,12 +1528,12 @@ __device__ __forceinline__ void pass_close(const Consts &K, const Bufs &B, int i
 
 // Ghost neighbours and the epilogue of particle i (inside the box), its
 // fluid sums already in A.
-template <int CL>
+template <int CL, int R = 0>
 __device__ __forceinline__ void pass_finish(const Consts &K, const Bufs &B, int i, float2 ri,
                                             float2 vi, float4 ai, float2 rd, int c, float dt,
                                             int prime, const Self &I, Acc &A, PassPart &P)
 {
-    pass_ghosts<CL>(K, B, ri, c, I, A, P);
+    pass_ghosts<CL, R>(K, B, ri, c, I, A, P);
     pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
 }
 
@@ -1560,10 +1565,10 @@ __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int 
     const float ci = CL == 1 ? K.c_av : ai.w;
     const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
     Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
-    const int c = cell_of(K, ri.x, ri.y);
+    const int c = cell_of<R>(K, ri.x, ri.y);
     if (R == 2 || (R == 0 && K.sr == 2)) pass_fluid5<CL>(K, B, i, ri, c, I, A);
     else pass_fluid<CL>(K, B, i, ri, c, I, A);
-    pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
+    pass_finish<CL, R>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
 }
 
 // Block partials of a pass block: FP32 within the warp, then a fixed-order
@@ -2134,14 +2139,16 @@ __global__ void __launch_bounds__(kGhostWarps * 32) kb_ghost(const Consts *Ks, c
     b_ghost<CL>(K, B, m.local, m.nlocal);
 }
 
-template <int CL>
+// R: the stencil reach of every case on the map (the batch launches one
+// map per reach).
+template <int CL, int R>
 __global__ void __launch_bounds__(kPassThreads) kb_pass(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
 {
     __shared__ Consts K;
     __shared__ Bufs B;
     __shared__ BatchBlock m;
     if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_pass<CL>(K, B, m.local, m.nlocal, 0);
+    b_pass<CL, R>(K, B, m.local, m.nlocal, 0);
 }
 
 template <int CL>
