@@ -638,6 +638,8 @@ void make_consts(hr_case *c)
     }
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
+    // the sort's overflow list: particles past the kBucket of their cell
+    K.ovf_cap = (int)std::max<long long>(1024, c->nf / 8);
     K.closure = P.closure;
     const double sd = 10.0 / (7.0 * M_PI * h * h);
     K.cub_sd = (float)sd;
@@ -655,7 +657,7 @@ void make_consts(hr_case *c)
 
 struct Offsets {
     size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_a, st_D, st_X, u_pos, u_vel,
-        u_id, u_key, u_slot, cell_count, cell_start, tile_sum, perm_tmp, gw_pos, gw_nrm,
+        u_id, u_key, cell_count, cell_start, tile_sum, bucket, ovf, ovf_count, gw_pos, gw_nrm,
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
         probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
         fin_part, fin_vmax, fin_npen, fin_ticket;
@@ -687,11 +689,12 @@ Offsets plan(const hr_case *c)
     o.u_vel = L.add(n * 8);
     o.u_id = L.add(n * 4);
     o.u_key = L.add(n * 4);
-    o.u_slot = L.add(n * 4);
     o.cell_count = L.add((nc + 1) * 4);
     o.cell_start = L.add((nc + 2) * 4);
     o.tile_sum = L.add((size_t)c->n_tiles * 4);
-    o.perm_tmp = L.add(n * 4);
+    o.bucket = L.add((nc + 1) * kBucket * 4);
+    o.ovf = L.add((size_t)K.ovf_cap * 8);
+    o.ovf_count = L.add(4);
     o.gw_pos = L.add((size_t)c->nw * 8);
     o.gw_nrm = L.add((size_t)c->nw * 8);
     o.gw_kind = L.add((size_t)c->nw * 4);
@@ -779,11 +782,12 @@ void bind(hr_case *c, const Offsets &o)
     B.u_vel = at<float2>(w, o.u_vel);
     B.u_id = at<int>(w, o.u_id);
     B.u_key = at<int>(w, o.u_key);
-    B.u_slot = at<int>(w, o.u_slot);
     B.cell_count = at<int>(w, o.cell_count);
     B.cell_start = at<int>(w, o.cell_start);
     B.tile_sum = at<int>(w, o.tile_sum);
-    B.perm_tmp = at<int>(w, o.perm_tmp);
+    B.bucket = at<int>(w, o.bucket);
+    B.ovf = at<int2>(w, o.ovf);
+    B.ovf_count = at<int>(w, o.ovf_count);
     B.gw_pos = at<float2>(w, o.gw_pos);
     B.gw_nrm = at<float2>(w, o.gw_nrm);
     B.gw_kind = at<int>(w, o.gw_kind);
@@ -880,7 +884,6 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
-    k_slot<<<c->drift_blocks, 256, 0, s>>>(K, B);
     const bool paper = K.closure == 1;
     if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     else k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
@@ -963,7 +966,7 @@ int device_status(hr_case *c)
     int rc = st & (HR_WPENETRATION | HR_WOUTSIDE | HR_WPROBEFULL);
     if (st & ST_BOUNDS) rc = HR_ECHECK;
     else if (st & ST_N3WAIT) rc = HR_ETIMEOUT;
-    else if (st & ST_N3CAP) rc = HR_ERANGE;
+    else if (st & (ST_N3CAP | ST_SORTCAP)) rc = HR_ERANGE;
     else if (st & ST_NAN) rc = HR_ENAN;
     else if (st & ST_DT) rc = HR_EDT;
     if (rc < 0) c->sticky = rc;
@@ -990,6 +993,7 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
     CK(cudaMemsetAsync(c->B.cell_count, 0, ((size_t)c->K.ncell + 1) * 4, c->stream));
     CK(cudaMemsetAsync(c->B.tile_sum, 0, (size_t)c->n_tiles * 4, c->stream));
     CK(cudaMemsetAsync(c->B.fin_ticket, 0, 4, c->stream));
+    CK(cudaMemsetAsync(c->B.ovf_count, 0, 4, c->stream));
     CK(cudaMemsetAsync(c->B.S, 0, sizeof(Scalars), c->stream));
     if (c->n3) {
         CK(cudaMemsetAsync(c->B.n3_flag, 0, (size_t)c->K.n3_tiles_max * 4, c->stream));
@@ -1306,7 +1310,6 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     CK(cudaEventRecord(c->join, c->cap2));
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs);
-    k_slot<<<c->drift_blocks, 256, 0, s>>>(K, Bs);
     k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
     CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);
@@ -2193,7 +2196,6 @@ int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
     CK(cudaEventRecord(b->join, side));
     kb_drift_key<<<b->nblocks[BK_DRIFT], 256, 0, s>>>(K, B, b->map[BK_DRIFT]);
     kb_scan_apply<<<b->nblocks[BK_APPLY], kScanThreads, 0, s>>>(K, B, b->map[BK_APPLY]);
-    kb_slot<<<b->nblocks[BK_SLOT], 256, 0, s>>>(K, B, b->map[BK_SLOT]);
     if (b->closure == 1) {
         kb_rank_scatter<1><<<b->nblocks[BK_RANK], 256, 0, s>>>(K, B, b->map[BK_RANK]);
         CK(cudaStreamWaitEvent(s, b->join, 0));
@@ -2253,7 +2255,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
         const hr_case *c = cases[k];
         const int fin = 4 + c->K.n_probes;  // four reduction blocks, one per probe
         const int p3 = c->K.sr == 1 ? c->pass_blocks : 0, p5 = c->K.sr == 2 ? c->pass_blocks : 0;
-        const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, c->drift_blocks,
+        const int nb[kBatchKernels] = {1, c->drift_blocks, c->n_tiles, 0 /* no slot kernel */,
                                        c->drift_blocks, c->ghost_blocks, p3, fin,
                                        c->drift_blocks, p5};
         return nb[q];

@@ -1,17 +1,17 @@
 // hram_device.cuh -- device data layout and kernels of the planar WCSPH
 // hydrodynamic-ram step on B300 (sm_103a).
 //
-// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is eight kernels (nine with the
-// paper's closure, which adds k_density after the sort):
-//   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key and
-//                   in-cell slot (atomic count)                  [T, first half]
+// One step U^{n+1} = T(L(G(U^n))) (Section 4.6) is seven kernels (eight with
+// the paper's closure, which adds k_density after the sort):
+//   k_drift_key     opening kick, XSPH drift, wall enforcement, cell key,
+//                   in-cell slot (atomic count) and the particle's fluid ID
+//                   filed in its cell's bucket                 [T, first half]
 //   k_kinematics     advances t, projectile kinematics (FP64), disk ghost ring
 //                    (a branch of the step graph, beside the drift and sort)
 //   k_scan_apply     cell starts (each block scans the tile sums before it;
 //                    k_drift_key counts the tile sums beside the cells)
-//   k_slot           provisional scatter of old indices into cell order
-//   k_rank_scatter   stable rank by fluid ID inside the cell, SoA reorder,
-//                    Tait pressure of the predicted density
+//   k_rank_scatter   stable rank by fluid ID among the cell's bucket, SoA
+//                    reorder, Tait pressure of the predicted density
 //   k_ghost          Adami ghost extrapolation G (disk ring and wall layers)
 //   k_pass           fused interaction sums L + closing kick epilogue
 //   k_finalize       probes, FP64 accumulators, CFL gate           [T, gate]
@@ -53,6 +53,8 @@ constexpr int ST_PROBEFULL = 4;
 constexpr int ST_NAN = 256;
 constexpr int ST_DT = 512;
 constexpr int ST_N3CAP = 2048;    // a Newton-3 pass tile went past a capacity
+constexpr int ST_SORTCAP = 8192;  // more particles past their cell's bucket than the overflow list holds
+constexpr int kBucket = 16;       // fluid IDs filed per cell by the drift (more go to the overflow list)
 constexpr int ST_N3WAIT = 4096;   // a Newton-3 pass tile gave up waiting for another
 constexpr int kN3Threads = 128;   // particles per Newton-3 pass tile
 
@@ -87,6 +89,7 @@ struct Consts {
     long long probe_cap;
     int n_pass_blocks, n_ghost_blocks;
     int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
+    int ovf_cap;            // entries of the sort's overflow list
     // closure 1 (the paper's): cubic B-spline, summation density,
     // Mie-Grueneisen EOS with the internal-energy equation
     int closure;
@@ -139,12 +142,14 @@ struct Bufs {
     float2 *st_X;    // XSPH sum X^{n+1}
     // drifted, unsorted
     float2 *u_pos, *u_vel;
-    int *u_id, *u_key, *u_slot;
+    int *u_id, *u_key;
     // cell list
     int *cell_count; // ncell + 1 (last = frozen particles)
     int *cell_start; // ncell + 2
     int *tile_sum;
-    int *perm_tmp;   // fluid IDs in provisional cell order
+    int *bucket;     // (ncell + 1) x kBucket: the fluid IDs of each cell, in slot order
+    int2 *ovf;       // {cell, fluid ID} of the particles past their cell's bucket
+    int *ovf_count;  // entries of ovf this step (reset by k_finalize)
     int *perm_dst;   // previous slot -> slot of this step (tangent mode only, else null)
     float4 *s_ex;    // closure 1: {a^n, e^n, De^n} in this step's cell order (else null)
     // wall ghosts (static, cell order) and disk ghosts
@@ -606,7 +611,18 @@ __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, cons
     int slot0 = 0;
     if (key >= 0 && lane == head) slot0 = atomicAdd(&B.cell_count[key], len);
     slot0 = __shfl_sync(0xffffffffu, slot0, head);
-    if (key >= 0) B.u_slot[i] = slot0 + (lane - head);
+    if (key >= 0) {
+        // the particle's fluid ID in its cell's bucket (past it: the overflow list)
+        const int slot = slot0 + (lane - head);
+        const int id = B.u_id[i];
+        if (slot < kBucket) {
+            B.bucket[key * kBucket + slot] = id;
+        } else {
+            const int o = atomicAdd(B.ovf_count, 1);
+            if (o < K.ovf_cap) B.ovf[o] = make_int2(key, id);
+            else atomicOr(&B.S->status, ST_SORTCAP);
+        }
+    }
     // The scan's tile sums, counted here too.  A block's particles, in the
     // previous step's cell order, almost always fall in one tile: then one
     // atomic adds the block's count.  Otherwise each warp adds its own (one
@@ -756,8 +772,8 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
 
 // Cell starts: each block adds up the sums of the tiles before it (counted
 // by k_drift_key), then an exclusive scan of its own tile; the counts are
-// reset for the next step (the tile sums in k_slot, once every block here
-// has read them).
+// reset for the next step (the tile sums in k_rank_scatter, once every block
+// here has read them).
 __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int wsum[kScanThreads / 32];
@@ -828,27 +844,11 @@ __device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
     }
 }
 
-// Provisional scatter of the IDs by (cell start + atomic slot).  Block 0
-// also clears the tile sums for the next step's k_drift_key (and builds the
-// Newton-3 pass's tile table).
-__device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int bx, const int nbx)
-{
-    if (bx == 0 && K.n3) n3_table(K, B);
-    if (bx == 0) {
-        const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
-        for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
-    }
-    const int i = bx * blockDim.x + threadIdx.x;
-    if (i >= K.nf) return;
-    const int key = B.u_key[i];
-    if (kChecked && !hr_ok(key >= 0 && key <= K.ncell, &B.S->status)) return;
-    const int dst = B.cell_start[key] + B.u_slot[i];
-    if (kChecked && !hr_ok(dst >= 0 && dst < K.nf, &B.S->status)) return;
-    B.perm_tmp[dst] = B.u_id[i];
-}
-
-// Stable order inside a cell: rank by fluid ID among the cell's members.
-// Then the reorder into the SoA arrays of this step.  Closure 0: with the
+// Stable order inside a cell: rank by fluid ID among the cell's members
+// (its bucket, and for a cell of more than kBucket particles the overflow
+// list too).  Then the reorder into the SoA arrays of this step.  Block 0
+// first clears the tile sums for the next step's k_drift_key (and builds the
+// Newton-3 pass's tile table).  Closure 0: with the
 // predicted density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n -
 // D^{n-1}))) and its Tait pressure.  Closure 1: with the predicted velocity
 // v* = v^{n+1/2} + dt/2 a^n that the pass sees, and {a^n, e^n, De^n} for the
@@ -856,6 +856,11 @@ __device__ __forceinline__ void b_slot(const Consts &K, const Bufs &B, const int
 template <int CL>
 __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
+    if (bx == 0) {
+        if (K.n3) n3_table(K, B);
+        const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
+        for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
+    }
     const int i = bx * blockDim.x + threadIdx.x;
     if (i >= K.nf) return;
     // the particle's own data first, so their loads overlap the rank loop's
@@ -887,8 +892,17 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
         rec = eos_record(K, dp);
     }
     int rank = 0;
+    const int n = ce - cs;
+    const int *bk = B.bucket + (size_t)key * kBucket;
 #pragma unroll 4
-    for (int k = cs; k < ce; ++k) rank += HR_DYNAMIC_LOAD(&B.perm_tmp[k]) < id;
+    for (int k = 0; k < min(n, kBucket); ++k) rank += HR_DYNAMIC_LOAD(&bk[k]) < id;
+    if (n > kBucket) {
+        const int no = min(*B.ovf_count, K.ovf_cap);
+        for (int k = 0; k < no; ++k) {
+            const int2 e = B.ovf[k];
+            rank += e.x == key && e.y < id;
+        }
+    }
     const int dst = cs + rank;
     if (kChecked && !hr_ok(dst < ce, &B.S->status)) return;
     B.s_pos[dst] = up;
@@ -1933,6 +1947,7 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     __syncthreads();
     if (threadIdx.x == 0) {
         *B.fin_ticket = 0;
+        *B.ovf_count = 0;   // the sort's overflow list, for the next step
         S.Fdx = m2 * ((double)tot[0].hi + (double)tot[0].lo);
         S.Fdy = m2 * ((double)tot[1].hi + (double)tot[1].lo);
         S.Fwall = m2 * ((double)tot[2].hi + (double)tot[2].lo);
@@ -2007,10 +2022,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
     b_scan_apply(K, B, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(256) k_slot(Consts K, Bufs B)
-{
-    b_slot(K, B, blockIdx.x, gridDim.x);
-}
 
 template <int CL>
 __global__ void __launch_bounds__(256) k_rank_scatter(Consts K, Bufs B, int prime)
@@ -2101,14 +2112,6 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const Consts *Ks, 
     b_scan_apply(K, B, m.local, m.nlocal);
 }
 
-__global__ void __launch_bounds__(256) kb_slot(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)
-{
-    __shared__ Consts K;
-    __shared__ Bufs B;
-    __shared__ BatchBlock m;
-    if (!batch_enter(Ks, Bs, map, K, B, m)) return;
-    b_slot(K, B, m.local, m.nlocal);
-}
 
 template <int CL>
 __global__ void __launch_bounds__(256) kb_rank_scatter(const Consts *Ks, const Bufs *Bs, const BatchBlock *map)

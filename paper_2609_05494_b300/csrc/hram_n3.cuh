@@ -9,7 +9,7 @@
 // j > i in the sorted order) or anywhere in the three cells of the row above
 // (c + ncx - 1 .. c + ncx + 1).  Work is split into tiles: runs of up to 128
 // consecutive particles of one cell row (the tile table is built from the
-// cell starts each step, by the first block of k_slot).
+// cell starts each step, by the first block of k_rank_scatter).
 //
 // The sums stay deterministic, with no floating-point atomics:
 //  A. each thread evaluates its particle's half-stencil pairs, adds its own

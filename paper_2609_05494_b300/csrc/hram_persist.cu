@@ -3,9 +3,9 @@
 // Every case of a batch gets a fixed set of thread blocks (its share of the
 // GPU, chosen by the host's autotuner); all blocks stay resident for the
 // whole run (cooperative launch).  A case's blocks advance that case through
-// the stages of each step in order -- kinematics and drift, cell scan,
-// provisional slots, stable reorder, (summed density,) ghosts, interaction
-// pass, closing reduction -- and meet at a per-case barrier between stages,
+// the stages of each step in order -- kinematics and drift, cell scan, stable
+// reorder, (summed density,) ghosts, interaction pass, closing reduction --
+// and meet at a per-case barrier between stages,
 // so cases of different sizes and time steps run at their own pace with no
 // grid-wide synchronisation.  A case whose time reaches its stop time leaves
 // the loop; the launch ends when every case has.
@@ -206,8 +206,6 @@ __global__ void __launch_bounds__(kPersistThreads) kp_batch(const Consts *Ks, co
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
         const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
         for (int vb = r; vb < n_tiles; vb += nb) scan_tile(K, B, vb);
-        if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
-        for (int vb = r; vb < n256; vb += nb) b_slot(K, B, vb, n256);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
         for (int vb = r; vb < n256; vb += nb) b_rank_scatter<CL>(K, B, vb, n256, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
