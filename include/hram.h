@@ -175,7 +175,8 @@ int hr_workspace_bytes(const hr_params *p, int64_t n_fluid, size_t *bytes);
 /* Creates a case.  xy: n_fluid initial positions (float, host, ID order);
  * vel (n_fluid x 2) and rho (n_fluid) may be NULL for rest at rho0.
  * d_workspace: device memory of at least hr_workspace_bytes bytes owned by
- * the caller (it must outlive the case), or NULL to let the library allocate.
+ * the caller (it must outlive the case), aligned to 256 bytes (else
+ * HR_EINVAL), or NULL to let the library allocate.
  * cuda_stream: a cudaStream_t (0 = legacy default stream).  Computes the
  * initial a, D rho, XSPH sums and dt (t = 0), captures the step graph and
  * synchronises.  On failure *out is NULL and nothing is retained. */

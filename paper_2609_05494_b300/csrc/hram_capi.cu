@@ -1506,6 +1506,8 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
         return code;
     };
     if (d_workspace) {
+        // the arrays are carved at 256-byte offsets and read with vector loads
+        if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return fail(HR_EINVAL);
         if (workspace_bytes < o.total) return fail(HR_ENOMEM);
         c->ws = d_workspace;
         c->ws_bytes = workspace_bytes;

@@ -893,9 +893,18 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     }
     int rank = 0;
     const int n = ce - cs;
-    const int *bk = B.bucket + (size_t)key * kBucket;
-#pragma unroll 4
-    for (int k = 0; k < min(n, kBucket); ++k) rank += HR_DYNAMIC_LOAD(&bk[k]) < id;
+    // the cell's bucket as four 16-byte loads issued together (a bucket row
+    // is 64 B, aligned), entries past the cell's count left out
+    const int4 *bk = reinterpret_cast<const int4 *>(B.bucket + (size_t)key * kBucket);
+    static_assert(kBucket == 16, "four int4 loads per bucket");
+    int4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = HR_DYNAMIC_LOAD(&bk[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        rank += (4 * u + 0 < n && q[u].x < id) + (4 * u + 1 < n && q[u].y < id) +
+                (4 * u + 2 < n && q[u].z < id) + (4 * u + 3 < n && q[u].w < id);
+    }
     if (n > kBucket) {
         const int no = min(*B.ovf_count, K.ovf_cap);
         for (int k = 0; k < no; ++k) {
