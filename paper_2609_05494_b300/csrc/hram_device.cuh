@@ -65,7 +65,6 @@ struct Consts {
     // grid and box
     float x0, y0, inv_dc;
     int ncx, ncy, ncell;
-    int sr;   // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
     float xlo, xhi, ylo, yhi;
     float W2, Lx;
     int side_walls, end_walls;
@@ -88,8 +87,6 @@ struct Consts {
     float probe_x[kMaxProbes], probe_y[kMaxProbes];
     long long probe_cap;
     int n_pass_blocks, n_ghost_blocks;
-    int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
-    int ovf_cap;            // entries of the sort's overflow list
     // closure 1 (the paper's): cubic B-spline, summation density,
     // Mie-Grueneisen EOS with the internal-energy equation
     int closure;
@@ -97,6 +94,10 @@ struct Consts {
     float self_w;                  // (m / rho0) W(0): a particle's own share of its density
     float c_av;                    // -alpha h C: the artificial-viscosity factor of every particle
     float mg_K, mg_k1, mg_s1m1, mg_g0, mg_a, mg_mu_max;  // rho0 C^2, 1 - gamma0/2, S1 - 1, gamma0, a, cap
+    // (appended last, so the fields above keep their offsets in the parameter bank)
+    int sr;                 // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
+    int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
+    int ovf_cap;            // entries of the sort's overflow list
 };
 
 // Device-resident scalars of the case.
@@ -1791,19 +1792,8 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
         Srx = fmaf(rw, dx, Srx);
         Sry = fmaf(rw, dy, Sry);
     };
-    if (!outside_box(K, px, py) && K.sr != 1) {
-        // 5 x 5 stencil: the rows one after another
-        const int c = cell_of(K, px, py);
-        const int R = K.sr;
-        for (int dy = -R; dy <= R; ++dy) {
-            const int row = c + dy * K.ncx;
-            if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
-            const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
-            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
-            for (int j = a + lane; j < b; j += 32) add(j);
-        }
-    } else if (!outside_box(K, px, py)) {
-        const int c = cell_of(K, px, py);
+    if (!outside_box(K, px, py) && K.sr == 1) {
+        const int c = cell_of<1>(K, px, py);
         if (kChecked && !hr_ok(c - K.ncx - 1 >= 0 && c + K.ncx + 2 <= K.ncell, &B.S->status))
             return 0.0f;
         const int a0 = B.cell_start[c - K.ncx - 1], b0 = B.cell_start[c - K.ncx + 2];
@@ -1816,6 +1806,16 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
         const int n0 = b0 - a0, n1 = b1 - a1, n = n0 + n1 + (b2 - a2);
         for (int k = lane; k < n; k += 32)
             add(k < n0 ? a0 + k : (k < n0 + n1 ? a1 + (k - n0) : a2 + (k - n0 - n1)));
+    } else if (!outside_box(K, px, py)) {
+        // 5 x 5 stencil: the rows one after another
+        const int c = cell_of<2>(K, px, py);
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int row = c + dy * K.ncx;
+            if (kChecked && !hr_ok(row - 2 >= 0 && row + 3 <= K.ncell, &B.S->status)) continue;
+            const int a = B.cell_start[row - 2], b = B.cell_start[row + 3];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
+            for (int j = a + lane; j < b; j += 32) add(j);
+        }
     }
     SW = warp_sum(SW);
     Sp = warp_sum(Sp);
