@@ -638,8 +638,6 @@ void make_consts(hr_case *c)
     }
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
-    // the sort's overflow list: particles past the kBucket of their cell
-    K.ovf_cap = (int)std::max<long long>(1024, c->nf / 8);
     K.closure = P.closure;
     const double sd = 10.0 / (7.0 * M_PI * h * h);
     K.cub_sd = (float)sd;
@@ -657,7 +655,7 @@ void make_consts(hr_case *c)
 
 struct Offsets {
     size_t s_pos, s_vel, s_aux, s_rd, s_id, st_vel, st_rho, st_a, st_D, st_X, u_pos, u_vel,
-        u_id, u_key, cell_count, cell_start, tile_sum, bucket, ovf, ovf_count, gw_pos, gw_nrm,
+        u_id, u_key, cell_count, cell_start, tile_sum, bucket, ovf, ovf_count, perm_tmp, gw_pos, gw_nrm,
         gw_kind, gw_id, wall_start, disk_off, gd_pos, g_vel, g_aux, ghost_vmax, pass_part,
         probe_now, probe_hist, probe_t, S, diag_part, diag_out, diag_hist, io, part_vmax, part_npen, part_w,
         fin_part, fin_vmax, fin_npen, fin_ticket;
@@ -693,8 +691,9 @@ Offsets plan(const hr_case *c)
     o.cell_start = L.add((nc + 2) * 4);
     o.tile_sum = L.add((size_t)c->n_tiles * 4);
     o.bucket = L.add((nc + 1) * kBucket * 4);
-    o.ovf = L.add((size_t)K.ovf_cap * 8);
+    o.ovf = L.add(n * 16);
     o.ovf_count = L.add(4);
+    o.perm_tmp = L.add(n * 4);
     o.gw_pos = L.add((size_t)c->nw * 8);
     o.gw_nrm = L.add((size_t)c->nw * 8);
     o.gw_kind = L.add((size_t)c->nw * 4);
@@ -786,8 +785,9 @@ void bind(hr_case *c, const Offsets &o)
     B.cell_start = at<int>(w, o.cell_start);
     B.tile_sum = at<int>(w, o.tile_sum);
     B.bucket = at<int>(w, o.bucket);
-    B.ovf = at<int2>(w, o.ovf);
+    B.ovf = at<int4>(w, o.ovf);
     B.ovf_count = at<int>(w, o.ovf_count);
+    B.perm_tmp = at<int>(w, o.perm_tmp);
     B.gw_pos = at<float2>(w, o.gw_pos);
     B.gw_nrm = at<float2>(w, o.gw_nrm);
     B.gw_kind = at<int>(w, o.gw_kind);
@@ -966,7 +966,7 @@ int device_status(hr_case *c)
     int rc = st & (HR_WPENETRATION | HR_WOUTSIDE | HR_WPROBEFULL);
     if (st & ST_BOUNDS) rc = HR_ECHECK;
     else if (st & ST_N3WAIT) rc = HR_ETIMEOUT;
-    else if (st & (ST_N3CAP | ST_SORTCAP)) rc = HR_ERANGE;
+    else if (st & ST_N3CAP) rc = HR_ERANGE;
     else if (st & ST_NAN) rc = HR_ENAN;
     else if (st & ST_DT) rc = HR_EDT;
     if (rc < 0) c->sticky = rc;

@@ -53,7 +53,6 @@ constexpr int ST_PROBEFULL = 4;
 constexpr int ST_NAN = 256;
 constexpr int ST_DT = 512;
 constexpr int ST_N3CAP = 2048;    // a Newton-3 pass tile went past a capacity
-constexpr int ST_SORTCAP = 8192;  // more particles past their cell's bucket than the overflow list holds
 constexpr int kBucket = 16;       // fluid IDs filed per cell by the drift (more go to the overflow list)
 constexpr int ST_N3WAIT = 4096;   // a Newton-3 pass tile gave up waiting for another
 constexpr int kN3Threads = 128;   // particles per Newton-3 pass tile
@@ -97,7 +96,6 @@ struct Consts {
     // (appended last, so the fields above keep their offsets in the parameter bank)
     int sr;                 // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
     int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
-    int ovf_cap;            // entries of the sort's overflow list
 };
 
 // Device-resident scalars of the case.
@@ -149,8 +147,9 @@ struct Bufs {
     int *cell_start; // ncell + 2
     int *tile_sum;
     int *bucket;     // (ncell + 1) x kBucket: the fluid IDs of each cell, in slot order
-    int2 *ovf;       // {cell, fluid ID} of the particles past their cell's bucket
+    int4 *ovf;       // {cell, fluid ID, slot} of the particles past their cell's bucket (nf)
     int *ovf_count;  // entries of ovf this step (reset by k_finalize)
+    int *perm_tmp;   // the IDs of slots >= kBucket at cell start + slot (overflowing cells only)
     int *perm_dst;   // previous slot -> slot of this step (tangent mode only, else null)
     float4 *s_ex;    // closure 1: {a^n, e^n, De^n} in this step's cell order (else null)
     // wall ghosts (static, cell order) and disk ghosts
@@ -618,10 +617,9 @@ __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, cons
         const int id = B.u_id[i];
         if (slot < kBucket) {
             B.bucket[key * kBucket + slot] = id;
-        } else {
+        } else {   // at most nf entries: the list cannot fill
             const int o = atomicAdd(B.ovf_count, 1);
-            if (o < K.ovf_cap) B.ovf[o] = make_int2(key, id);
-            else atomicOr(&B.S->status, ST_SORTCAP);
+            B.ovf[o] = make_int4(key, id, slot, 0);
         }
     }
     // The scan's tile sums, counted here too.  A block's particles, in the
@@ -771,10 +769,27 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
     }
 }
 
+// The particles past their cell's bucket (the drift's overflow list, empty
+// unless a cell holds more than kBucket particles), for the cells [c0, c1)
+// whose starts this block has just written: each ID goes to perm_tmp at its
+// cell's start + its slot, where the reorder reads it.
+__device__ __forceinline__ void scan_overflow(const Consts &K, const Bufs &B, int c0, int c1)
+{
+    __syncthreads();   // this block's cell starts are written
+    const int no = *B.ovf_count;
+    for (int k = threadIdx.x; k < no; k += blockDim.x) {
+        const int4 e = B.ovf[k];
+        if (e.x < c0 || e.x >= c1) continue;
+        const int dst = B.cell_start[e.x] + e.z;
+        if (kChecked && !hr_ok(dst >= 0 && dst < K.nf, &B.S->status)) continue;
+        B.perm_tmp[dst] = e.y;
+    }
+}
+
 // Cell starts: each block adds up the sums of the tiles before it (counted
-// by k_drift_key), then an exclusive scan of its own tile; the counts are
-// reset for the next step (the tile sums in k_rank_scatter, once every block
-// here has read them).
+// by k_drift_key), then an exclusive scan of its own tile, and places its
+// cells' overflowing IDs; the counts are reset for the next step (the tile
+// sums in k_rank_scatter, once every block here has read them).
 __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int wsum[kScanThreads / 32];
@@ -810,6 +825,7 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
         ex += v[k];
     }
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
+    scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n));
 }
 
 // The Newton-3 pass's tile table: chunks of kN3Threads particles of each
@@ -846,8 +862,8 @@ __device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
 }
 
 // Stable order inside a cell: rank by fluid ID among the cell's members
-// (its bucket, and for a cell of more than kBucket particles the overflow
-// list too).  Then the reorder into the SoA arrays of this step.  Block 0
+// (its bucket, and for a cell of more than kBucket particles the rest, which
+// the scan placed in perm_tmp).  Then the reorder into the SoA arrays of this step.  Block 0
 // first clears the tile sums for the next step's k_drift_key (and builds the
 // Newton-3 pass's tile table).  Closure 0: with the
 // predicted density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n -
@@ -906,13 +922,8 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
         rank += (4 * u + 0 < n && q[u].x < id) + (4 * u + 1 < n && q[u].y < id) +
                 (4 * u + 2 < n && q[u].z < id) + (4 * u + 3 < n && q[u].w < id);
     }
-    if (n > kBucket) {
-        const int no = min(*B.ovf_count, K.ovf_cap);
-        for (int k = 0; k < no; ++k) {
-            const int2 e = B.ovf[k];
-            rank += e.x == key && e.y < id;
-        }
-    }
+    // slots kBucket.. of an overflowing cell, placed by the scan
+    for (int k = cs + kBucket; k < ce; ++k) rank += HR_DYNAMIC_LOAD(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
     if (kChecked && !hr_ok(dst < ce, &B.S->status)) return;
     B.s_pos[dst] = up;
