@@ -634,6 +634,26 @@ def _oracle_sample(args):
     return xy.shape[0], steps, time.perf_counter() - t1, t1 - t0
 
 
+def _oracle_config_runs():
+    """The oracle as it stands, one thread, on the two small workloads run in
+    full: the 150 x 150 mm parity case (dx = 2 mm, 250 steps) and the
+    22,500-particle derivative workload (dx = 1 mm, 400 steps, fixed dt)."""
+    import oracle
+    out = {}
+    for name, p in (("parity_150x150_dx2mm_250_steps", casegen.config_parity()),
+                    ("adjoint_150x150_dx1mm_400_steps", casegen.config_adjoint())):
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                                   disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
+        o = oracle.OracleCase(p, xy.astype(np.float64))
+        n = int(p["n_steps"])
+        t0 = time.perf_counter()
+        o.run(n)
+        el = time.perf_counter() - t0
+        out[name] = {"particles": int(xy.shape[0]), "steps": n, "seconds": el,
+                     "particle_steps_per_s": xy.shape[0] * n / el}
+    return out
+
+
 def cpu_baseline(seconds=10.0, Lx=0.075):
     """The FP64 oracle as it stands on a bounded sample of the workload (the
     first Lx of the channel at the same spacing, from t = 0), timed on the
@@ -657,6 +677,7 @@ def cpu_baseline(seconds=10.0, Lx=0.075):
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "single_thread": {"value": single, "cores": 1, "steps": steps, "seconds": el},
+            "full_runs_single_thread": _oracle_config_runs(),
             "sample": "first %d mm of the 300 mm channel at dx = 0.2 mm (%d fluid particles) "
                       "from t = 0; %d independent copies at once (one per host core) for about "
                       "%.0f s each, %d steps in all (one thread alone: %d steps, set-up %.1f s)"
