@@ -531,10 +531,10 @@ def paper_event_benchmark(stream):
                                    disk=(p["x_c0"], p["y_c0"], p["R_disk"])).astype(np.float32)
         return p, xy
 
-    def event(dx, alpha, v0):
+    def event(dx, alpha, v0, lanes=1):
         p, xy = setup(dx, alpha, v0)
         with torch.cuda.stream(stream):
-            c = Case(p, xy, stream=stream)
+            c = Case(p, xy, stream=stream, lanes=lanes)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = c.run(0, p["t_end"])
@@ -551,6 +551,11 @@ def paper_event_benchmark(stream):
     main = event(1.5e-3, 0.03, 900.0)
     main.update(particle_steps_per_s=main["particles"] * main["steps"] / main["wall_s"],
                 paper_wall_s_titan_rtx=14.0)
+    # the same event with the pass on four lanes per particle (a small,
+    # latency-bound case; its sums differ from the one-lane run's in order)
+    l4 = event(1.5e-3, 0.03, 900.0, lanes=4)
+    main["lanes4"] = {k: l4[k] for k in ("steps", "wall_s", "ms_per_step", "ptn_peak_MPa",
+                                         "ptf_peak_MPa", "status")}
     # the paper's printed peaks (MPa) for the same runs
     paper_res = {2.0: (785.8, 658.0), 1.5: (850.3, 714.9), 1.0: (830.5, 737.5)}
     paper_alpha = {(900.0, 0.01): 855.7, (900.0, 0.03): 850.3, (900.0, 0.06): 893.7,
