@@ -261,3 +261,28 @@ def test_fp32_rate_measurement():
     for packed in (False, True):
         r = fp32_rate(packed)
         assert 0.05 * bound < r < 2.2 * bound, (packed, r, bound)
+
+
+def test_caller_workspace_must_be_aligned():
+    # a caller-owned workspace 16 bytes off a 256-byte boundary is refused
+    # before any device work; the aligned one is taken
+    import ctypes as C
+    from paper_2609_05494_b300 import make_params
+    p, xy = impact_case()
+    L = _lib.lib()
+    par = make_params(p, 0, 64, 0)
+    n = xy.shape[0]
+    nbytes = C.c_size_t(0)
+    assert L.hr_workspace_bytes(C.byref(par), n, C.byref(nbytes)) == 0
+    ws = torch.empty(nbytes.value + 512, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    xyc = np.ascontiguousarray(xy, dtype=np.float32)
+    h = C.c_void_p()
+    rc = L.hr_init_case(C.byref(par), xyc.ctypes.data, n, None, None, C.c_void_p(base + 16),
+                        nbytes.value, None, C.byref(h))
+    assert rc == _lib.HR_EINVAL and not h.value
+    rc = L.hr_init_case(C.byref(par), xyc.ctypes.data, n, None, None, C.c_void_p(base),
+                        nbytes.value, None, C.byref(h))
+    assert rc >= 0 and h.value
+    L.hr_destroy(h)
+    torch.cuda.synchronize()
