@@ -743,6 +743,9 @@ def run_only(args):
     stream = torch.cuda.Stream()
     if args.only == "sweep":
         out = sweep_benchmark(stream)
+    elif args.only == "scaling":
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = scaling_benchmark(stream, flush, steps=args.steps)
     elif args.only == "small":
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         out = small_case_benchmark(stream, flush, steps=args.steps)
@@ -793,7 +796,7 @@ def main():
     ap.add_argument("--no-production", action="store_true")
     ap.add_argument("--no-passvar", action="store_true")
     ap.add_argument("--no-small", action="store_true")
-    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small"),
+    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small", "scaling"),
                     help="run one leg alone on the channel at --dx for --steps steps "
                          "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
