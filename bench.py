@@ -177,6 +177,34 @@ def shard(items, rank, world):
     return list(items)[rank::world]
 
 
+def batch_steps_benchmark(stream, steps, n_cases=64):
+    """The 64-case sweep as one batch (default cell grids and schedule), the
+    first `steps` batched steps timed with CUDA events: for profiling the
+    batched kernels alone."""
+    import torch
+    from paper_2609_05494_b300 import Batch, Case
+    specs = []
+    for p in casegen.sweep_draws(casegen.DEFAULT_SEED, n_cases):
+        xy = casegen.fluid_lattice(p["Lx"], p["W"], p["dx"], p["jitter"], p["seed"],
+                                   disk=(p["x_c0"], p["y_c0"], p["R_disk"]))
+        specs.append((p, xy.astype(np.float32)))
+    cases = [Case(p, xy, stream=stream) for p, xy in specs]
+    with Batch(cases, 1.0, stream=stream) as b:      # no case reaches t = 1 s here
+        b.run(max_steps=3)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            b.step()
+        e.record(stream)
+        e.synchronize()
+        ms = a.elapsed_time(e) / steps
+    n = sum(xy.shape[0] for _, xy in specs)
+    for c in cases:
+        c.close()
+    return {"cases": n_cases, "particles": n, "steps": steps, "ms_per_batched_step": ms,
+            "particle_steps_per_s": n / (ms * 1e-3)}
+
+
 def sweep_benchmark(stream, rank=0, world=1, dist=None, n_cases=64, t_end=0.5e-3):
     """The batched coefficient sweep: n_cases cases from casegen.sweep_draws
     (alpha, c0, cutoff, v0, width; dx = 1 mm), each run to t_end, first one
@@ -743,6 +771,8 @@ def run_only(args):
     stream = torch.cuda.Stream()
     if args.only == "sweep":
         out = sweep_benchmark(stream)
+    elif args.only == "batch":
+        out = batch_steps_benchmark(stream, args.steps)
     elif args.only == "scaling":
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         out = scaling_benchmark(stream, flush, steps=args.steps)
@@ -796,7 +826,8 @@ def main():
     ap.add_argument("--no-production", action="store_true")
     ap.add_argument("--no-passvar", action="store_true")
     ap.add_argument("--no-small", action="store_true")
-    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small", "scaling"),
+    ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small", "scaling",
+                                       "batch"),
                     help="run one leg alone on the channel at --dx for --steps steps "
                          "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
