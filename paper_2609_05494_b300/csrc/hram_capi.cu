@@ -462,6 +462,7 @@ struct hr_case {
     long long nf = 0, nw = 0, ng = 0;
     int device = -1;  // the CUDA device current at hr_init_case
     int n_tiles = 0, pass_blocks = 0, ghost_blocks = 0, drift_blocks = 0, diag_blocks = 0;
+    int tghost_blocks = 0;   // blocks of the tangent ghost kernel (one warp per ghost)
     cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
@@ -623,7 +624,9 @@ void make_consts(hr_case *c)
     K.probe_cap = P.probe_capacity > 0 ? P.probe_capacity : (1LL << 16);
     c->drift_blocks = (int)((c->nf + 255) / 256);
     c->pass_blocks = (int)((c->nf + kPassThreads - 1) / kPassThreads);
-    c->ghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + kGhostWarps - 1) / kGhostWarps);
+    c->ghost_blocks =
+        (int)std::max<long long>(1, (c->nw + c->ng + kGhostsPerBlock - 1) / kGhostsPerBlock);
+    c->tghost_blocks = (int)std::max<long long>(1, (c->nw + c->ng + kGhostWarps - 1) / kGhostWarps);
     c->n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
     c->diag_blocks = (int)((c->nf + kDiagThreads - 1) / kDiagThreads);
     c->tpass_blocks = (int)((c->nf + kTPassThreads - 1) / kTPassThreads);
@@ -897,7 +900,7 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     } else {
         k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
     }
-    if (c->tangent) kt_ghost<<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
+    if (c->tangent) kt_ghost<<<c->tghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     if (c->n3) k_pass_n3<<<c->pass_blocks, kN3Threads, 0, s>>>(K, B, prime);
     else if (c->lanes == 2 && paper) k_pass_lanes<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);

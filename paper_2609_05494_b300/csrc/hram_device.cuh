@@ -45,6 +45,8 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kFinalizeThreads = 256;
 constexpr int kFinalizeBlocks = 64;
 constexpr int kGhostWarps = 8;
+constexpr int kGhostLanes = 8;                                  // lanes per ghost in b_ghost
+constexpr int kGhostsPerBlock = kGhostWarps * 32 / kGhostLanes;  // ghosts per b_ghost block
 
 // device status bits (warnings share the public HR_W* values)
 constexpr int ST_PENETRATION = 1;
@@ -1043,54 +1045,65 @@ __device__ __forceinline__ void b_density(const Consts &K, const Bufs &B, const 
 // disk ghosts [nw, nw + ng), over fluid neighbours in the 3x3 cell stencil:
 //   p_g = max((S_p + (g - a_w) . S_rr) / S_W, p_cav),
 //   rho_g = rho0 (1 + p_g / (rho0 c0^2)),  v_g = 2 v_w - S_v / S_W.
-// One warp per ghost: the lanes split the stencil's candidates, then the six
-// Shepard sums are reduced across the warp.
+// kGhostLanes lanes per ghost (four ghosts per warp): the lanes split the
+// stencil's candidates, then the six Shepard sums are combined over the
+// ghost's lanes by a butterfly of shuffles.
 template <int CL>
 __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ float red[kGhostWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = bx * kGhostWarps + w;
-    float vabs = 0.0f;
-    if (g < K.nw + K.ng) {
-        const bool disk = g >= K.nw;
-        const float2 rg = disk ? B.gd_pos[g - K.nw] : B.gw_pos[g];
-        const float vwx = disk ? B.S->vproj_f : 0.0f;
-        const float awx = disk ? B.S->aproj_f : 0.0f;
-        float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f, Svx = 0.f, Svy = 0.f;
-        const bool inside = !outside_box(K, rg.x, rg.y);
-        if (inside) {
-            const int c = cell_of(K, rg.x, rg.y);
-            const int R = K.sr;
+    const int sub = lane & (kGhostLanes - 1);
+    const int g = bx * kGhostsPerBlock + (int)threadIdx.x / kGhostLanes;
+    const bool active = g < K.nw + K.ng;
+    const bool disk = g >= K.nw;
+    float2 rg = make_float2(0.f, 0.f);
+    bool inside = false;
+    float SW = 0.f, Sp = 0.f, Srx = 0.f, Sry = 0.f, Svx = 0.f, Svy = 0.f;
+    if (active) {
+        rg = disk ? B.gd_pos[g - K.nw] : B.gw_pos[g];
+        inside = !outside_box(K, rg.x, rg.y);
+    }
+    if (inside) {
+        const int c = cell_of(K, rg.x, rg.y);
+        const int R = K.sr;
 #pragma unroll 1
-            for (int dy = -R; dy <= R; ++dy) {
-                const int row = c + dy * K.ncx;
-                if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
-                const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
-                if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
-                for (int j = a + lane; j < b; j += 32) {
-                    const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
-                    if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
-                    const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
-                    const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy2 * dy2)));
-                    const float4 aux = HR_DYNAMIC_LOAD(&B.s_aux[j]);
-                    const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
-                    const float rw = (1.0f + aux.x) * W;
-                    SW += W;
-                    Sp = fmaf(aux.y, W, Sp);
-                    Srx = fmaf(rw, dx, Srx);
-                    Sry = fmaf(rw, dy2, Sry);
-                    Svx = fmaf(vj.x, W, Svx);
-                    Svy = fmaf(vj.y, W, Svy);
-                }
+        for (int dy = -R; dy <= R; ++dy) {
+            const int row = c + dy * K.ncx;
+            if (kChecked && !hr_ok(row - R >= 0 && row + R + 1 <= K.ncell, &B.S->status)) continue;
+            const int a = B.cell_start[row - R], b = B.cell_start[row + R + 1];
+            if (kChecked && !row_ok(K, row, a, b, K.nf, &B.S->status)) continue;
+            for (int j = a + sub; j < b; j += kGhostLanes) {
+                const float2 rj = HR_DYNAMIC_LOAD(&B.s_pos[j]);
+                if (!in_support(rg.x, rg.y, rj.x, rj.y, K.s2)) continue;
+                const float dx = rg.x - rj.x, dy2 = rg.y - rj.y;
+                const float W = kernel_w<CL>(K, sqrtf(fmaf(dx, dx, dy2 * dy2)));
+                const float4 aux = HR_DYNAMIC_LOAD(&B.s_aux[j]);
+                const float2 vj = HR_DYNAMIC_LOAD(&B.s_vel[j]);
+                const float rw = (1.0f + aux.x) * W;
+                SW += W;
+                Sp = fmaf(aux.y, W, Sp);
+                Srx = fmaf(rw, dx, Srx);
+                Sry = fmaf(rw, dy2, Sry);
+                Svx = fmaf(vj.x, W, Svx);
+                Svy = fmaf(vj.y, W, Svy);
             }
         }
-        SW = warp_sum(SW);
-        Sp = warp_sum(Sp);
-        Srx = warp_sum(Srx);
-        Sry = warp_sum(Sry);
-        Svx = warp_sum(Svx);
-        Svy = warp_sum(Svy);
+    }
+    // the ghost's kGhostLanes lanes combine their sums (every lane takes part)
+#pragma unroll
+    for (int o = kGhostLanes / 2; o > 0; o >>= 1) {
+        SW += __shfl_xor_sync(0xffffffffu, SW, o);
+        Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
+        Srx += __shfl_xor_sync(0xffffffffu, Srx, o);
+        Sry += __shfl_xor_sync(0xffffffffu, Sry, o);
+        Svx += __shfl_xor_sync(0xffffffffu, Svx, o);
+        Svy += __shfl_xor_sync(0xffffffffu, Svy, o);
+    }
+    float vabs = 0.0f;
+    if (active) {
+        const float vwx = disk ? B.S->vproj_f : 0.0f;
+        const float awx = disk ? B.S->aproj_f : 0.0f;
         float4 aux;
         float2 vg;
         if (SW > 0.0f) {
@@ -1107,12 +1120,13 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
             aux = make_float4(0.0f, 0.0f, 0.0f, CL == 1 ? 0.0f : -K.alpha_h * K.c0);
             vg = make_float2(vwx, 0.0f);
         }
-        if (lane == 0) {
+        if (sub == 0) {
             B.g_aux[g] = aux;
             B.g_vel[g] = vg;
         }
         if (inside) vabs = sqrtf(vg.x * vg.x + vg.y * vg.y);
     }
+    vabs = warp_max(vabs);
     if (lane == 0) red[w] = vabs;
     __syncthreads();
     if (threadIdx.x == 0) {
