@@ -152,6 +152,26 @@ def test_checkpoint_resume_bitwise():
     assert a.scalars() == b.scalars()
 
 
+@pytest.mark.parametrize("variant", [dict(stage=1), dict(newton3=True), dict(lanes=4),
+                                     dict(cell_factor=0.5)])
+def test_pass_variants_with_frozen_particles(variant):
+    # particles outside the box keep their state in every pass variant
+    kw = dict(variant)
+    cf = kw.pop("cell_factor", None)
+    p, xy = impact_case(Lx=0.03, W=0.03, dx=1e-3, Ng=0, **({"cell_factor": cf} if cf else {}))
+    xy = xy.copy()
+    xy[:5, 0] = 1.0
+    g = Case(p, xy, **kw)
+    o = oracle.OracleCase(p, as64(xy))
+    g.run(10)
+    o.run(10)
+    sg, fo = g.get_state(), o.fluid()
+    assert np.array_equal(sg["xy"][:5], xy[:5])
+    assert np.abs(sg["rho"] / fo["rho"] - 1).max() <= 1e-5
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    assert g.diagnostics()["n_in"] == fo["out"].size - 5
+
+
 def test_caller_owned_output_buffers():
     # pinned (page-locked) caller buffers receive exactly what the library's
     # own arrays receive; wrong shapes or dtypes are refused before any copy
