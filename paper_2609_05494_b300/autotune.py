@@ -146,7 +146,7 @@ def block_counts(specs, capacity: int, a: float, b: float, t_end: float) -> np.n
     return n.astype(np.int32)
 
 
-def tune_persistent(specs, t_end: float, horizon: float = 60e-6, stream=None, weights=BLOCK_WEIGHTS):
+def tune_persistent(specs, t_end: float, horizon: float = 250e-6, stream=None, weights=BLOCK_WEIGHTS):
     """Block counts of a persistent batch: each candidate split of the resident
     blocks (weights (a, b) of block_counts) runs the sweep's first ``horizon``
     seconds of simulated time on throw-away copies; the fastest split wins.

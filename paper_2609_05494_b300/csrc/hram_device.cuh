@@ -1857,7 +1857,10 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 // results, updates the FP64 accumulators and applies the CFL gate (a6); its
 // scalar updates are split over three warps.  The sums are compensated FP32
 // (two-float) in a fixed tree order, converted to FP64 once at the end.
-template <int CL>
+// SKIP_EMPTY (the persistent batch, where a case's blocks take the virtual
+// blocks one after another): a reduction block whose slice holds no partial
+// writes its zero sums without the block reduction.
+template <int CL, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     constexpr int NW = kFinalizeThreads / 32;
@@ -1923,6 +1926,16 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
                 __threadfence();
                 is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
             }
+        }
+    } else if (SKIP_EMPTY && bx * (int)blockDim.x >= max(K.n_pass_blocks, K.n_ghost_blocks)) {
+        // a slice past every partial: its sums are zero (what the reduction
+        // below would produce), written without the block reduction
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 8; ++k) B.fin_part[bx * 8 + k] = 0.0f;
+            B.fin_vmax[bx] = 0.0f;
+            B.fin_npen[bx] = 0;
+            __threadfence();
+            is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
         }
     } else {
         F2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};

@@ -201,12 +201,13 @@ __global__ void __launch_bounds__(kPersistThreads) kp_batch(const Consts *Ks, co
         if (threadIdx.x == 0) done = ld_acquire(&B.S->done);
         __syncthreads();
         if (done) break;
-        // kinematics (first block) beside the drift
-        if (r == 0) b_kinematics(K, B, 0, 1, 0);
         for (int vb = r; vb < n256; vb += nb) b_drift_key(K, B, vb, n256, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
+        // the scan tiles, and the kinematics (needed from the ghost stage on)
+        // by a block with no tile, or the last one, off the drift's path
         const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
         for (int vb = r; vb < n_tiles; vb += nb) scan_tile(K, B, vb);
+        if (r == (n_tiles < nb ? n_tiles : nb - 1)) b_kinematics(K, B, 0, 1, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
         for (int vb = r; vb < n256; vb += nb) b_rank_scatter<CL>(K, B, vb, n256, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kPersistThreads) kp_batch(const Consts *Ks, co
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
         for (int q = r; q < n256; q += nb) pass_pair<CL>(K, B, q);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
-        for (int vb = r; vb < nfin; vb += nb) b_finalize<CL>(K, B, vb, nfin, 0);
+        for (int vb = r; vb < nfin; vb += nb) b_finalize<CL, true>(K, B, vb, nfin, 0);
         if (!case_barrier(cnt, gen, nb, spin_limit, err, &flag)) return;
     }
 }
