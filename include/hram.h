@@ -92,6 +92,19 @@ extern "C" {
                             >= 1, single-case steps; not with the tangent or
                             reverse modes.  At most one pass-variant flag */
 #define HR_FLAG_PASS_LANES4 64 /* as HR_FLAG_PASS_LANES2 with 4 lanes */
+#define HR_FLAG_PASS_SPLIT 128 /* run the interaction pass split: the interior
+                            particles (no wall ghost in their cell stencil, not
+                            near the disk) in one kernel that does not wait for
+                            the ghost pass, and the boundary particles, listed by
+                            the reorder, after the ghost pass on a
+                            high-priority graph branch beside it.  Results are
+                            the same bit for bit as the one-kernel pass.  By
+                            default a case of at least 262,144 fluid particles
+                            with the 3 x 3 stencil, no pass-variant flag and no
+                            HR_FLAG_TANGENT runs split; this flag asks for it
+                            at any size (same conditions otherwise) */
+#define HR_FLAG_PASS_FUSED 256 /* never run the interaction pass split (not
+                            with HR_FLAG_PASS_SPLIT) */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)
@@ -242,7 +255,9 @@ int hr_get_ghosts(hr_case *c, float *xy, float *p, float *rho, float *vel, int64
  * W_boundary, wall_impulse, dissipation, diss_rate (14 doubles). */
 int hr_get_scalars(hr_case *c, double *out, int n);
 
-/* Counts: n_fluid, n_wall, n_disk, ncx, ncy, pass_blocks (6 int64). */
+/* Counts: n_fluid, n_wall, n_disk, ncx, ncy, pass_blocks, and 1 when the
+ * interaction pass runs split (HR_FLAG_PASS_SPLIT) (7 int64; the first n of
+ * them are written). */
 int hr_case_info(hr_case *c, int64_t *out, int n);
 
 /* Neighbour sets of the current state as CSR over all points (fluid IDs,

@@ -39,6 +39,8 @@ HR_FLAG_STAGE_ALL = 8
 HR_FLAG_NEWTON3 = 16
 HR_FLAG_PASS_LANES2 = 32
 HR_FLAG_PASS_LANES4 = 64
+HR_FLAG_PASS_SPLIT = 128
+HR_FLAG_PASS_FUSED = 256
 
 EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",

@@ -75,13 +75,15 @@ class Case:
     candidates' positions in shared memory, 2 their whole records (the
     results are identical).  ``newton3`` evaluates every fluid pair once,
     ``lanes`` (2 or 4) splits each particle's pass work over that many lanes
-    (results equal to rounding).
+    (results equal to rounding).  ``split`` runs the interaction pass as
+    interior and boundary kernels beside the ghost pass (True), never
+    (False), or by the library's size rule (None); results are identical.
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
                  probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
                  tangent: bool = False, stage: int = 0, newton3: bool = False,
-                 lanes: int = 1):
+                 lanes: int = 1, split: bool | None = None):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -98,6 +100,8 @@ class Case:
         if lanes not in (1, 2, 4):
             raise ValueError("lanes must be 1, 2 or 4")
         flags |= {1: 0, 2: _lib.HR_FLAG_PASS_LANES2, 4: _lib.HR_FLAG_PASS_LANES4}[lanes]
+        if split is not None:
+            flags |= _lib.HR_FLAG_PASS_SPLIT if split else _lib.HR_FLAG_PASS_FUSED
         self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)
@@ -238,9 +242,9 @@ class Case:
         return dict(zip(SCALAR_FIELDS, s.tolist()))
 
     def info(self) -> dict:
-        v = np.empty(6, dtype=np.int64)
-        check(lib().hr_case_info(self._h, _ptr(v), 6), "hr_case_info")
-        return dict(zip(("n_fluid", "n_wall", "n_disk", "ncx", "ncy", "pass_blocks"),
+        v = np.empty(7, dtype=np.int64)
+        check(lib().hr_case_info(self._h, _ptr(v), 7), "hr_case_info")
+        return dict(zip(("n_fluid", "n_wall", "n_disk", "ncx", "ncy", "pass_blocks", "split"),
                         (int(x) for x in v)))
 
     def neighbours(self) -> tuple[np.ndarray, np.ndarray]:

@@ -48,6 +48,12 @@ constexpr int kTimingEvents = 6;
 // latency of its launches, and one graph of several steps leaves out the gaps
 // between graph launches
 constexpr int kMultiSteps = 4;
+// the split interaction pass: on by default from this many fluid particles
+// (below it the step is bound by its kernels' latency, and the boundary
+// particles are too large a share to hide); grid of its boundary kernels
+// (grid-stride over their lists)
+constexpr long long kSplitMinParticles = 262144;
+constexpr int kSplitBlocks = 592;
 
 // ------------------------------------------------ auxiliary device kernels
 
@@ -439,6 +445,12 @@ int validate(const hr_params *P, long long nf)
     if (P->cell_factor < 1.0 &&
         (P->flags & (HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL)))
         return HR_EINVAL;
+    // the split pass: the plain 3 x 3 pass only
+    if ((P->flags & HR_FLAG_PASS_SPLIT) &&
+        ((P->flags & (HR_FLAG_PASS_FUSED | HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL |
+                      HR_FLAG_NEWTON3 | HR_FLAG_PASS_LANES2 | HR_FLAG_PASS_LANES4)) ||
+         P->cell_factor < 1.0))
+        return HR_EINVAL;
     // tangent mode: fixed time step (smooth in c0) and a prescribed motion
     if ((P->flags & HR_FLAG_TANGENT) && (P->dt_mode != 1 || P->motion > 2)) return HR_EINVAL;
     if (P->closure < 0 || P->closure > 1) return HR_EINVAL;
@@ -490,6 +502,9 @@ struct hr_case {
     int stage = 0;                // pass variant: 0 global loads, 1/2 staged candidates
     bool n3 = false;              // pass variant: each fluid pair evaluated once
     int lanes = 1;                // pass variant: lanes per particle
+    int split_blocks = 0;         // blocks of the split pass's boundary kernels
+    cudaEvent_t fork2 = nullptr, join2 = nullptr;   // the split pass's ghost branch
+    int prio_hi = 0;              // the device's greatest stream priority (that branch's)
     TBufs T{};
     int tpass_blocks = 0;
     void *t_base = nullptr;
@@ -639,6 +654,15 @@ void make_consts(hr_case *c)
         c->pass_blocks = (int)((c->nf + kN3Threads - 1) / kN3Threads) + K.ncy + 1;
         K.n3_tiles_max = c->pass_blocks;
     }
+    // the split pass (interior particles beside the ghost pass): large
+    // cases with the plain 3 x 3 pass, unless asked for or refused
+    {
+        const int variants = HR_FLAG_TANGENT | HR_FLAG_STAGE_POS | HR_FLAG_STAGE_ALL | HR_FLAG_NEWTON3 |
+                             HR_FLAG_PASS_LANES2 | HR_FLAG_PASS_LANES4 | HR_FLAG_PASS_FUSED;
+        const bool plain = K.sr == 1 && !(P.flags & variants) && c->nw + c->ng > 0;
+        K.split = plain && ((P.flags & HR_FLAG_PASS_SPLIT) || c->nf >= kSplitMinParticles) ? 1 : 0;
+    }
+    c->split_blocks = std::max(1, std::min(c->pass_blocks, kSplitBlocks));
     K.n_pass_blocks = c->pass_blocks;
     K.n_ghost_blocks = c->ghost_blocks;
     K.closure = P.closure;
@@ -664,6 +688,9 @@ struct Offsets {
         fin_part, fin_vmax, fin_npen, fin_ticket;
     size_t s_ex;  // closure 1 only
     size_t n3_row_base, n3_tile_row, n3_info, n3_flag, n3_ext_a, n3_ext_b, n3_ctl;  // Newton-3 only
+    size_t wall_near;
+    size_t split_n, split_pi, split_bi, split_mask, split_pf, split_pv, split_part, split_vmax,
+        split_npen;  // the split pass only
     // tangent arrays (zero-sized unless HR_FLAG_TANGENT)
     size_t t_begin, t_s_pos, t_s_vel, t_s_aux, t_s_rd, t_st_vel, t_st_rho, t_st_a, t_st_D, t_st_X,
         t_u_pos, t_u_vel, t_g_vel, t_g_aux, t_perm, t_part, t_sc, t_end;
@@ -734,6 +761,19 @@ Offsets plan(const hr_case *c)
         o.n3_ext_a = L.add(nt * kN3ExtCap * 16);
         o.n3_ext_b = L.add(nt * kN3ExtCap * 4);
         o.n3_ctl = L.add(K.n3 ? 8 : 0);
+    }
+    o.wall_near = L.add(nc);
+    {
+        const size_t ns = K.split ? n : 0, nb = K.split ? (size_t)c->pass_blocks : 0;
+        o.split_n = L.add(K.split ? 8 : 0);
+        o.split_pi = L.add(ns * 4);
+        o.split_bi = L.add(nb * 4);
+        o.split_mask = L.add((nb + 31) / 32 * 4);
+        o.split_pf = L.add(ns * 16);
+        o.split_pv = L.add(ns * 8);
+        o.split_part = L.add(nb * 16);
+        o.split_vmax = L.add(nb * 4);
+        o.split_npen = L.add(nb * 4);
     }
     const size_t tn = (c->P.flags & HR_FLAG_TANGENT) ? n * kDir : 0;
     const size_t tg = (c->P.flags & HR_FLAG_TANGENT) ? ng * kDir : 0;
@@ -829,6 +869,17 @@ void bind(hr_case *c, const Offsets &o)
     B.n3_ext_a = c->n3 ? at<float4>(w, o.n3_ext_a) : nullptr;
     B.n3_ext_b = c->n3 ? at<float>(w, o.n3_ext_b) : nullptr;
     B.n3_ctl = c->n3 ? at<int>(w, o.n3_ctl) : nullptr;
+    B.wall_near = at<unsigned char>(w, o.wall_near);
+    const bool sp = c->K.split != 0;
+    B.split_n = sp ? at<int>(w, o.split_n) : nullptr;
+    B.split_pi = sp ? at<int>(w, o.split_pi) : nullptr;
+    B.split_bi = sp ? at<int>(w, o.split_bi) : nullptr;
+    B.split_mask = sp ? at<unsigned>(w, o.split_mask) : nullptr;
+    B.split_pf = sp ? at<float4>(w, o.split_pf) : nullptr;
+    B.split_pv = sp ? at<int2>(w, o.split_pv) : nullptr;
+    B.part_b.f = sp ? at<float4>(w, o.split_part) : nullptr;
+    B.part_b.vmax = sp ? at<float>(w, o.split_vmax) : nullptr;
+    B.part_b.npen = sp ? at<int>(w, o.split_npen) : nullptr;
     if (c->tangent) {
         TBufs &T = c->T;
         T.n = (int)c->nf;
@@ -865,9 +916,34 @@ void bind(hr_case *c, const Offsets &o)
         }                                                           \
     } while (0)
 
+// A launch at stream priority prio (kept by graph capture as the kernel
+// node's priority).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_prio(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, int prio,
+                        Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // The kernels of one step (prime = 1: evaluate without advancing).  With a
 // side stream (graph capture) the kinematics run on a branch that joins
-// before the ghost pass; without one they run first on the same stream.
+// before the ghost pass (before the reorder when the pass runs split);
+// without one they run first on the same stream.  The split pass: after the
+// reorder (and the summed density), the ghost pass and the boundary
+// particles' pass and partials run on a high-priority branch while the
+// interior particles' pass runs on the main stream; both join before
+// k_finalize.  (With HR_FLAG_TIMING the "ghost" group is then empty and the
+// "pass" group holds both branches.)
 int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side)
 {
     const Consts &K = c->K;
@@ -876,7 +952,9 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (side) {
         CK(cudaEventRecord(c->fork, s));
         CK(cudaStreamWaitEvent(side, c->fork, 0));
-        k_kinematics<<<1, 128, 0, side>>>(K, B, prime);
+        // one block, ahead of the drift's blocks (the split pass's reorder
+        // waits for it)
+        CK(launch_prio(k_kinematics, 1, 128, side, c->prio_hi, K, B, prime));
         if (c->tangent) kt_kinematics<<<1, 32, 0, side>>>(K, B, c->T, prime);
         CK(cudaEventRecord(c->join, side));
     } else {
@@ -888,21 +966,44 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     const bool paper = K.closure == 1;
+    const bool split = K.split != 0;
+    // the split pass's reorder marks the particles near the disk at t^{n+1}
+    if (side && split) CK(cudaStreamWaitEvent(s, c->join, 0));
     if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     else k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
-    if (side) CK(cudaStreamWaitEvent(s, c->join, 0));
-    if (paper) {
-        // closure 1: the summed density needs the disk ghosts at t^{n+1}
-        k_density<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
-        k_ghost<1><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+    if (side && !split) CK(cudaStreamWaitEvent(s, c->join, 0));
+    // closure 1: the summed density needs the disk ghosts at t^{n+1}
+    if (paper) k_density<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    if (split) {
+        cudaStream_t g = side ? side : s;
+        if (side) {
+            CK(cudaEventRecord(c->fork2, s));
+            CK(cudaStreamWaitEvent(side, c->fork2, 0));
+        }
+        if (paper) {
+            CK(launch_prio(k_ghost<1>, c->ghost_blocks, kGhostWarps * 32, g, c->prio_hi, K, B));
+            CK(launch_prio(k_pass_boundary<1>, c->split_blocks, kPassThreads, g, c->prio_hi, K, B, prime));
+        } else {
+            CK(launch_prio(k_ghost<0>, c->ghost_blocks, kGhostWarps * 32, g, c->prio_hi, K, B));
+            CK(launch_prio(k_pass_boundary<0>, c->split_blocks, kPassThreads, g, c->prio_hi, K, B, prime));
+        }
+        CK(launch_prio(k_pass_boundary_sums, c->split_blocks, kPassThreads, g, c->prio_hi, K, B));
+        if (side) CK(cudaEventRecord(c->join2, side));
+        if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
+        if (paper) k_pass<1, 1, kPassInterior><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+        else k_pass<0, 1, kPassInterior><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
+        if (side) CK(cudaStreamWaitEvent(s, c->join2, 0));
     } else {
-        k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+        if (paper) k_ghost<1><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+        else k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, B);
+        if (c->tangent) kt_ghost<<<c->tghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
+        if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     }
-    if (c->tangent) kt_ghost<<<c->tghost_blocks, kGhostWarps * 32, 0, s>>>(K, B, c->T);
-    if (with_events) CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
-    if (c->n3) k_pass_n3<<<c->pass_blocks, kN3Threads, 0, s>>>(K, B, prime);
+    if (split) {
+        // the interior and boundary passes above
+    } else if (c->n3) k_pass_n3<<<c->pass_blocks, kN3Threads, 0, s>>>(K, B, prime);
     else if (c->lanes == 2 && paper) k_pass_lanes<1, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->lanes == 2) k_pass_lanes<0, 2><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     else if (c->lanes == 4 && paper) k_pass_lanes<1, 4><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
@@ -919,8 +1020,8 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
     // kFinalizeBlocks reduction blocks, then one block per probe
     const int fin_blocks = kFinalizeBlocks + K.n_probes;
-    if (paper) k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime);
-    else k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime);
+    if (paper) k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0);
+    else k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0);
     if (c->tangent) kt_finalize<<<1, kTFinThreads, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
@@ -944,7 +1045,8 @@ int capture(hr_case *c)
     if (rc != HR_OK) return rc;
     CK(e);
     c->graph = g;
-    CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    // the split pass's ghost branch runs at its nodes' priority
+    CK(cudaGraphInstantiate(&c->exec, c->graph, cudaGraphInstantiateFlagUseNodePriority));
     if (!c->timing) {
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         int rcm = HR_OK;
@@ -955,7 +1057,7 @@ int capture(hr_case *c)
         if (rcm != HR_OK) return rcm;
         CK(em);
         c->graph_multi = gm;
-        CK(cudaGraphInstantiate(&c->exec_multi, c->graph_multi, 0));
+        CK(cudaGraphInstantiate(&c->exec_multi, c->graph_multi, cudaGraphInstantiateFlagUseNodePriority));
     }
     return HR_OK;
 }
@@ -1002,6 +1104,10 @@ int upload_state(hr_case *c, const float *xy, const float *vel, const float *rho
         CK(cudaMemsetAsync(c->B.n3_flag, 0, (size_t)c->K.n3_tiles_max * 4, c->stream));
         CK(cudaMemsetAsync(c->B.n3_ctl, 0, 8, c->stream));
     }
+    if (c->K.split) {
+        CK(cudaMemsetAsync(c->B.split_n, 0, 8, c->stream));
+        CK(cudaMemsetAsync(c->B.split_mask, 0, ((size_t)c->pass_blocks + 31) / 32 * 4, c->stream));
+    }
     if (c->tangent) {
         // the uploaded state does not depend on the parameters; dt = C h /
         // (c0 + v0) has d dt / d ln c0 = -dt c0 / (c0 + v0)
@@ -1026,13 +1132,35 @@ int prime(hr_case *c)
     return device_status(c);
 }
 
+// Per cell, 1 where the rows of its stencil (reach K.sr; the pass's
+// for_fluid_candidates ranges) hold a wall ghost.  start: the wall ghosts'
+// cell starts (ncell + 1 entries).
+int upload_wall_near(hr_case *c, const std::vector<int> &start)
+{
+    const Consts &K = c->K;
+    const int R = K.sr;
+    std::vector<unsigned char> near((size_t)K.ncell, 0);
+    for (int cc = 0; cc < K.ncell; ++cc) {
+        bool any = false;
+        for (int dy = -R; dy <= R && !any; ++dy) {
+            const int row = cc + dy * K.ncx;
+            const int a = std::min(std::max(row - R, 0), K.ncell);
+            const int b = std::min(std::max(row + R + 1, 0), K.ncell);
+            any = start[b] > start[a];
+        }
+        near[cc] = any ? 1 : 0;
+    }
+    CK(cudaMemcpy(c->B.wall_near, near.data(), near.size(), cudaMemcpyHostToDevice));
+    return HR_OK;
+}
+
 int build_walls(hr_case *c, const Geometry &G)
 {
     const int nw = (int)c->nw;
     if (nw == 0) {
         std::vector<int> ws((size_t)c->K.ncell + 1, 0);
         CK(cudaMemcpy(c->B.wall_start, ws.data(), ws.size() * 4, cudaMemcpyHostToDevice));
-        return HR_OK;
+        return upload_wall_near(c, ws);
     }
     std::vector<float2> pos(nw);
     for (int k = 0; k < nw; ++k) pos[k] = make_float2((float)G.wx[k], (float)G.wy[k]);
@@ -1068,7 +1196,7 @@ int build_walls(hr_case *c, const Geometry &G)
     CK(cudaMemcpy(c->B.gw_kind, skind.data(), nw * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.gw_id, sid.data(), nw * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->B.wall_start, start.data(), start.size() * 4, cudaMemcpyHostToDevice));
-    return HR_OK;
+    return upload_wall_near(c, start);
 }
 
 // ------------------------------------------------------ reverse mode
@@ -1289,7 +1417,8 @@ Bufs slot_bufs(const hr_case *c, const Slot &sl, bool with_S)
 // the scalars snapshot.  The live scalars c->B.S advance as in a plain step.
 int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, int prime)
 {
-    const Consts &K = c->K;
+    Consts K = c->K;
+    K.split = 0;   // the one-kernel pass (the same bits as the split one)
     Bufs Bk = c->B;
     Bk.gd_pos = cur.gd_pos;
     Bufs Bd = c->B;   // the drift reads the previous state
@@ -1317,7 +1446,7 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);
     k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, Bc, prime);
-    k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime);
+    k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime, 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(cur.S, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
     return HR_OK;
@@ -1524,10 +1653,14 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
         c->ws_bytes = o.total;
     }
     bind(c, o);
+    int prio_lo = 0;
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &c->prio_hi) != cudaSuccess)
         return fail(HR_ECUDA);
     for (int k = 0; k < kTimingEvents; ++k)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(HR_ECUDA);
@@ -1774,8 +1907,8 @@ int hr_get_scalars(hr_case *c, double *out, int n)
 int hr_case_info(hr_case *c, int64_t *out, int n)
 {
     if (!c || !out) return HR_EINVAL;
-    const int64_t v[6] = {c->nf, c->nw, c->ng, c->K.ncx, c->K.ncy, c->pass_blocks};
-    for (int k = 0; k < n && k < 6; ++k) out[k] = v[k];
+    const int64_t v[7] = {c->nf, c->nw, c->ng, c->K.ncx, c->K.ncy, c->pass_blocks, c->K.split};
+    for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
     return HR_OK;
 }
 
@@ -2296,6 +2429,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
     std::vector<Bufs> hb(n_cases);
     for (int k = 0; k < n_cases; ++k) {
         hk[k] = cases[k]->K;
+        hk[k].split = 0;   // batched steps take the one-kernel pass
         hb[k] = cases[k]->B;
     }
     if (cudaMemcpy(b->dK, hk.data(), sizeof(Consts) * n_cases, cudaMemcpyHostToDevice) !=
@@ -2420,6 +2554,7 @@ int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
     for (int k = 0; k < n_cases; ++k) {
         hk[k] = cases[k]->K;
         hk[k].n_probes = cases[k]->K.n_probes;
+        hk[k].split = 0;   // the persistent batch takes the one-kernel pass
         hb[k] = cases[k]->B;
     }
     if (cudaMemcpy(b->dK, hk.data(), sizeof(Consts) * n_cases, cudaMemcpyHostToDevice) !=
@@ -2577,6 +2712,8 @@ void hr_destroy(hr_case *c)
     if (c->cap2) cudaStreamDestroy(c->cap2);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
+    if (c->fork2) cudaEventDestroy(c->fork2);
+    if (c->join2) cudaEventDestroy(c->join2);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     adj_free(c);
     delete c;

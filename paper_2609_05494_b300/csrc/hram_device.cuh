@@ -98,6 +98,7 @@ struct Consts {
     // (appended last, so the fields above keep their offsets in the parameter bank)
     int sr;                 // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
     int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
+    int split;              // the interaction pass runs split (interior / boundary particles)
 };
 
 // Device-resident scalars of the case.
@@ -186,6 +187,22 @@ struct Bufs {
     float4 *n3_ext_a;
     float *n3_ext_b;
     int *n3_ctl;
+    // per cell, nonzero where the cell's stencil holds wall ghosts (static)
+    unsigned char *wall_near;
+    // the split pass (K.split; null otherwise): the reorder lists the
+    // boundary particles (those with ghost candidates) and the pass blocks
+    // holding them (counts in split_n[0], split_n[1]; any order) and marks
+    // the blocks in split_mask; the boundary pass leaves each boundary
+    // particle's block-partial terms at its sorted index ({F_disk,x,
+    // F_disk,y, F_wall, dissipation rate}, {max |v| bits, penetration});
+    // the boundary share of each listed block's partials goes to part_b
+    int *split_n;
+    int *split_pi;
+    int *split_bi;
+    unsigned *split_mask;
+    float4 *split_pf;
+    int2 *split_pv;
+    PassPartials part_b;
 };
 
 // ----------------------------------------------- bounds-checked build
@@ -538,6 +555,16 @@ __device__ __forceinline__ bool near_disk(const Consts &K, float x, float y, flo
     return dx * dx + dy * dy < K.disk_reach2;
 }
 
+// A boundary particle: one whose interaction pass looks at ghosts, because
+// its cell c's stencil holds wall ghosts or it lies near the disk (the
+// disk at this step's t^{n+1}).  Every pass form and the reorder decide it
+// with this one test on the same FP32 position.
+__device__ __forceinline__ bool has_ghost_candidates(const Consts &K, const Bufs &B, float2 r, int c)
+{
+    return (K.nw > 0 && B.wall_near[c] != 0) ||
+           (K.ng > 0 && near_disk(K, r.x, r.y, B.S->xc_f, B.S->yc_f));
+}
+
 // The disk ghosts that can lie within the support of a point near the disk.
 // Ghost k sits at angle 2 pi k / ng on the circle of radius R about the
 // centre, so at distance rho from the centre only ghosts within the angle
@@ -872,6 +899,37 @@ __device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
 // D^{n-1}))) and its Tait pressure.  Closure 1: with the predicted velocity
 // v* = v^{n+1/2} + dt/2 a^n that the pass sees, and {a^n, e^n, De^n} for the
 // closing kick (the density comes from k_density).
+// The split pass's lists: the warp's boundary particles (bnd; dst their
+// sorted index) take consecutive slots of split_pi with one atomic, and
+// each pass block holding one is marked in split_mask and listed once in
+// split_bi (one mark per pass block of the warp).  Every lane of the warp
+// takes part.  The lists' order varies from run to run; what is computed
+// from them does not depend on it.
+__device__ __forceinline__ void split_mark(const Bufs &B, int dst, bool bnd)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, bnd);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&B.split_n[0], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (bnd) {
+        B.split_pi[base + __popc(m & ((1u << lane) - 1u))] = dst;
+        const int pb = dst / kPassThreads;
+        const unsigned same = __match_any_sync(m, pb);
+        if (lane == __ffs(same) - 1) {
+            const unsigned bit = 1u << (pb & 31);
+            const unsigned old = atomicOr(&B.split_mask[pb >> 5], bit);
+            if (!(old & bit)) B.split_bi[atomicAdd(&B.split_n[1], 1)] = pb;
+        }
+    }
+}
+
+template <int CL>
+__device__ __forceinline__ int rank_scatter_one(const Consts &K, const Bufs &B, const int i, int prime,
+                                                bool &bnd);
+
 template <int CL>
 __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
@@ -881,7 +939,18 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
         for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
     }
     const int i = bx * blockDim.x + threadIdx.x;
-    if (i >= K.nf) return;
+    bool bnd = false;
+    const int dst = i < K.nf ? rank_scatter_one<CL>(K, B, i, prime, bnd) : -1;
+    if (K.split) split_mark(B, dst, bnd && dst >= 0);
+}
+
+// Particle i of the previous order: its rank, its reorder; returns its
+// sorted index (-1 on a failed bounds check), and with K.split whether it
+// is a boundary particle.
+template <int CL>
+__device__ __forceinline__ int rank_scatter_one(const Consts &K, const Bufs &B, const int i, int prime,
+                                                bool &bnd)
+{
     // the particle's own data first, so their loads overlap the rank loop's
     const int key = B.u_key[i];
     const int id = B.u_id[i];
@@ -889,9 +958,11 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     const float2 D = B.st_D[i];
     const float2 up = B.u_pos[i];
     float2 uv = B.u_vel[i];
-    if (kChecked && !hr_ok(key >= 0 && key <= K.ncell, &B.S->status)) return;
+    if (kChecked && !hr_ok(key >= 0 && key <= K.ncell, &B.S->status)) return -1;
     const int cs = B.cell_start[key], ce = B.cell_start[key + 1];
-    if (kChecked && !hr_ok(0 <= cs && cs < ce && ce <= K.nf, &B.S->status)) return;
+    // (the split pass's test, its loads issued with the cell starts')
+    const bool near = K.split && key != K.ncell && has_ghost_candidates(K, B, up, key);
+    if (kChecked && !hr_ok(0 <= cs && cs < ce && ce <= K.nf, &B.S->status)) return -1;
     float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 a = make_float2(0.f, 0.f);
     if constexpr (CL == 1) {
@@ -927,7 +998,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     // slots kBucket.. of an overflowing cell, placed by the scan
     for (int k = cs + kBucket; k < ce; ++k) rank += HR_DYNAMIC_LOAD(&B.perm_tmp[k]) < id;
     const int dst = cs + rank;
-    if (kChecked && !hr_ok(dst < ce, &B.S->status)) return;
+    if (kChecked && !hr_ok(dst < ce, &B.S->status)) return -1;
     B.s_pos[dst] = up;
     B.s_vel[dst] = uv;
     if constexpr (CL == 1) B.s_ex[dst] = make_float4(a.x, a.y, D.y, D.x);
@@ -935,6 +1006,8 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     B.s_rd[dst] = make_float2(d, D.x);
     B.s_id[dst] = id;
     if (B.perm_dst) B.perm_dst[i] = dst;
+    bnd = near;
+    return dst;
 }
 
 // Predicate mask of the candidates [base, base + cnt), cnt <= 32, in fixed
@@ -1212,10 +1285,12 @@ __device__ __forceinline__ float2 pair_terms(const Consts &K, const Self &I, flo
 // block's warps in a fixed order; k_finalize sums the block partials in
 // compensated FP32.
 
-// Per-thread partials of a pass block.
+// Per-thread partials of a pass block (def: the particle is a boundary
+// particle, whose dissipation goes to the block's boundary share).
 struct PassPart {
     float fdx, fdy, fw, diss, vmax;
     int npen;
+    int def;
 };
 
 // Phase 1 and 2 of particle i (inside the box): fluid neighbours into A.
@@ -1494,14 +1569,17 @@ __device__ __forceinline__ void pass_fluid_staged(const Consts &K, const Bufs &B
 }
 
 // The wall and disk ghost neighbours of a particle (inside the box) into A,
-// their forces into the block partials (split over lanes as for_fluid_candidates).
+// their forces into the block partials (split over lanes as
+// for_fluid_candidates); P.def is set where there are ghost candidates (the
+// test of has_ghost_candidates).
 template <int CL, int R = 0>
 __device__ __forceinline__ void pass_ghosts(const Consts &K, const Bufs &B, float2 ri, int c,
                                             const Self &I, Acc &A, PassPart &P, int lane = 0,
                                             int lanes = 1)
 {
     // wall ghosts (static cell list)
-    if (K.nw > 0) {
+    if (K.nw > 0 && B.wall_near[c] != 0) {
+        P.def = 1;
         for_fluid_candidates<R>(K, B.wall_start, c, K.nw, &B.S->status, [&](int k) {
             const float2 rg = __ldg(&B.gw_pos[k]);
             if (!in_support(ri.x, ri.y, rg.x, rg.y, K.s2)) return;
@@ -1520,6 +1598,7 @@ __device__ __forceinline__ void pass_ghosts(const Consts &K, const Bufs &B, floa
     if (K.ng > 0) {
         const float xc = B.S->xc_f, yc = B.S->yc_f;
         if (near_disk(K, ri.x, ri.y, xc, yc)) {
+            P.def = 1;
             for_disk_arc(K, disk_arc(K, ri.x, ri.y, xc, yc), &B.S->status, [&](int k) {
                 const float2 rg = B.gd_pos[k];
                 if (outside_box(K, rg.x, rg.y)) return;
@@ -1597,9 +1676,15 @@ __device__ __forceinline__ void pass_frozen(const Bufs &B, int i, float2 vi, flo
     B.st_X[i] = make_float2(0.f, 0.f);
 }
 
+// Which particles a pass launch takes: all of them, only the interior ones
+// (no ghost candidates; the split pass's first part, which does not wait for
+// the ghost states), or only the boundary ones (its second part).
+enum PassMode { kPassAll = 0, kPassInterior = 1, kPassBoundary = 2 };
+
 // R: the stencil reach (1 or 2), or 0 to take it from K.sr (batched and
-// persistent kernels, whose cases may differ).
-template <int CL, int R = 0>
+// persistent kernels, whose cases may differ).  kPassBoundary is handed
+// boundary particles only (the reorder's list).
+template <int CL, int R = 0, int MODE = kPassAll>
 __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int i, float dt,
                                             int prime, PassPart &P)
 {
@@ -1608,70 +1693,124 @@ __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int 
     const float4 ai = B.s_aux[i];
     const float2 rd = B.s_rd[i];
     if (outside_box(K, ri.x, ri.y)) {
-        pass_frozen<CL>(B, i, vi, rd);
+        if (MODE != kPassBoundary) pass_frozen<CL>(B, i, vi, rd);
         return;
     }
+    const int c = cell_of<R>(K, ri.x, ri.y);
+    if (MODE == kPassInterior && has_ghost_candidates(K, B, ri, c)) return;
     const float ci = CL == 1 ? K.c_av : ai.w;
     const Self I{ri, vi, fmaf(K.rho0, ai.x, K.rho0), ai.z, ci};
     Acc A{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
-    const int c = cell_of<R>(K, ri.x, ri.y);
     if (R == 2 || (R == 0 && K.sr == 2)) pass_fluid5<CL>(K, B, i, ri, c, I, A);
     else pass_fluid<CL>(K, B, i, ri, c, I, A);
-    pass_finish<CL, R>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
+    if (MODE == kPassInterior) pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
+    else pass_finish<CL, R>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
 }
 
 // Block partials of a pass block: FP32 within the warp, then a fixed-order
-// sum over the block's warps.
+// sum over the block's warps, into out at index bx.  The dissipation rate is
+// summed as two shares, the interior particles' and the boundary particles'
+// (P.def), added last: the split pass forms the two shares in separate
+// kernels and k_finalize adds them, so every pass form gives the same bits.
 template <int NT>
-__device__ __forceinline__ void pass_block_partials(const Bufs &B, const int bx, PassPart P)
+__device__ __forceinline__ void pass_block_partials(const PassPartials &out, const int bx, PassPart P)
 {
-    __shared__ float red[NT / 32][5];
+    __shared__ float red[NT / 32][6];
     __shared__ int redn[NT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // most warps meet no ghost: their ghost sums are all zero, and lane 0
-    // already holds the warp's sum
-    if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0)) {
+    float da = P.def ? 0.f : P.diss, db = P.def ? P.diss : 0.f;
+    // most warps meet no ghost: their ghost sums and boundary share are all
+    // zero, and lane 0 already holds the warp's sum
+    if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0 || P.def)) {
         P.fdx = warp_sum(P.fdx);
         P.fdy = warp_sum(P.fdy);
         P.fw = warp_sum(P.fw);
         P.npen = warp_sum(P.npen);
+        db = warp_sum(db);
     }
-    P.diss = warp_sum(P.diss);
+    da = warp_sum(da);
     P.vmax = warp_max(P.vmax);
     if (lane == 0) {
         red[w][0] = P.fdx;
         red[w][1] = P.fdy;
         red[w][2] = P.fw;
-        red[w][3] = P.diss;
+        red[w][3] = da;
         red[w][4] = P.vmax;
+        red[w][5] = db;
         redn[w] = P.npen;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, v = 0.f;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a5 = 0.f, v = 0.f;
         int np = 0;
         for (int k = 0; k < NT / 32; ++k) {
             a0 += red[k][0];
             a1 += red[k][1];
             a2 += red[k][2];
             a3 += red[k][3];
+            a5 += red[k][5];
             v = fmaxf(v, red[k][4]);
             np += redn[k];
         }
-        B.part.f[bx] = make_float4(a0, a1, a2, a3);
-        B.part.vmax[bx] = v;
-        B.part.npen[bx] = np;
+        out.f[bx] = make_float4(a0, a1, a2, a3 + a5);
+        out.vmax[bx] = v;
+        out.npen[bx] = np;
     }
 }
 
-template <int CL, int R = 0>
+template <int CL, int R = 0, int MODE = kPassAll>
 __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
 {
     const int i = bx * blockDim.x + threadIdx.x;
     const float dt = prime ? 0.0f : B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
-    if (i < K.nf) pass_single<CL, R>(K, B, i, dt, prime, P);
-    pass_block_partials<kPassThreads>(B, bx, P);
+    if (i < K.nf) pass_single<CL, R, MODE>(K, B, i, dt, prime, P);
+    pass_block_partials<kPassThreads>(B.part, bx, P);
+}
+
+// The split pass's boundary part: the listed boundary particles, one per
+// thread in list order (grid-stride), each through the whole pass (fluid
+// and ghost neighbours, epilogue); its block-partial terms are left at its
+// sorted index for b_pass_boundary_sums.
+template <int CL>
+__device__ __forceinline__ void b_pass_boundary(const Consts &K, const Bufs &B, int prime)
+{
+    const int n = B.split_n[0];
+    const float dt = prime ? 0.0f : B.S->dt_f;
+#pragma unroll 1
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = B.split_pi[k];
+        if (kChecked && !hr_ok(i >= 0 && i < K.nf, &B.S->status)) continue;
+        PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        pass_single<CL, 1, kPassBoundary>(K, B, i, dt, prime, P);
+        B.split_pf[i] = make_float4(P.fdx, P.fdy, P.fw, P.diss);
+        B.split_pv[i] = make_int2(__float_as_int(P.vmax), P.npen);
+    }
+}
+
+// The boundary share of the partials of each listed pass block: the block's
+// boundary particles' terms, the others' zero, through the same warp and
+// block sums as pass_block_partials (one 128-thread block per listed pass
+// block, grid-stride).
+__device__ __forceinline__ void b_pass_boundary_sums(const Consts &K, const Bufs &B)
+{
+    const int n = B.split_n[1];
+#pragma unroll 1
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int bx = B.split_bi[k];
+        const int i = bx * kPassThreads + threadIdx.x;
+        PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        if (i < K.nf) {
+            const float2 ri = B.s_pos[i];
+            if (!outside_box(K, ri.x, ri.y) && has_ghost_candidates(K, B, ri, cell_of<1>(K, ri.x, ri.y))) {
+                const float4 f = B.split_pf[i];
+                const int2 v = B.split_pv[i];
+                P = PassPart{f.x, f.y, f.z, f.w, __int_as_float(v.x), v.y, 1};
+            }
+        }
+        pass_block_partials<kPassThreads>(B.part_b, bx, P);
+        __syncthreads();   // the reduction's shared arrays, before the next block
+    }
 }
 
 // The pass block with staged candidates (see PassStage).
@@ -1700,7 +1839,7 @@ __device__ __forceinline__ void b_pass_staged(const Consts &K, const Bufs &B, co
             pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
         }
     }
-    pass_block_partials<kPassThreads>(B, bx, P);
+    pass_block_partials<kPassThreads>(B.part, bx, P);
 }
 
 // The pass with each particle's work split over L consecutive lanes (a
@@ -1790,7 +1929,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_lanes(Consts K, Bufs B, i
     A.X.y = lane_group_sum<L>(A.X.y);
     A.dr = lane_group_sum<L>(A.dr);
     if (live && lane == 0) pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
-    pass_block_partials<kPassThreads>(B, blockIdx.x, P);
+    pass_block_partials<kPassThreads>(B.part, blockIdx.x, P);
 }
 
 // ----------------------------------- a6, a7: probes, accumulators, gate
@@ -1859,9 +1998,14 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 // (two-float) in a fixed tree order, converted to FP64 once at the end.
 // SKIP_EMPTY (the persistent batch, where a case's blocks take the virtual
 // blocks one after another): a reduction block whose slice holds no partial
-// writes its zero sums without the block reduction.
+// writes its zero sums without the block reduction.  split: the pass ran
+// split, and a pass block marked in split_mask has its boundary share in
+// part_b, added to its interior share here (the sum pass_block_partials
+// forms when one kernel takes the whole block).  With K.split the last block
+// also clears the reorder's lists for the next step.
 template <int CL, bool SKIP_EMPTY = false>
-__device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+__device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime,
+                                           int split = 0)
 {
     constexpr int NW = kFinalizeThreads / 32;
     __shared__ F2 redd[4][NW];
@@ -1943,13 +2087,28 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         int npen = 0;
         for (int b = bx * blockDim.x + threadIdx.x; b < K.n_pass_blocks;
              b += nb * blockDim.x) {
-            const float4 f = B.part.f[b];
+            float4 f = B.part.f[b];
+            float v = B.part.vmax[b];
+            int np = B.part.npen[b];
+            if (split) {
+                // every load issued before the mark decides (an unlisted
+                // block's part_b entry is stale and left unused)
+                const unsigned word = B.split_mask[b >> 5];
+                const float4 g = B.part_b.f[b];
+                const float gv = B.part_b.vmax[b];
+                const int gn = B.part_b.npen[b];
+                if ((word >> (b & 31)) & 1u) {
+                    f = make_float4(f.x + g.x, f.y + g.y, f.z + g.z, f.w + g.w);
+                    v = fmaxf(v, gv);
+                    np += gn;
+                }
+            }
             a0 = f2_add(a0, F2{f.x, 0.f});
             a1 = f2_add(a1, F2{f.y, 0.f});
             a2 = f2_add(a2, F2{f.z, 0.f});
             a3 = f2_add(a3, F2{f.w, 0.f});
-            vmax = fmaxf(vmax, B.part.vmax[b]);
-            npen += B.part.npen[b];
+            vmax = fmaxf(vmax, v);
+            npen += np;
         }
         for (int b = bx * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
              b += nb * blockDim.x)
@@ -1992,6 +2151,14 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     const long long k = S.step;
     const double m2 = (double)K.m * (double)K.m;
     __syncthreads();
+    if (K.split) {
+        // every block has read the marks: clear them and the lists
+        for (int k = threadIdx.x; k < (K.n_pass_blocks + 31) / 32; k += blockDim.x) B.split_mask[k] = 0u;
+        if (threadIdx.x == 0) {
+            B.split_n[0] = 0;
+            B.split_n[1] = 0;
+        }
+    }
     if (threadIdx.x == 0) {
         *B.fin_ticket = 0;
         *B.ovf_count = 0;   // the sort's overflow list, for the next step
@@ -2090,10 +2257,21 @@ __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
 // 10 resident blocks per SM (48 registers): 40 warps against 36 at the
 // compiler's own 54 registers, 3 % faster on the 1.125M workload, no spills
 constexpr int kPassMinBlocks = 10;
-template <int CL, int R = 1>
+template <int CL, int R = 1, int MODE = kPassAll>
 __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass(Consts K, Bufs B, int prime)
 {
-    b_pass<CL, R>(K, B, blockIdx.x, gridDim.x, prime);
+    b_pass<CL, R, MODE>(K, B, blockIdx.x, gridDim.x, prime);
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass_boundary(Consts K, Bufs B, int prime)
+{
+    b_pass_boundary<CL>(K, B, prime);
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_pass_boundary_sums(Consts K, Bufs B)
+{
+    b_pass_boundary_sums(K, B);
 }
 
 template <int CL, int SV>
@@ -2103,9 +2281,9 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass_staged(Co
 }
 
 template <int CL>
-__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime)
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime, int split)
 {
-    b_finalize<CL>(K, B, blockIdx.x, gridDim.x, prime);
+    b_finalize<CL>(K, B, blockIdx.x, gridDim.x, prime, split);
 }
 
 // --------------------------------------------- kernels (a batch of cases)

@@ -120,31 +120,34 @@ __device__ __forceinline__ void scan_tile(const Consts &K, const Bufs &B, int bx
 // Two 128-particle pass blocks (pass block indices 2 q and 2 q + 1) in one
 // 256-thread block, with the partials of each half formed as the
 // 128-thread kernel forms them (warp sums, then the half's four warps in
-// order).
+// order; the dissipation as its interior and boundary shares).
 template <int CL>
 __device__ __forceinline__ void pass_pair(const Consts &K, const Bufs &B, int q)
 {
-    __shared__ float red[kPersistThreads / 32][5];
+    __shared__ float red[kPersistThreads / 32][6];
     __shared__ int redn[kPersistThreads / 32];
     const int i = q * kPersistThreads + threadIdx.x;
     const float dt = B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
     if (i < K.nf) pass_single<CL, 1>(K, B, i, dt, 0, P);   // 3 x 3 stencil (cell_factor >= 1)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0)) {
+    float da = P.def ? 0.f : P.diss, db = P.def ? P.diss : 0.f;
+    if (__any_sync(0xffffffffu, P.fdx != 0.f || P.fdy != 0.f || P.fw != 0.f || P.npen != 0 || P.def)) {
         P.fdx = warp_sum(P.fdx);
         P.fdy = warp_sum(P.fdy);
         P.fw = warp_sum(P.fw);
         P.npen = warp_sum(P.npen);
+        db = warp_sum(db);
     }
-    P.diss = warp_sum(P.diss);
+    da = warp_sum(da);
     P.vmax = warp_max(P.vmax);
     if (lane == 0) {
         red[w][0] = P.fdx;
         red[w][1] = P.fdy;
         red[w][2] = P.fw;
-        red[w][3] = P.diss;
+        red[w][3] = da;
         red[w][4] = P.vmax;
+        red[w][5] = db;
         redn[w] = P.npen;
     }
     __syncthreads();
@@ -153,17 +156,18 @@ __device__ __forceinline__ void pass_pair(const Consts &K, const Bufs &B, int q)
         const int half = threadIdx.x / kPassThreads;
         const int bx = 2 * q + half;
         if (bx < K.n_pass_blocks) {
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, v = 0.f;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a5 = 0.f, v = 0.f;
             int np = 0;
             for (int k = half * NW; k < half * NW + NW; ++k) {
                 a0 += red[k][0];
                 a1 += red[k][1];
                 a2 += red[k][2];
                 a3 += red[k][3];
+                a5 += red[k][5];
                 v = fmaxf(v, red[k][4]);
                 np += redn[k];
             }
-            B.part.f[bx] = make_float4(a0, a1, a2, a3);
+            B.part.f[bx] = make_float4(a0, a1, a2, a3 + a5);
             B.part.vmax[bx] = v;
             B.part.npen[bx] = np;
         }

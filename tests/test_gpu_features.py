@@ -246,6 +246,7 @@ def test_full_size_one_step_against_oracle():
     p, xy = impact_case(p)
     vel, rho = perturbed(p, xy, seed=3, v_amp=10.0, rho_rel=0.005)
     g, o = both(p, xy, vel, rho)
+    assert g.info()["split"] == 1   # the size takes the split pass by default
     dt = o.scalars()["dt"]
     g.step()
     o.step()
@@ -256,6 +257,23 @@ def test_full_size_one_step_against_oracle():
     assert_p_close("full_size_1.125M", p, sg["p"], o, dt)
     assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
     assert g.scalars()["dt"] == pytest.approx(o.scalars()["dt"], rel=1e-6)
+
+
+def test_full_size_split_pass_bitwise():
+    # the bench workload's split pass against the one-kernel pass over a few
+    # impact steps: every array, probe and scalar equal
+    p = casegen.config_scaling(2e-4)
+    p, xy = impact_case(p)
+    a = Case(p, xy, split=False, probe_capacity=64)
+    b = Case(p, xy, probe_capacity=64)
+    assert a.info()["split"] == 0 and b.info()["split"] == 1
+    a.run(6)
+    b.run(6)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.probe_pressure(), b.probe_pressure())
+    assert a.scalars() == b.scalars()
 
 
 def test_two_way_coupling_matches_oracle():

@@ -382,6 +382,92 @@ def test_staged_pass_variants_bitwise(stage, kind):
     assert a.scalars() == b.scalars()
 
 
+def _split_case(kind):
+    if kind == "impact":
+        p, xy = impact_case()
+        return p, xy, None
+    if kind == "paper":
+        p, xy = impact_case(closure=1)
+        return p, xy, None
+    if kind == "end_walls":
+        # a closed box: end-wall cells start every cell row, so most pass
+        # blocks hold boundary and interior particles together
+        p, xy = impact_case(end_walls=1)
+        vel, _ = perturbed(p, xy, seed=9, v_amp=5.0, rho_rel=0.0)
+        return p, xy, vel
+    if kind == "coupled":
+        # two-way coupling: the disk ghosts' force (the boundary share of the
+        # partials) moves the disk
+        p, xy = impact_case(motion=3, t_ramp=2e-6, v0=300.0)
+        return p, xy, None
+    p = casegen.base_params()   # dense: stencil rows over 32 candidates
+    p.update(dx=1e-3, Lx=0.02, W=0.02, Ng=0, wall_layers=3, gy=0.0)
+    xy = casegen.fluid_lattice(0.012, 0.012, 0.5e-3, 0.01, 21, disk=None)
+    xy[:, 0] += 0.004
+    xy = xy.astype(np.float32)
+    vel, _ = perturbed(p, xy, seed=5, v_amp=3.0, rho_rel=0.0)
+    return p, xy, vel
+
+
+@pytest.mark.parametrize("kind", ["impact", "paper", "end_walls", "coupled", "dense"])
+def test_split_pass_bitwise(kind):
+    # the interior particles in one kernel beside the ghost pass, the
+    # boundary particles after it: every array, probe and scalar (the ghost
+    # forces and the dissipation, whose block sums the two parts form
+    # separately) equals the one-kernel pass's
+    p, xy, vel = _split_case(kind)
+    a = Case(p, xy, vel, split=False)
+    b = Case(p, xy, vel, split=True)
+    assert a.info()["split"] == 0 and b.info()["split"] == 1
+    a.run(40)
+    b.run(40)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.probe_pressure(), b.probe_pressure())
+    assert a.scalars() == b.scalars()
+    if kind == "coupled":
+        assert b.scalars()["vproj"] < 300.0
+
+
+def test_split_pass_one_step_against_oracle():
+    p, xy = impact_case()
+    vel, rho = perturbed(p, xy, seed=7)
+    g, o = both(p, xy, vel, rho, split=True)
+    assert g.info()["split"] == 1
+    dt = o.scalars()["dt"]
+    g.step()
+    o.step()
+    sg, fo = g.get_state(), o.fluid()
+    assert np.abs(sg["rho"] / fo["rho"] - 1.0).max() <= 1e-5
+    assert_p_close("split", p, sg["p"], o, dt)
+    assert np.abs(sg["xy"] - fo["xy"]).max() <= 1e-6
+    assert g.scalars()["dt"] == pytest.approx(o.scalars()["dt"], rel=1e-6)
+
+
+def test_split_case_in_a_batch_and_alone():
+    # a split case taken into a batch (whose steps use the one-kernel pass)
+    # continues bit for bit as it would alone, and runs split again after
+    from paper_2609_05494_b300 import Batch
+    p, xy = impact_case()
+    a = Case(p, xy, split=True)
+    b = Case(p, xy, split=True)
+    a.run(10)
+    b.run(10)
+    t_end = a.scalars()["t"] + 3e-6
+    with Batch([b], t_end) as bt:
+        bt.run()
+    n = int(round(b.scalars()["step"] - a.scalars()["step"]))
+    assert n > 0
+    a.run(n)
+    a.run(10)
+    b.run(10)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert a.scalars() == b.scalars()
+
+
 @pytest.mark.parametrize("closure", [0, 1])
 def test_dense_rows_over_32_candidates(closure):
     # a patch at half the spacing the smoothing length is set for: about 27

@@ -61,6 +61,32 @@ def test_workspace_bytes_is_host_only_and_grows_with_n(lib):
     assert lib.hr_workspace_bytes(C.byref(bad), 5625, C.byref(a)) == _lib.HR_EINVAL
 
 
+def test_split_pass_flags_checked_on_the_host(lib):
+    # the split pass: refused with the one-kernel flag, a pass variant, the
+    # tangent mode or the 5 x 5 stencil; its lists enlarge the workspace,
+    # at any size when asked for, from 262,144 particles by default
+    lib.hr_workspace_bytes.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]
+    base = casegen.config_parity()
+    n = C.c_size_t()
+
+    def ws(flags, nf=5625, **kw):
+        p = make_params(dict(base, **kw), flags)
+        rc = lib.hr_workspace_bytes(C.byref(p), nf, C.byref(n))
+        return rc, n.value
+
+    S, F = _lib.HR_FLAG_PASS_SPLIT, _lib.HR_FLAG_PASS_FUSED
+    for bad in (S | F, S | _lib.HR_FLAG_PASS_LANES2, S | _lib.HR_FLAG_NEWTON3,
+                S | _lib.HR_FLAG_STAGE_POS, S | _lib.HR_FLAG_TANGENT):
+        assert ws(bad, dt_mode=1)[0] == _lib.HR_EINVAL, bad
+    assert ws(S, cell_factor=0.5)[0] == _lib.HR_EINVAL
+    rc0, fused = ws(0)
+    rc1, split = ws(S)
+    assert rc0 == rc1 == _lib.HR_OK and split > fused
+    big = 300000
+    assert ws(0, big)[1] > ws(F, big)[1] == ws(F, big)[1]
+    assert ws(0, big)[1] == ws(S, big)[1]
+
+
 def test_jacobian_refuses_a_zero_parameter():
     from paper_2609_05494_b300.grad import jacobian
     p = casegen.config_parity()
