@@ -863,9 +863,9 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # the interaction pass runs split at this size (interior particles beside
-    # the ghost pass, boundary particles after it): 9 launches per step, else 7
+    # the ghost pass, boundary particles after it): 8 launches per step, else 6
     split = bool(case.info()["split"])
-    launches_per_step = 9 if split else 7
+    launches_per_step = 8 if split else 6
     # pairs per step (for the flop count), from the neighbour lists of the start state
     off, _ = case.neighbours()
     pairs_fluid_rows = int(off[n] - off[0])

@@ -54,6 +54,7 @@ constexpr int kMultiSteps = 4;
 // (grid-stride over their lists)
 constexpr long long kSplitMinParticles = 262144;
 constexpr int kSplitBlocks = 592;
+constexpr int kSplitListBlocks = 296;   // extra blocks of the ghost launch
 
 // ------------------------------------------------ auxiliary device kernels
 
@@ -935,45 +936,45 @@ cudaError_t launch_prio(void (*kern)(KArgs...), int grid, int block, cudaStream_
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// The kernels of one step (prime = 1: evaluate without advancing).  With a
-// side stream (graph capture) the kinematics run on a branch that joins
-// before the ghost pass (before the reorder when the pass runs split);
-// without one they run first on the same stream.  The split pass: after the
-// reorder (and the summed density), the ghost pass and the boundary
-// particles' pass and partials run on a high-priority branch while the
-// interior particles' pass runs on the main stream; both join before
-// k_finalize.  (With HR_FLAG_TIMING the "ghost" group is then empty and the
-// "pass" group holds both branches.)
+// The kernels of one step (prime = 1: evaluate without advancing).  The
+// drift's first block evaluates the kinematics; in tangent mode they run,
+// with their derivatives, on a side branch that joins before the ghost pass
+// (side stream: graph capture), or first on the same stream.  The split
+// pass: after the reorder (and the summed density), the boundary lists, the
+// ghost pass and the boundary particles' pass and partials run on a
+// high-priority branch while the interior particles' pass runs on the main
+// stream; both join before k_finalize.  (With HR_FLAG_TIMING the "ghost"
+// group is then empty and the "pass" group holds both branches.)
 int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side)
 {
     const Consts &K = c->K;
     const Bufs &B = c->B;
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
-    if (side) {
+    // the kinematics: in the drift's first block, or (tangent mode, whose
+    // kinematics derivatives follow them) on a branch beside the drift and
+    // the sort
+    const bool kin_branch = c->tangent;
+    if (kin_branch && side) {
         CK(cudaEventRecord(c->fork, s));
         CK(cudaStreamWaitEvent(side, c->fork, 0));
-        // one block, ahead of the drift's blocks (the split pass's reorder
-        // waits for it)
-        CK(launch_prio(k_kinematics, 1, 128, side, c->prio_hi, K, B, prime));
-        if (c->tangent) kt_kinematics<<<1, 32, 0, side>>>(K, B, c->T, prime);
+        k_kinematics<<<1, 128, 0, side>>>(K, B, prime);
+        kt_kinematics<<<1, 32, 0, side>>>(K, B, c->T, prime);
         CK(cudaEventRecord(c->join, side));
-    } else {
+    } else if (kin_branch) {
         k_kinematics<<<1, 128, 0, s>>>(K, B, prime);
-        if (c->tangent) kt_kinematics<<<1, 32, 0, s>>>(K, B, c->T, prime);
+        kt_kinematics<<<1, 32, 0, s>>>(K, B, c->T, prime);
     }
-    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime, kin_branch ? 0 : 1);
     if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
     const bool paper = K.closure == 1;
-    const bool split = K.split != 0;
-    // the split pass's reorder marks the particles near the disk at t^{n+1}
-    if (side && split) CK(cudaStreamWaitEvent(s, c->join, 0));
+    const bool split = K.split != 0;   // (never with the tangent mode)
     if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     else k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_scatter<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
-    if (side && !split) CK(cudaStreamWaitEvent(s, c->join, 0));
+    if (kin_branch && side) CK(cudaStreamWaitEvent(s, c->join, 0));
     // closure 1: the summed density needs the disk ghosts at t^{n+1}
     if (paper) k_density<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (split) {
@@ -982,11 +983,13 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
             CK(cudaEventRecord(c->fork2, s));
             CK(cudaStreamWaitEvent(side, c->fork2, 0));
         }
+        // the ghost pass, and in its extra blocks the boundary lists
+        const int gb = c->ghost_blocks + kSplitListBlocks;
         if (paper) {
-            CK(launch_prio(k_ghost<1>, c->ghost_blocks, kGhostWarps * 32, g, c->prio_hi, K, B));
+            CK(launch_prio(k_ghost<1>, gb, kGhostWarps * 32, g, c->prio_hi, K, B));
             CK(launch_prio(k_pass_boundary<1>, c->split_blocks, kPassThreads, g, c->prio_hi, K, B, prime));
         } else {
-            CK(launch_prio(k_ghost<0>, c->ghost_blocks, kGhostWarps * 32, g, c->prio_hi, K, B));
+            CK(launch_prio(k_ghost<0>, gb, kGhostWarps * 32, g, c->prio_hi, K, B));
             CK(launch_prio(k_pass_boundary<0>, c->split_blocks, kPassThreads, g, c->prio_hi, K, B, prime));
         }
         CK(launch_prio(k_pass_boundary_sums, c->split_blocks, kPassThreads, g, c->prio_hi, K, B));
@@ -1440,7 +1443,7 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     k_kinematics<<<1, 128, 0, c->cap2>>>(K, Bk, prime);
     ka_kin<<<1, 32, 0, c->cap2>>>(K, c->B.S, cur.kin);
     CK(cudaEventRecord(c->join, c->cap2));
-    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime, 0);
     k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs);
     k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
     CK(cudaStreamWaitEvent(s, c->join, 0));

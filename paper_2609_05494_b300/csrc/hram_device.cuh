@@ -189,10 +189,10 @@ struct Bufs {
     int *n3_ctl;
     // per cell, nonzero where the cell's stencil holds wall ghosts (static)
     unsigned char *wall_near;
-    // the split pass (K.split; null otherwise): the reorder lists the
-    // boundary particles (those with ghost candidates) and the pass blocks
-    // holding them (counts in split_n[0], split_n[1]; any order) and marks
-    // the blocks in split_mask; the boundary pass leaves each boundary
+    // the split pass (K.split; null otherwise): the reorder marks in
+    // split_mask the pass blocks holding boundary particles (those with
+    // ghost candidates); the ghost launch's extra blocks list those blocks and their boundary
+    // particles (counts in split_n[0], split_n[1]; any order); the boundary pass leaves each boundary
     // particle's block-partial terms at its sorted index ({F_disk,x,
     // F_disk,y, F_wall, dissipation rate}, {max |v| bits, penetration});
     // the boundary share of each listed block's partials goes to part_b
@@ -899,30 +899,52 @@ __device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
 // D^{n-1}))) and its Tait pressure.  Closure 1: with the predicted velocity
 // v* = v^{n+1/2} + dt/2 a^n that the pass sees, and {a^n, e^n, De^n} for the
 // closing kick (the density comes from k_density).
-// The split pass's lists: the warp's boundary particles (bnd; dst their
-// sorted index) take consecutive slots of split_pi with one atomic, and
-// each pass block holding one is marked in split_mask and listed once in
-// split_bi (one mark per pass block of the warp).  Every lane of the warp
-// takes part.  The lists' order varies from run to run; what is computed
-// from them does not depend on it.
-__device__ __forceinline__ void split_mark(const Bufs &B, int dst, bool bnd)
+// The split pass's marks: the pass block of each boundary particle (bnd;
+// dst its sorted index) is marked in split_mask, once per pass block of the
+// warp, by an atomic whose result is not waited for.  Every lane of the
+// warp takes part.
+__device__ __forceinline__ void split_flag(const Bufs &B, int dst, bool bnd)
 {
     const int lane = threadIdx.x & 31;
     const unsigned m = __ballot_sync(0xffffffffu, bnd);
     if (m == 0u) return;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&B.split_n[0], __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
     if (bnd) {
-        B.split_pi[base + __popc(m & ((1u << lane) - 1u))] = dst;
         const int pb = dst / kPassThreads;
         const unsigned same = __match_any_sync(m, pb);
-        if (lane == __ffs(same) - 1) {
-            const unsigned bit = 1u << (pb & 31);
-            const unsigned old = atomicOr(&B.split_mask[pb >> 5], bit);
-            if (!(old & bit)) B.split_bi[atomicAdd(&B.split_n[1], 1)] = pb;
+        if (lane == __ffs(same) - 1) atomicOr(&B.split_mask[pb >> 5], 1u << (pb & 31));
+    }
+}
+
+// The split pass's lists, from the marks (extra blocks of the ghost pass's
+// launch): the marked pass blocks into split_bi, their boundary particles
+// into split_pi (one atomic per warp for its slots).  Each NT-thread block
+// takes NT / kPassThreads pass blocks at a time (bx, nbx: its index among
+// the nbx list blocks, grid-stride); the lists' order varies from run to
+// run, what is computed from them does not depend on it.
+template <int NT>
+__device__ __forceinline__ void b_split_list(const Consts &K, const Bufs &B, const int bx, const int nbx)
+{
+    constexpr int P = NT / kPassThreads;
+    const int lane = threadIdx.x & 31, t = threadIdx.x % kPassThreads, h = threadIdx.x / kPassThreads;
+#pragma unroll 1
+    for (int b0 = bx * P; b0 < K.n_pass_blocks; b0 += nbx * P) {
+        const int b = b0 + h;   // this thread's pass block (uniform in each warp)
+        if (b >= K.n_pass_blocks || !((B.split_mask[b >> 5] >> (b & 31)) & 1u)) continue;
+        const int i = b * kPassThreads + t;
+        bool bnd = false;
+        if (i < K.nf) {
+            const float2 r = B.s_pos[i];
+            bnd = !outside_box(K, r.x, r.y) && has_ghost_candidates(K, B, r, cell_of<1>(K, r.x, r.y));
         }
+        const unsigned m = __ballot_sync(0xffffffffu, bnd);
+        if (m != 0u) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&B.split_n[0], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (bnd) B.split_pi[base + __popc(m & ((1u << lane) - 1u))] = i;
+        }
+        if (t == 0) B.split_bi[atomicAdd(&B.split_n[1], 1)] = b;
     }
 }
 
@@ -941,7 +963,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
     const int i = bx * blockDim.x + threadIdx.x;
     bool bnd = false;
     const int dst = i < K.nf ? rank_scatter_one<CL>(K, B, i, prime, bnd) : -1;
-    if (K.split) split_mark(B, dst, bnd && dst >= 0);
+    if (K.split) split_flag(B, dst, bnd && dst >= 0);
 }
 
 // Particle i of the previous order: its rank, its reorder; returns its
@@ -2221,8 +2243,12 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
 // HR_NO_STEP_KERNELS, so the kernels below are defined in one unit only.)
 #ifndef HR_NO_STEP_KERNELS
 
-__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
+// kin: block 0 first advances t and places the disk (b_kinematics, one
+// block's work, done long before the drift's last blocks), so the step
+// needs no separate kinematics launch.
+__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime, int kin)
 {
+    if (kin && blockIdx.x == 0) b_kinematics(K, B, 0, 1, prime);
     b_drift_key(K, B, blockIdx.x, gridDim.x, prime);
 }
 
@@ -2248,10 +2274,16 @@ __global__ void __launch_bounds__(256) k_density(Consts K, Bufs B, int prime)
     b_density(K, B, blockIdx.x, gridDim.x, prime);
 }
 
+// Blocks past K.n_ghost_blocks (a split-pass step launches them) build the
+// split pass's lists.
 template <int CL>
 __global__ void __launch_bounds__(kGhostWarps * 32) k_ghost(Consts K, Bufs B)
 {
-    b_ghost<CL>(K, B, blockIdx.x, gridDim.x);
+    if ((int)blockIdx.x >= K.n_ghost_blocks) {
+        b_split_list<kGhostWarps * 32>(K, B, blockIdx.x - K.n_ghost_blocks, gridDim.x - K.n_ghost_blocks);
+        return;
+    }
+    b_ghost<CL>(K, B, blockIdx.x, K.n_ghost_blocks);
 }
 
 // 10 resident blocks per SM (48 registers): 40 warps against 36 at the
