@@ -936,8 +936,8 @@ cudaError_t launch_prio(void (*kern)(KArgs...), int grid, int block, cudaStream_
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// The kernels of one step (prime = 1: evaluate without advancing).  The
-// drift's first block evaluates the kinematics; in tangent mode they run,
+// The kernels of one step (prime = 1: evaluate without advancing).  An
+// extra block of the scan launch evaluates the kinematics; in tangent mode they run,
 // with their derivatives, on a side branch that joins before the ghost pass
 // (side stream: graph capture), or first on the same stream.  The split
 // pass: after the reorder (and the summed density), the boundary lists, the
@@ -950,7 +950,7 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     const Consts &K = c->K;
     const Bufs &B = c->B;
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
-    // the kinematics: in the drift's first block, or (tangent mode, whose
+    // the kinematics: in an extra block of the scan launch, or (tangent mode, whose
     // kinematics derivatives follow them) on a branch beside the drift and
     // the sort
     const bool kin_branch = c->tangent;
@@ -964,10 +964,10 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
         k_kinematics<<<1, 128, 0, s>>>(K, B, prime);
         kt_kinematics<<<1, 32, 0, s>>>(K, B, c->T, prime);
     }
-    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime, kin_branch ? 0 : 1);
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
-    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, B);
+    k_scan_apply<<<c->n_tiles + (kin_branch ? 0 : 1), kScanThreads, 0, s>>>(K, B, prime, kin_branch ? 0 : 1);
     const bool paper = K.closure == 1;
     const bool split = K.split != 0;   // (never with the tangent mode)
     if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
@@ -1443,8 +1443,8 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     k_kinematics<<<1, 128, 0, c->cap2>>>(K, Bk, prime);
     ka_kin<<<1, 32, 0, c->cap2>>>(K, c->B.S, cur.kin);
     CK(cudaEventRecord(c->join, c->cap2));
-    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime, 0);
-    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs);
+    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
+    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs, prime, 0);
     k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
     CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);

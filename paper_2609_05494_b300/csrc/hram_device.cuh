@@ -2243,12 +2243,8 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
 // HR_NO_STEP_KERNELS, so the kernels below are defined in one unit only.)
 #ifndef HR_NO_STEP_KERNELS
 
-// kin: block 0 first advances t and places the disk (b_kinematics, one
-// block's work, done long before the drift's last blocks), so the step
-// needs no separate kinematics launch.
-__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime, int kin)
+__global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
 {
-    if (kin && blockIdx.x == 0) b_kinematics(K, B, 0, 1, prime);
     b_drift_key(K, B, blockIdx.x, gridDim.x, prime);
 }
 
@@ -2257,9 +2253,16 @@ __global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
     b_kinematics(K, B, blockIdx.x, gridDim.x, prime);
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B)
+// kin: one block past the scan tiles advances t and places the disk
+// (b_kinematics) on an SM of its own beside the tiles, so the step needs no
+// kinematics launch; the reorder that follows sees the disk at t^{n+1}.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B, int prime, int kin)
 {
-    b_scan_apply(K, B, blockIdx.x, gridDim.x);
+    if (kin && blockIdx.x == gridDim.x - 1) {
+        b_kinematics(K, B, 0, 1, prime);
+        return;
+    }
+    b_scan_apply(K, B, blockIdx.x, gridDim.x - kin);
 }
 
 
