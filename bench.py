@@ -321,6 +321,52 @@ def pass_variant_benchmark(stream, xy, p, flush, steps=50):
     return out
 
 
+def close_benchmark(stream, flush, big_xy, big_p, steps=60, blocks=3, warmup=5):
+    """A/B of the step close: inside each step's own graph
+    (HR_FLAG_CLOSE_INLINE) against the default, deferred to the next step's
+    graph beside its drift.  ms per step of the graphs without timing events
+    (L2 flushed before every step; the two forms in alternating blocks of
+    steps/blocks steps), and whether the end states and scalars are equal
+    bit for bit."""
+    import torch
+    from paper_2609_05494_b300 import Case
+    p1, xy1 = workload(1e-3)
+    out = []
+    for name, q, x in (("300 x 150 mm, dx = 1 mm", p1, xy1),
+                       ("300 x 150 mm, dx = 0.2 mm", big_p, big_xy)):
+        with torch.cuda.stream(stream):
+            forms = {"inline": Case(q, x, stream=stream, close_inline=True,
+                                    probe_capacity=steps + warmup + 8),
+                     "deferred": Case(q, x, stream=stream, probe_capacity=steps + warmup + 8)}
+        for c in forms.values():
+            c.run(warmup)
+        torch.cuda.synchronize()
+        ms = {k: 0.0 for k in forms}
+        per = steps // blocks
+        for _ in range(blocks):
+            for key, c in forms.items():
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(per)]
+                for k in range(per):
+                    with torch.cuda.stream(stream):
+                        flush.fill_(k & 0xFF)
+                        ev[k][0].record(stream)
+                        c.step()
+                        ev[k][1].record(stream)
+                torch.cuda.synchronize()
+                ms[key] += sum(a.elapsed_time(b) for a, b in ev)
+        sa, sb = forms["inline"].get_state(), forms["deferred"].get_state()
+        equal = (all(np.array_equal(sa[k], sb[k]) for k in sa) and
+                 forms["inline"].scalars() == forms["deferred"].scalars())
+        for c in forms.values():
+            c.close()
+        out.append({"case": name, "particles": int(x.shape[0]),
+                    "inline_ms_per_step": ms["inline"] / (per * blocks),
+                    "deferred_ms_per_step": ms["deferred"] / (per * blocks),
+                    "bitwise_equal": equal})
+    return out
+
+
 def tangent_benchmark(stream, big_xy=None, big_p=None, big_steps=20):
     """Cost of the tangent-linear mode (derivatives of the peak probe pressure
     and the wall impulse along alpha, c0, tau): the 22,500-particle fixed-dt
@@ -779,6 +825,10 @@ def run_only(args):
     elif args.only == "small":
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         out = small_case_benchmark(stream, flush, steps=args.steps)
+    elif args.only == "close":
+        p, xy = workload(args.dx)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = close_benchmark(stream, flush, xy, p, steps=args.steps)
     elif args.only == "passvar":
         p, xy = workload(args.dx)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -826,8 +876,9 @@ def main():
     ap.add_argument("--no-production", action="store_true")
     ap.add_argument("--no-passvar", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-close", action="store_true")
     ap.add_argument("--only", choices=("adjoint", "tangent", "sweep", "passvar", "small", "scaling",
-                                       "batch"),
+                                       "batch", "close"),
                     help="run one leg alone on the channel at --dx for --steps steps "
                          "(profiling runs); prints that leg's JSON")
     args = ap.parse_args()
@@ -871,7 +922,9 @@ def main():
     pairs_fluid_rows = int(off[n] - off[0])
     for _ in range(args.warmup):
         case.step()
-    case.sync()
+    # (the last warm-up step's close stays pending: the first timed step's
+    # graph runs it, so the K timed steps hold K closes)
+    torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -944,6 +997,7 @@ def main():
     production = None if args.no_production else production_benchmark(stream)
     passvar = None if args.no_passvar else pass_variant_benchmark(stream, xy, p, flush)
     small = None if args.no_small else small_case_benchmark(stream, flush)
+    close_ab = None if args.no_close else close_benchmark(stream, flush, xy, p)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -966,7 +1020,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.dx, world),
         "timing": "step graph without timing events; kernel durations from a second run of "
-                  "the workload with in-graph CUDA events",
+                  "the workload with in-graph CUDA events; each step graph runs the previous "
+                  "step's close in the first blocks of its drift launch (k_close_drift), so "
+                  "the drift group holds it and the finalize group is empty",
         "status": status,
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT,
@@ -1002,6 +1058,7 @@ def main():
         "production": production,
         "pass_variants": passvar,
         "small_cases": small,
+        "step_close": close_ab,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

@@ -105,6 +105,19 @@ extern "C" {
                             at any size (same conditions otherwise) */
 #define HR_FLAG_PASS_FUSED 256 /* never run the interaction pass split (not
                             with HR_FLAG_PASS_SPLIT) */
+#define HR_FLAG_CLOSE_INLINE 512 /* close every step inside its own step graph.
+                            By default a step graph leaves the step's close
+                            (the reductions of the pass partials, the probes,
+                            the FP64 accumulators, the CFL gate) to the next
+                            step's graph, where it runs beside that step's
+                            drift, which derives its dt from the maximum |v|
+                            of the last pass directly; the library runs a
+                            pending close itself before any call that reads,
+                            saves, replaces or batches the case, so every
+                            result is the same bit for bit.  Cases with
+                            HR_FLAG_TANGENT or the two-way coupled disk
+                            (motion 3, whose next step needs the close's
+                            force) always close inline */
 
 /* Case parameters.  Field meanings follow the paper's notation.
  *  dx, h_over_dx   particle spacing and smoothing length ratio (h = 1.3 dx)
@@ -200,7 +213,9 @@ int hr_init_case(const hr_params *p, const float *xy, int64_t n_fluid, const flo
 /* One time step U^{n+1} = T(L(G(U^n))) (operator order of Section 4.6; the
  * velocity Stoermer-Verlet advance with the CFL gate of Section 2.5, eq. cfl),
  * replayed from the captured step graph, asynchronous.  Returns the last
- * known status. */
+ * known status.  Unless the case was created with HR_FLAG_CLOSE_INLINE the
+ * step's close runs with the next step or before the next call that reads
+ * the case (HR_FLAG_CLOSE_INLINE). */
 int hr_step(hr_case *c);
 
 /* n_steps steps of hr_step (Sections 4.6 and 2.5); with t_end > 0 stops at
@@ -255,9 +270,10 @@ int hr_get_ghosts(hr_case *c, float *xy, float *p, float *rho, float *vel, int64
  * W_boundary, wall_impulse, dissipation, diss_rate (14 doubles). */
 int hr_get_scalars(hr_case *c, double *out, int n);
 
-/* Counts: n_fluid, n_wall, n_disk, ncx, ncy, pass_blocks, and 1 when the
- * interaction pass runs split (HR_FLAG_PASS_SPLIT) (7 int64; the first n of
- * them are written). */
+/* Counts: n_fluid, n_wall, n_disk, ncx, ncy, pass_blocks, 1 when the
+ * interaction pass runs split (HR_FLAG_PASS_SPLIT), and 1 when the step
+ * graphs defer each step's close to the next (not HR_FLAG_CLOSE_INLINE)
+ * (8 int64; the first n of them are written). */
 int hr_case_info(hr_case *c, int64_t *out, int n);
 
 /* Neighbour sets of the current state as CSR over all points (fluid IDs,

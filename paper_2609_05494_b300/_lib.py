@@ -41,6 +41,7 @@ HR_FLAG_PASS_LANES2 = 32
 HR_FLAG_PASS_LANES4 = 64
 HR_FLAG_PASS_SPLIT = 128
 HR_FLAG_PASS_FUSED = 256
+HR_FLAG_CLOSE_INLINE = 512
 
 EXPORTS = (
     "hr_workspace_bytes", "hr_init_case", "hr_step", "hr_run", "hr_sync", "hr_probe_pressure",

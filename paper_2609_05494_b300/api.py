@@ -78,12 +78,15 @@ class Case:
     (results equal to rounding).  ``split`` runs the interaction pass as
     interior and boundary kernels beside the ghost pass (True), never
     (False), or by the library's size rule (None); results are identical.
+    ``close_inline`` closes every step (partial sums, probes, FP64
+    accumulators, CFL gate) inside its own step graph instead of beside the
+    next step's drift; results are identical.
     """
 
     def __init__(self, params: dict, xy, vel=None, rho=None, stream=None, timing: bool = False,
                  probe_capacity: int = 1 << 16, diag_every: int = 0, torch_workspace: bool = True,
                  tangent: bool = False, stage: int = 0, newton3: bool = False,
-                 lanes: int = 1, split: bool | None = None):
+                 lanes: int = 1, split: bool | None = None, close_inline: bool = False):
         L = lib()
         xy = _f32(xy)
         n = xy.shape[0]
@@ -102,6 +105,8 @@ class Case:
         flags |= {1: 0, 2: _lib.HR_FLAG_PASS_LANES2, 4: _lib.HR_FLAG_PASS_LANES4}[lanes]
         if split is not None:
             flags |= _lib.HR_FLAG_PASS_SPLIT if split else _lib.HR_FLAG_PASS_FUSED
+        if close_inline:
+            flags |= _lib.HR_FLAG_CLOSE_INLINE
         self._p = make_params(params, flags, probe_capacity, diag_every)
         self.n_probes = self._p.n_probes
         nbytes = C.c_size_t(0)
@@ -242,10 +247,10 @@ class Case:
         return dict(zip(SCALAR_FIELDS, s.tolist()))
 
     def info(self) -> dict:
-        v = np.empty(7, dtype=np.int64)
-        check(lib().hr_case_info(self._h, _ptr(v), 7), "hr_case_info")
-        return dict(zip(("n_fluid", "n_wall", "n_disk", "ncx", "ncy", "pass_blocks", "split"),
-                        (int(x) for x in v)))
+        v = np.empty(8, dtype=np.int64)
+        check(lib().hr_case_info(self._h, _ptr(v), 8), "hr_case_info")
+        return dict(zip(("n_fluid", "n_wall", "n_disk", "ncx", "ncy", "pass_blocks", "split",
+                         "close_deferred"), (int(x) for x in v)))
 
     def neighbours(self) -> tuple[np.ndarray, np.ndarray]:
         """CSR over all points (fluid IDs, wall ghosts, disk ghosts), ids ascending."""

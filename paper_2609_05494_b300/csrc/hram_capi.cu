@@ -505,6 +505,11 @@ struct hr_case {
     int lanes = 1;                // pass variant: lanes per particle
     int split_blocks = 0;         // blocks of the split pass's boundary kernels
     cudaEvent_t fork2 = nullptr, join2 = nullptr;   // the split pass's ghost branch
+    // the deferred step close: the step graphs leave each step's close to run
+    // beside the next step's drift (defer), and the host settles a pending
+    // one (settle) before it reads or hands on the case
+    bool defer = false;
+    bool pending = false;
     int prio_hi = 0;              // the device's greatest stream priority (that branch's)
     TBufs T{};
     int tpass_blocks = 0;
@@ -860,6 +865,9 @@ void bind(hr_case *c, const Offsets &o)
     c->io = at<float>(w, o.io);
     c->tangent = (c->P.flags & HR_FLAG_TANGENT) != 0;
     c->stage = (c->P.flags & HR_FLAG_STAGE_POS) ? 1 : (c->P.flags & HR_FLAG_STAGE_ALL) ? 2 : 0;
+    // (the two-way coupled disk needs the close's force before its next
+    // step; the tangent mode's close carries derivatives of the gate)
+    c->defer = !(c->P.flags & HR_FLAG_CLOSE_INLINE) && !c->tangent && c->K.motion != 3;
     B.s_ex = c->P.closure == 1 ? at<float4>(w, o.s_ex) : nullptr;
     B.perm_dst = nullptr;
     c->n3 = c->K.n3 != 0;
@@ -945,11 +953,16 @@ cudaError_t launch_prio(void (*kern)(KArgs...), int grid, int block, cudaStream_
 // high-priority branch while the interior particles' pass runs on the main
 // stream; both join before k_finalize.  (With HR_FLAG_TIMING the "ghost"
 // group is then empty and the "pass" group holds both branches.)
-int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side)
+int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side,
+                bool defer = false)
 {
     const Consts &K = c->K;
     const Bufs &B = c->B;
+    const int fin_blocks = kFinalizeBlocks + K.n_probes;   // reduction blocks, then one per probe
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
+    // defer (step graphs, never with the tangent mode): the last step's
+    // close, if pending, in the first blocks of the drift launch
+    // (k_close_drift); this step's close is left pending
     // the kinematics: in an extra block of the scan launch, or (tangent mode, whose
     // kinematics derivatives follow them) on a branch beside the drift and
     // the sort
@@ -964,10 +977,16 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
         k_kinematics<<<1, 128, 0, s>>>(K, B, prime);
         kt_kinematics<<<1, 32, 0, s>>>(K, B, c->T, prime);
     }
-    k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
+    if (defer && K.closure == 1)
+        k_close_drift<1><<<fin_blocks + c->drift_blocks, 256, 0, s>>>(K, B, fin_blocks, K.split ? 1 : 0);
+    else if (defer)
+        k_close_drift<0><<<fin_blocks + c->drift_blocks, 256, 0, s>>>(K, B, fin_blocks, K.split ? 1 : 0);
+    else
+        k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
     if (c->tangent) kt_drift<<<c->drift_blocks, 256, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
-    k_scan_apply<<<c->n_tiles + (kin_branch ? 0 : 1), kScanThreads, 0, s>>>(K, B, prime, kin_branch ? 0 : 1);
+    k_scan_apply<<<c->n_tiles + (kin_branch ? 0 : 1), kScanThreads, 0, s>>>(K, B, prime, kin_branch ? 0 : 1,
+                                                                         defer ? 1 : 0);
     const bool paper = K.closure == 1;
     const bool split = K.split != 0;   // (never with the tangent mode)
     if (paper) k_rank_scatter<1><<<c->drift_blocks, 256, 0, s>>>(K, B, prime);
@@ -1021,10 +1040,13 @@ int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStr
     else k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, B, prime);
     if (c->tangent) kt_pass<<<c->tpass_blocks, kTPassThreads, 0, s>>>(K, B, c->T, prime);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-    // kFinalizeBlocks reduction blocks, then one block per probe
-    const int fin_blocks = kFinalizeBlocks + K.n_probes;
-    if (paper) k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0);
-    else k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0);
+    if (defer) {
+        // the close runs in the next step's graph (or when the host settles)
+    } else if (paper) {
+        k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0, 0);
+    } else {
+        k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, s>>>(K, B, prime, split ? 1 : 0, 0);
+    }
     if (c->tangent) kt_finalize<<<1, kTFinThreads, 0, s>>>(K, B, c->T, prime, c->tpass_blocks);
     if (with_events) CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     CK(cudaGetLastError());
@@ -1042,7 +1064,7 @@ int capture(hr_case *c)
         c->graph = nullptr;
     }
     CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_step(c, c->cap, 0, c->timing, c->cap2);
+    const int rc = launch_step(c, c->cap, 0, c->timing, c->cap2, c->defer);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (rc != HR_OK) return rc;
@@ -1054,7 +1076,7 @@ int capture(hr_case *c)
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         int rcm = HR_OK;
         for (int q = 0; q < kMultiSteps && rcm == HR_OK; ++q)
-            rcm = launch_step(c, c->cap, 0, false, c->cap2);
+            rcm = launch_step(c, c->cap, 0, false, c->cap2, c->defer);
         cudaGraph_t gm = nullptr;
         const cudaError_t em = cudaStreamEndCapture(c->cap, &gm);
         if (rcm != HR_OK) return rcm;
@@ -1065,8 +1087,27 @@ int capture(hr_case *c)
     return HR_OK;
 }
 
+// Runs the close that the last step graph left pending, then the CFL gate
+// (k_finalize mode 2), so the case's scalars, probe records and status are
+// those of a close at the end of the step, bit for bit.  Asynchronous.
+int settle(hr_case *c)
+{
+    if (!c->pending) return HR_OK;
+    c->pending = false;
+    const int fin_blocks = kFinalizeBlocks + c->K.n_probes;
+    const int split = c->K.split ? 1 : 0;
+    if (c->K.closure == 1)
+        k_finalize<1><<<fin_blocks, kFinalizeThreads, 0, c->stream>>>(c->K, c->B, 0, split, 2);
+    else
+        k_finalize<0><<<fin_blocks, kFinalizeThreads, 0, c->stream>>>(c->K, c->B, 0, split, 2);
+    CK(cudaGetLastError());
+    return HR_OK;
+}
+
 int device_status(hr_case *c)
 {
+    const int rs = settle(c);
+    if (rs != HR_OK) return rs;
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
     int st = 0;
@@ -1444,12 +1485,12 @@ int launch_tape_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &pr
     ka_kin<<<1, 32, 0, c->cap2>>>(K, c->B.S, cur.kin);
     CK(cudaEventRecord(c->join, c->cap2));
     k_drift_key<<<c->drift_blocks, 256, 0, s>>>(K, Bd, prime);
-    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs, prime, 0);
+    k_scan_apply<<<c->n_tiles, kScanThreads, 0, s>>>(K, Bs, prime, 0, 0);
     k_rank_scatter<0><<<c->drift_blocks, 256, 0, s>>>(K, Br, prime);
     CK(cudaStreamWaitEvent(s, c->join, 0));
     k_ghost<0><<<c->ghost_blocks, kGhostWarps * 32, 0, s>>>(K, Bc);
     k_pass<0><<<c->pass_blocks, kPassThreads, 0, s>>>(K, Bc, prime);
-    k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime, 0);
+    k_finalize<0><<<kFinalizeBlocks + K.n_probes, kFinalizeThreads, 0, s>>>(K, Bc, prime, 0, 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(cur.S, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
     return HR_OK;
@@ -1693,8 +1734,11 @@ int hr_step(hr_case *c)
     if (!c || !c->exec) return HR_EINVAL;
     if (c->sticky < 0) return c->sticky;
     if (cudaGraphLaunch(c->exec, c->stream) != cudaSuccess) return c->sticky = HR_ECUDA;
+    c->pending = c->defer;
     c->host_step++;
     if (c->P.diag_every > 0 && c->host_step % c->P.diag_every == 0) {
+        const int rs = settle(c);
+        if (rs != HR_OK) return c->sticky = rs;
         k_diag_partial<<<c->diag_blocks, kDiagThreads, 0, c->stream>>>(c->K, c->B, c->diag_part);
         k_diag_final<<<1, 32, 0, c->stream>>>(c->K, c->B, c->diag_part, c->diag_blocks,
                                               c->diag_out, c->diag_hist, c->diag_rec,
@@ -1720,6 +1764,7 @@ static int run_steps(hr_case *c, int64_t k)
             if (c->sticky < 0) return c->sticky;
             if (cudaGraphLaunch(c->exec_multi, c->stream) != cudaSuccess)
                 return c->sticky = HR_ECUDA;
+            c->pending = c->defer;
             c->host_step += kMultiSteps;
             k -= kMultiSteps;
         } else {
@@ -1744,6 +1789,7 @@ int hr_run(hr_case *c, int64_t n_steps, double t_end)
     int64_t done = 0;
     for (;;) {
         double sc[2];
+        if (settle(c) != HR_OK) return HR_ECUDA;
         if (cudaMemcpyAsync(sc, &c->B.S->t, 16, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return HR_ECUDA;
         const int st = device_status(c);
@@ -1794,6 +1840,7 @@ int hr_probe_times(hr_case *c, double *host_out, int64_t cap, int64_t *n_out)
 int hr_diagnostics(hr_case *c, hr_diag *out)
 {
     if (!c || !out) return HR_EINVAL;
+    if (settle(c) != HR_OK) return HR_ECUDA;
     k_diag_partial<<<c->diag_blocks, kDiagThreads, 0, c->stream>>>(c->K, c->B, c->diag_part);
     k_diag_final<<<1, 32, 0, c->stream>>>(c->K, c->B, c->diag_part, c->diag_blocks, c->diag_out,
                                           c->diag_hist, -1, c->diag_cap);
@@ -1825,6 +1872,7 @@ int hr_get_state(hr_case *c, float *xy, float *vel, float *rho, float *p, int64_
     const NvtxRange nvtx_range("hr_get_state");
     if (!c) return HR_EINVAL;
     if (cap < c->nf) return HR_ERANGE;
+    if (settle(c) != HR_OK) return HR_ECUDA;
     const size_t n = (size_t)c->nf;
     float2 *dxy = reinterpret_cast<float2 *>(c->io);
     float2 *dv = dxy + n;
@@ -1844,6 +1892,7 @@ int hr_get_energy(hr_case *c, float *e, float *de, int64_t cap)
 {
     if (!c || c->K.closure != 1) return HR_EINVAL;
     if (cap < c->nf) return HR_ERANGE;
+    if (settle(c) != HR_OK) return HR_ECUDA;
     const size_t n = (size_t)c->nf;
     float *de_ = c->io, *dd = c->io + n;
     k_unsort_energy<<<c->drift_blocks, 256, 0, c->stream>>>(c->K, c->B, de_, dd);
@@ -1910,14 +1959,16 @@ int hr_get_scalars(hr_case *c, double *out, int n)
 int hr_case_info(hr_case *c, int64_t *out, int n)
 {
     if (!c || !out) return HR_EINVAL;
-    const int64_t v[7] = {c->nf, c->nw, c->ng, c->K.ncx, c->K.ncy, c->pass_blocks, c->K.split};
-    for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
+    const int64_t v[8] = {c->nf, c->nw, c->ng, c->K.ncx, c->K.ncy, c->pass_blocks, c->K.split,
+                          c->defer ? 1 : 0};
+    for (int k = 0; k < n && k < 8; ++k) out[k] = v[k];
     return HR_OK;
 }
 
 int hr_debug_neighbors(hr_case *c, int64_t *offsets, int32_t *ids, int64_t cap, int64_t *n_pairs)
 {
     if (!c || !offsets) return HR_EINVAL;
+    if (settle(c) != HR_OK) return HR_ECUDA;
     const long long npts = c->nf + c->nw + c->ng;
     int *dcount = nullptr;
     long long *doff = nullptr;
@@ -2158,6 +2209,7 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
     while (done < plain_end) {
         const long long k = std::min<long long>(a->L, plain_end - done);
         if ((rc = run_steps(c, k)) != HR_OK) return rc;
+        if ((rc = settle(c)) != HR_OK) return rc;   // the checkpoint takes the scalars
         done += k;
         if (done < n_steps && (rc = save_ckpt(c, a->ckpt[done / a->L], s)) != HR_OK) return rc;
     }
@@ -2171,6 +2223,7 @@ int hr_adjoint_forward(hr_case *c, int64_t n_steps, int32_t checkpoint_every, do
         if ((rc = tape_to_live(c, a->tape[(size_t)(len - 1)], s)) != HR_OK) return rc;
         c->host_step += len;
     }
+    if ((rc = settle(c)) != HR_OK) return rc;
     CK(cudaMemcpyAsync(a->S_final, c->B.S, sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
     st = device_status(c);
     if (st < 0) return st;
@@ -2327,6 +2380,20 @@ __global__ void k_batch_count_done(const Bufs *Bs, int n, int *out)
     }
 }
 
+// The batch's cases with a step close still pending from their own step
+// graphs: settled on their streams and waited for, before the batch reads
+// or steps them on its own stream.
+int settle_cases(hr_batch *b)
+{
+    for (hr_case *c : b->cases) {
+        if (!c->pending) continue;
+        const int rc = settle(c);
+        if (rc != HR_OK) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return HR_OK;
+}
+
 int batch_launch(hr_batch *b, cudaStream_t s, cudaStream_t side)
 {
     const Consts *K = b->dK;
@@ -2381,6 +2448,7 @@ int hr_batch_create(hr_case *const *cases, int n_cases, double t_end, int schedu
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }
+    if (settle_cases(b) != HR_OK) return fail(HR_ECUDA);
     b->stream = (cudaStream_t)cuda_stream;
     // per-kernel block maps: (case, local block, blocks of that case), in the
     // order of the schedule: 0 case after case, 1 round robin over the cases,
@@ -2503,6 +2571,7 @@ int hr_batch_create_persistent(hr_case *const *cases, int n_cases, double t_end,
             return fail(HR_EINVAL);
         b->cases.push_back(cases[k]);
     }
+    if (settle_cases(b) != HR_OK) return fail(HR_ECUDA);
     b->stream = (cudaStream_t)cuda_stream;
     b->closure = cases[0]->K.closure;
     b->persistent = true;
@@ -2611,6 +2680,7 @@ static int persist_run(hr_batch *b, int64_t max_steps)
 int hr_batch_step(hr_batch *b)
 {
     const NvtxRange nvtx_range("hr_batch_step");
+    if (b && settle_cases(b) != HR_OK) return HR_ECUDA;
     if (b && b->persistent) {
         const int rc = persist_run(b, 1);
         if (rc == HR_OK) b->steps++;
@@ -2637,6 +2707,7 @@ int hr_batch_run(hr_batch *b, int64_t max_steps, int64_t *steps_done)
 {
     const NvtxRange nvtx_range("hr_batch_run");
     if (!b) return HR_EINVAL;
+    if (settle_cases(b) != HR_OK) return HR_ECUDA;
     const int n = (int)b->cases.size();
     int64_t done_steps = 0;
     int rc = HR_OK;

@@ -116,6 +116,14 @@ struct Scalars {
     // single-precision copies for the per-particle kernels (the FP64 pipe of
     // the B300 is far too slow to convert doubles in every thread)
     float dt_f, ratio_f, xc_f, yc_f, vproj_f, aproj_f;
+    // The deferred step close (a step graph whose closing reductions run in
+    // the next step, beside its drift): vmax_bits, max |v| over the fluid
+    // and the ghosts of the last pass (float bits, atomic max of the block
+    // maxima; the graph's kinematics clears it before its pass); close_pending,
+    // that step's close has not run yet; dt_stale, dt and its copies still
+    // hold that step's step size (the next one follows from vmax_bits).
+    unsigned vmax_bits;
+    int close_pending, dt_stale, pad_;
 };
 
 // Per-block partials of the interaction pass, structure of arrays so the
@@ -151,7 +159,7 @@ struct Bufs {
     int *tile_sum;
     int *bucket;     // (ncell + 1) x kBucket: the fluid IDs of each cell, in slot order
     int4 *ovf;       // {cell, fluid ID, slot} of the particles past their cell's bucket (nf)
-    int *ovf_count;  // entries of ovf this step (reset by k_finalize)
+    int *ovf_count;  // entries of ovf this step (reset by k_rank_scatter)
     int *perm_tmp;   // the IDs of slots >= kBucket at cell start + slot (overflowing cells only)
     int *perm_dst;   // previous slot -> slot of this step (tangent mode only, else null)
     float4 *s_ex;    // closure 1: {a^n, e^n, De^n} in this step's cell order (else null)
@@ -467,6 +475,36 @@ __device__ __forceinline__ F2 f2_warp_sum(F2 v)
     return v;
 }
 
+// a6, the CFL gate (eq. cfl): dt = C h / (c0 + max |v|) over fluid and
+// ghost velocities, in FP32 (a float ulp of dt is far below every
+// tolerance).  dt_mode 1 takes the fixed host value instead.
+__device__ __forceinline__ float cfl_dt_f(const Consts &K, float vmax)
+{
+    return __fdiv_rn(K.cfl_h_f, K.c0 + vmax);
+}
+
+// The deferred step close: the next step's size from the last pass's max |v|
+// (Scalars::vmax_bits), into the fields the close at the end of a step
+// writes (dt_prev, dt, dt_f, ratio_f), with the same arithmetic.  One thread.
+__device__ __forceinline__ void advance_dt(const Consts &K, Scalars *S)
+{
+    double dtn;
+    float dtf;
+    if (K.dt_mode == 1) {
+        dtn = K.dt_fixed;
+        dtf = (float)dtn;
+    } else {
+        dtf = cfl_dt_f(K, __uint_as_float(S->vmax_bits));
+        dtn = (double)dtf;
+    }
+    if (!(dtn > 1e-14)) atomicOr(&S->status, ST_DT);
+    S->ratio_f = __fdiv_rn(dtf, S->dt_f);
+    S->dt_prev = S->dt;
+    S->dt = dtn;
+    S->dt_f = dtf;
+    S->dt_stale = 0;
+}
+
 // Projectile kinematics in closed form (FP64).  Section 2.6.3 ramp,
 // exponential decay with time constant tau (motion 0), the paper's quadratic
 // drag law after the ramp (motion 1, Section 2.7), constant acceleration
@@ -612,7 +650,7 @@ __device__ __forceinline__ void for_disk_arc(const Consts &K, const DiskArc &A, 
 
 // ----------------------------------------------------- a2: drift and key
 
-__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, int prime);
+__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, float dt);
 
 // Opening kick, XSPH drift, wall enforcement and cell key (the predicted
 // density is formed in k_rank_scatter from the same state).  prime = 1
@@ -621,10 +659,19 @@ __device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const
 // lanes: the previous step's cell order keeps most of a warp's particles in
 // a few runs.  (Counting the scan's tile sums the same way was slower: a few
 // dozen tile counters take every warp's atomic and serialise them.)
-__device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+// defer: a step graph with the deferred close, where the step size may
+// still be the last step's (Scalars::dt_stale): each thread then forms this
+// step's from the last pass's max |v|, as the close would have.
+__device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime,
+                                            int defer = 0)
 {
+    float dt = 0.0f;
+    if (!prime) {
+        dt = (defer && K.dt_mode == 0 && B.S->dt_stale) ? cfl_dt_f(K, __uint_as_float(B.S->vmax_bits))
+                                                        : B.S->dt_f;
+    }
     const int i = bx * blockDim.x + threadIdx.x;
-    const int key = i < K.nf ? b_drift_one(K, B, i, prime) : -1;
+    const int key = i < K.nf ? b_drift_one(K, B, i, dt) : -1;
     const int lane = threadIdx.x & 31;
     const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;   // lanes 0..lane
     // runs of equal values in consecutive lanes: head lane and length
@@ -688,10 +735,10 @@ __device__ __forceinline__ void b_drift_key(const Consts &K, const Bufs &B, cons
     }
 }
 
-// The per-particle part of b_drift_key; returns the cell key.
-__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, int prime)
+// The per-particle part of b_drift_key (dt: this step's size, 0 when
+// priming); returns the cell key.
+__device__ __forceinline__ int b_drift_one(const Consts &K, const Bufs &B, const int i, float dt)
 {
-    const float dt = prime ? 0.0f : B.S->dt_f;
     float2 r = B.s_pos[i];
     const float2 v = B.st_vel[i];
     const float2 a = B.st_a[i];
@@ -762,11 +809,23 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int *
 // a1: advances t by dt (unless priming), evaluates the projectile
 // kinematics at t^{n+1} in FP64 and places the disk ghost ring there.  One
 // block; in the step graph it runs on a branch beside the drift and the sort.
-__device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime)
+// defer: a step graph with the deferred close.  The step size is brought
+// up to date first if the last step's close has not done it (dt_stale), and
+// the fluid and ghost maximum of |v| is cleared for this step's passes; the
+// step then leaves its close pending (run beside the next step's drift, or
+// by the host before it reads the case).
+__device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime,
+                                             int defer = 0)
 {
     __shared__ double kin[2];
     if (threadIdx.x == 0) {
         Scalars *S = B.S;
+        if (defer) {
+            if (S->dt_stale) advance_dt(K, S);
+            S->vmax_bits = 0u;
+            S->close_pending = 1;
+            S->dt_stale = 1;
+        }
         const double dt = prime ? 0.0 : S->dt;
         S->t += dt;
         double x, v, a;
@@ -893,8 +952,8 @@ __device__ __forceinline__ void n3_table(const Consts &K, const Bufs &B)
 // Stable order inside a cell: rank by fluid ID among the cell's members
 // (its bucket, and for a cell of more than kBucket particles the rest, which
 // the scan placed in perm_tmp).  Then the reorder into the SoA arrays of this step.  Block 0
-// first clears the tile sums for the next step's k_drift_key (and builds the
-// Newton-3 pass's tile table).  Closure 0: with the
+// first clears the tile sums and the overflow count for the next step's
+// k_drift_key (and builds the Newton-3 pass's tile table).  Closure 0: with the
 // predicted density rho~ = band(rho^n + dt (D^n + (dt^n / dt^{n-1})(D^n -
 // D^{n-1}))) and its Tait pressure.  Closure 1: with the predicted velocity
 // v* = v^{n+1/2} + dt/2 a^n that the pass sees, and {a^n, e^n, De^n} for the
@@ -959,6 +1018,7 @@ __device__ __forceinline__ void b_rank_scatter(const Consts &K, const Bufs &B, c
         if (K.n3) n3_table(K, B);
         const int n_tiles = (K.ncell + 2 + kScanTile - 1) / kScanTile;
         for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) B.tile_sum[t] = 0;
+        if (threadIdx.x == 0) *B.ovf_count = 0;   // the scan has placed the list
     }
     const int i = bx * blockDim.x + threadIdx.x;
     bool bnd = false;
@@ -1228,6 +1288,7 @@ __device__ __forceinline__ void b_ghost(const Consts &K, const Bufs &B, const in
         float v = 0.0f;
         for (int k = 0; k < kGhostWarps; ++k) v = fmaxf(v, red[k]);
         B.ghost_vmax[bx] = v;
+        atomicMax(&B.S->vmax_bits, __float_as_uint(v));   // for the deferred close
     }
 }
 
@@ -1735,7 +1796,8 @@ __device__ __forceinline__ void pass_single(const Consts &K, const Bufs &B, int 
 // (P.def), added last: the split pass forms the two shares in separate
 // kernels and k_finalize adds them, so every pass form gives the same bits.
 template <int NT>
-__device__ __forceinline__ void pass_block_partials(const PassPartials &out, const int bx, PassPart P)
+__device__ __forceinline__ void pass_block_partials(const PassPartials &out, const int bx, PassPart P,
+                                                    unsigned *vall)
 {
     __shared__ float red[NT / 32][6];
     __shared__ int redn[NT / 32];
@@ -1777,6 +1839,9 @@ __device__ __forceinline__ void pass_block_partials(const PassPartials &out, con
         out.f[bx] = make_float4(a0, a1, a2, a3 + a5);
         out.vmax[bx] = v;
         out.npen[bx] = np;
+        // the step's max |v| for the deferred close (v >= 0: its float bits
+        // order as the values do)
+        atomicMax(vall, __float_as_uint(v));
     }
 }
 
@@ -1787,7 +1852,7 @@ __device__ __forceinline__ void b_pass(const Consts &K, const Bufs &B, const int
     const float dt = prime ? 0.0f : B.S->dt_f;
     PassPart P{0.f, 0.f, 0.f, 0.f, 0.f, 0};
     if (i < K.nf) pass_single<CL, R, MODE>(K, B, i, dt, prime, P);
-    pass_block_partials<kPassThreads>(B.part, bx, P);
+    pass_block_partials<kPassThreads>(B.part, bx, P, &B.S->vmax_bits);
 }
 
 // The split pass's boundary part: the listed boundary particles, one per
@@ -1830,7 +1895,7 @@ __device__ __forceinline__ void b_pass_boundary_sums(const Consts &K, const Bufs
                 P = PassPart{f.x, f.y, f.z, f.w, __int_as_float(v.x), v.y, 1};
             }
         }
-        pass_block_partials<kPassThreads>(B.part_b, bx, P);
+        pass_block_partials<kPassThreads>(B.part_b, bx, P, &B.S->vmax_bits);
         __syncthreads();   // the reduction's shared arrays, before the next block
     }
 }
@@ -1861,7 +1926,7 @@ __device__ __forceinline__ void b_pass_staged(const Consts &K, const Bufs &B, co
             pass_finish<CL>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
         }
     }
-    pass_block_partials<kPassThreads>(B.part, bx, P);
+    pass_block_partials<kPassThreads>(B.part, bx, P, &B.S->vmax_bits);
 }
 
 // The pass with each particle's work split over L consecutive lanes (a
@@ -1951,7 +2016,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_lanes(Consts K, Bufs B, i
     A.X.y = lane_group_sum<L>(A.X.y);
     A.dr = lane_group_sum<L>(A.dr);
     if (live && lane == 0) pass_close<CL>(K, B, i, vi, ai, rd, dt, prime, A, P);
-    pass_block_partials<kPassThreads>(B.part, blockIdx.x, P);
+    pass_block_partials<kPassThreads>(B.part, blockIdx.x, P, &B.S->vmax_bits);
 }
 
 // ----------------------------------- a6, a7: probes, accumulators, gate
@@ -2025,10 +2090,18 @@ __device__ __forceinline__ float probe_value(const Consts &K, const Bufs &B, flo
 // part_b, added to its interior share here (the sum pass_block_partials
 // forms when one kernel takes the whole block).  With K.split the last block
 // also clears the reorder's lists for the next step.
+// mode 0: the close at the end of the step, all of the above.  mode 1: the
+// deferred close of the last step (Scalars::close_pending; nothing to do
+// otherwise), beside the next step's drift: all but the CFL gate, which that
+// step's drift and kinematics apply from Scalars::vmax_bits; it writes only
+// the scalars it owns (the drift sets status bits meanwhile).  mode 2: as
+// mode 1, then the CFL gate as advance_dt, which leaves the scalars as mode 0
+// would have (run by the host before it reads the case).
 template <int CL, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime,
-                                           int split = 0)
+                                           int split = 0, int mode = 0)
 {
+    if (mode != 0 && !__ldcg(&B.S->close_pending)) return;   // nothing deferred
     constexpr int NW = kFinalizeThreads / 32;
     __shared__ F2 redd[4][NW];
     __shared__ float redv[NW];
@@ -2132,9 +2205,10 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
             vmax = fmaxf(vmax, v);
             npen += np;
         }
-        for (int b = bx * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
-             b += nb * blockDim.x)
-            vmax = fmaxf(vmax, B.ghost_vmax[b]);
+        if (mode == 0)   // (the deferred close has no CFL gate to feed)
+            for (int b = bx * blockDim.x + threadIdx.x; b < K.n_ghost_blocks;
+                 b += nb * blockDim.x)
+                vmax = fmaxf(vmax, B.ghost_vmax[b]);
         block_reduce(a0, a1, a2, a3, vmax, npen);
         if (threadIdx.x == 0) {
             for (int k = 0; k < 4; ++k) {
@@ -2183,24 +2257,11 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     }
     if (threadIdx.x == 0) {
         *B.fin_ticket = 0;
-        *B.ovf_count = 0;   // the sort's overflow list, for the next step
         S.Fdx = m2 * ((double)tot[0].hi + (double)tot[0].lo);
         S.Fdy = m2 * ((double)tot[1].hi + (double)tot[1].lo);
         S.Fwall = m2 * ((double)tot[2].hi + (double)tot[2].lo);
         S.diss_rate = (double)tot[3].hi + (double)tot[3].lo;
         if (totn > 0) S.status |= ST_PENETRATION;
-        // a6: CFL gate over fluid and ghost velocities, FP32 (a float ulp of
-        // dt is far below every tolerance); dt_mode 1 uses the fixed host value
-        float dtf;
-        double dtn;
-        if (K.dt_mode == 1) {
-            dtn = K.dt_fixed;
-            dtf = (float)dtn;
-        } else {
-            dtf = __fdiv_rn(K.cfl_h_f, K.c0 + totv);
-            dtn = (double)dtf;
-        }
-        if (!(dtn > 1e-14)) S.status |= ST_DT;
         if (!prime) {
             if (k < K.probe_cap) {
                 B.probe_t[k] = S.t;
@@ -2210,11 +2271,25 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
             }
             S.step = k + 1;
         }
-        S.ratio_f = prime ? 1.0f : __fdiv_rn(dtf, S.dt_f);
-        S.done = (S.t_end > 0.0 && S.t >= S.t_end) ? 1 : 0;
-        S.dt_prev = prime ? dtn : dt;
-        S.dt = dtn;
-        S.dt_f = dtf;
+        if (mode == 0) {
+            // a6: the CFL gate over fluid and ghost velocities (cfl_dt_f);
+            // dt_mode 1 uses the fixed host value
+            float dtf;
+            double dtn;
+            if (K.dt_mode == 1) {
+                dtn = K.dt_fixed;
+                dtf = (float)dtn;
+            } else {
+                dtf = cfl_dt_f(K, totv);
+                dtn = (double)dtf;
+            }
+            if (!(dtn > 1e-14)) S.status |= ST_DT;
+            S.ratio_f = prime ? 1.0f : __fdiv_rn(dtf, S.dt_f);
+            S.done = (S.t_end > 0.0 && S.t >= S.t_end) ? 1 : 0;
+            S.dt_prev = prime ? dtn : dt;
+            S.dt = dtn;
+            S.dt_f = dtf;
+        }
     } else if (threadIdx.x == 32) {
         // the FP64 time integrals, beside thread 0 (another warp)
         if (!prime) {
@@ -2232,8 +2307,29 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
-        reinterpret_cast<double *>(B.S)[k] = reinterpret_cast<const double *>(&S)[k];
+    if (mode == 0) {
+        for (int k = threadIdx.x; k < (int)(sizeof(Scalars) / 8); k += blockDim.x)
+            reinterpret_cast<double *>(B.S)[k] = reinterpret_cast<const double *>(&S)[k];
+        return;
+    }
+    // the deferred close writes only what it owns
+    if (threadIdx.x == 0) {
+        Scalars *G = B.S;
+        G->Fdx = S.Fdx;
+        G->Fdy = S.Fdy;
+        G->Fwall = S.Fwall;
+        G->diss_rate = S.diss_rate;
+        G->Wb = S.Wb;
+        G->impulse = S.impulse;
+        G->diss = S.diss;
+        G->hist_n = S.hist_n;
+        G->step = S.step;
+        for (int q = 0; q < K.n_probes; ++q) G->probe_imp[q] = S.probe_imp[q];
+        const int bits = S.status & (ST_PENETRATION | ST_PROBEFULL);
+        if (bits) atomicOr(&G->status, bits);
+        G->close_pending = 0;
+        if (mode == 2) advance_dt(K, G);
+    }
 }
 
 
@@ -2248,6 +2344,23 @@ __global__ void __launch_bounds__(256) k_drift_key(Consts K, Bufs B, int prime)
     b_drift_key(K, B, blockIdx.x, gridDim.x, prime);
 }
 
+// A step graph with the deferred close: its first n_close blocks run the
+// last step's close (b_finalize mode 1, nothing if none is pending), the
+// rest the drift, which takes this step's dt from the last pass's max |v|
+// if that close has not set it.  The close's blocks come first so that they
+// start with the drift's first wave; the scan launch that follows (and
+// rewrites the cell starts the probes read) waits for both.
+static_assert(kFinalizeThreads == 256, "the close's blocks are the drift's size");
+template <int CL>
+__global__ void __launch_bounds__(256, 8) k_close_drift(Consts K, Bufs B, int n_close, int split)
+{
+    if ((int)blockIdx.x < n_close) {
+        b_finalize<CL>(K, B, blockIdx.x, n_close, 0, split, 1);
+        return;
+    }
+    b_drift_key(K, B, blockIdx.x - n_close, gridDim.x - n_close, 0, 1);
+}
+
 __global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
 {
     b_kinematics(K, B, blockIdx.x, gridDim.x, prime);
@@ -2256,10 +2369,10 @@ __global__ void __launch_bounds__(128) k_kinematics(Consts K, Bufs B, int prime)
 // kin: one block past the scan tiles advances t and places the disk
 // (b_kinematics) on an SM of its own beside the tiles, so the step needs no
 // kinematics launch; the reorder that follows sees the disk at t^{n+1}.
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B, int prime, int kin)
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Consts K, Bufs B, int prime, int kin, int defer)
 {
     if (kin && blockIdx.x == gridDim.x - 1) {
-        b_kinematics(K, B, 0, 1, prime);
+        b_kinematics(K, B, 0, 1, prime, defer);
         return;
     }
     b_scan_apply(K, B, blockIdx.x, gridDim.x - kin);
@@ -2315,10 +2428,12 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_pass_staged(Co
     b_pass_staged<CL, SV>(K, B, blockIdx.x, prime);
 }
 
+// mode: b_finalize's (0 at the end of the step, 1 deferred to the next
+// step's graph, 2 the host's settling of a deferred close)
 template <int CL>
-__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime, int split)
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(Consts K, Bufs B, int prime, int split, int mode)
 {
-    b_finalize<CL>(K, B, blockIdx.x, gridDim.x, prime, split);
+    b_finalize<CL>(K, B, blockIdx.x, gridDim.x, prime, split, mode);
 }
 
 // --------------------------------------------- kernels (a batch of cases)

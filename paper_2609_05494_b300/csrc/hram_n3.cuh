@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kN3Threads, 6) k_pass_n3(Consts K, Bufs B, int
         const int stride = (gridDim.x - n_tiles) * kN3Threads;
         for (int q = fz + (t - n_tiles) * kN3Threads + tid; q < K.nf; q += stride)
             pass_frozen<0>(B, q, B.s_vel[q], B.s_rd[q]);
-        pass_block_partials<kN3Threads>(B.part, t, P);
+        pass_block_partials<kN3Threads>(B.part, t, P, &B.S->vmax_bits);
         return;
     }
     const int epoch = B.n3_ctl[1];
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kN3Threads, 6) k_pass_n3(Consts K, Bufs B, int
         pass_finish<0>(K, B, i, ri, vi, ai, rd, c, dt, prime, I, A, P);
         P.diss += K.m * K.m * dissf;
     }
-    pass_block_partials<kN3Threads>(B.part, t, P);
+    pass_block_partials<kN3Threads>(B.part, t, P, &B.S->vmax_bits);
 }
 
 }  // namespace hr
