@@ -16,6 +16,12 @@
 //   k_pass           fused interaction sums L + closing kick epilogue
 //   k_finalize       probes, FP64 accumulators, CFL gate           [T, gate]
 //
+// By default a step graph leaves the step's close (b_finalize) pending and
+// the next step's graph runs it in the first blocks of its drift launch
+// (k_close_drift), the drift taking its dt from the last pass's max |v|;
+// k_finalize then only settles a close the host needs before it reads the
+// case.
+//
 // Densities are carried as the relative deviation d = rho/rho0 - 1 in FP32:
 // the Tait pressure B((1+d)^7 - 1) = B d (7 + 21 d + ...) then has no
 // cancellation and a pressure of 100 Pa is resolved (an FP32 rho near 1000
