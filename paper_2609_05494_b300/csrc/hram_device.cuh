@@ -867,10 +867,9 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
 // unless a cell holds more than kBucket particles), for the cells [c0, c1)
 // whose starts this block has just written: each ID goes to perm_tmp at its
 // cell's start + its slot, where the reorder reads it.
-__device__ __forceinline__ void scan_overflow(const Consts &K, const Bufs &B, int c0, int c1)
+__device__ __forceinline__ void scan_overflow(const Consts &K, const Bufs &B, int c0, int c1, int no)
 {
     __syncthreads();   // this block's cell starts are written
-    const int no = *B.ovf_count;
     for (int k = threadIdx.x; k < no; k += blockDim.x) {
         const int4 e = B.ovf[k];
         if (e.x < c0 || e.x >= c1) continue;
@@ -883,13 +882,21 @@ __device__ __forceinline__ void scan_overflow(const Consts &K, const Bufs &B, in
 // Cell starts: each block adds up the sums of the tiles before it (counted
 // by k_drift_key), then an exclusive scan of its own tile, and places its
 // cells' overflowing IDs; the counts are reset for the next step (the tile
-// sums in k_rank_scatter, once every block here has read them).
+// sums in k_rank_scatter, once every block here has read them).  The tile's
+// counts, the tile sums and the overflow count are all loaded before the
+// first barrier, in one round trip.
 __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
     __shared__ int wsum[kScanThreads / 32];
     __shared__ int offset;
+    const int n = K.ncell + 1;
+    const int base = bx * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
     int o = 0;
     for (int t = threadIdx.x; t < (int)bx; t += blockDim.x) o += B.tile_sum[t];
+    const int no = *B.ovf_count;
     o = warp_sum(o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = o;
     __syncthreads();
@@ -899,15 +906,9 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
         offset = t;
     }
     __syncthreads();
-    const int n = K.ncell + 1;
-    const int base = bx * kScanTile + threadIdx.x * kScanItems;
-    int v[kScanItems];
     int s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     int total;
     int ex = block_exclusive_scan(s, wsum, &total) + offset;
 #pragma unroll
@@ -919,7 +920,7 @@ __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, con
         ex += v[k];
     }
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
-    scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n));
+    if (no > 0) scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n), no);
 }
 
 // The Newton-3 pass's tile table: chunks of kN3Threads particles of each

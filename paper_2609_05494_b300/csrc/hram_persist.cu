@@ -113,7 +113,7 @@ __device__ __forceinline__ void scan_tile(const Consts &K, const Bufs &B, int bx
         ex += v[k];
     }
     if (base <= n && n < base + kItems) B.cell_start[n] = K.nf;
-    scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n));
+    scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n), *B.ovf_count);
     __syncthreads();
 }
 
