@@ -492,7 +492,10 @@ __device__ __forceinline__ float cfl_dt_f(const Consts &K, float vmax)
 // The deferred step close: the next step's size from the last pass's max |v|
 // (Scalars::vmax_bits), into the fields the close at the end of a step
 // writes (dt_prev, dt, dt_f, ratio_f), with the same arithmetic.  One thread.
-__device__ __forceinline__ void advance_dt(const Consts &K, Scalars *S)
+// vbits, dtf_old, dt_old: the scalars' vmax_bits, dt_f and dt as read by the
+// caller; returns the new dt.
+__device__ __forceinline__ double advance_dt(const Consts &K, Scalars *S, unsigned vbits, float dtf_old,
+                                             double dt_old)
 {
     double dtn;
     float dtf;
@@ -500,15 +503,16 @@ __device__ __forceinline__ void advance_dt(const Consts &K, Scalars *S)
         dtn = K.dt_fixed;
         dtf = (float)dtn;
     } else {
-        dtf = cfl_dt_f(K, __uint_as_float(S->vmax_bits));
+        dtf = cfl_dt_f(K, __uint_as_float(vbits));
         dtn = (double)dtf;
     }
     if (!(dtn > 1e-14)) atomicOr(&S->status, ST_DT);
-    S->ratio_f = __fdiv_rn(dtf, S->dt_f);
-    S->dt_prev = S->dt;
+    S->ratio_f = __fdiv_rn(dtf, dtf_old);
+    S->dt_prev = dt_old;
     S->dt = dtn;
     S->dt_f = dtf;
     S->dt_stale = 0;
+    return dtn;
 }
 
 // Projectile kinematics in closed form (FP64).  Section 2.6.3 ramp,
@@ -824,26 +828,36 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
                                              int defer = 0)
 {
     __shared__ double kin[2];
+    // the ring offsets of the first pass below, loaded before the barrier
+    const double2 off0 = (int)threadIdx.x < K.ng ? B.disk_off[threadIdx.x] : make_double2(0.0, 0.0);
     if (threadIdx.x == 0) {
         Scalars *S = B.S;
+        // every scalar read here, loaded before any is written
+        const int stale = defer ? S->dt_stale : 0;
+        const unsigned vbits = S->vmax_bits;
+        const float dtf_old = S->dt_f;
+        const double dt_old = S->dt, t_old = S->t;
+        const double Fdx = S->Fdx, vproj = S->vproj, xc = S->xc;
+        double dt_now = dt_old;
         if (defer) {
-            if (S->dt_stale) advance_dt(K, S);
+            if (stale) dt_now = advance_dt(K, S, vbits, dtf_old, dt_old);
             S->vmax_bits = 0u;
             S->close_pending = 1;
             S->dt_stale = 1;
         }
-        const double dt = prime ? 0.0 : S->dt;
-        S->t += dt;
+        const double dt = prime ? 0.0 : dt_now;
+        const double t = t_old + dt;
+        S->t = t;
         double x, v, a;
-        if (K.motion == 3 && !prime && !(K.t_ramp > 0.0 && S->t <= K.t_ramp)) {
+        if (K.motion == 3 && !prime && !(K.t_ramp > 0.0 && t <= K.t_ramp)) {
             // two-way coupling (the extension named in the paper's
             // Conclusions): M' dv/dt = -F_x, F the disk ghosts' force on the
             // fluid from the last interaction pass; symplectic Euler in FP64
-            a = -S->Fdx / K.disk_mass;
-            v = S->vproj + dt * a;
-            x = S->xc + dt * v;
+            a = -Fdx / K.disk_mass;
+            v = vproj + dt * a;
+            x = xc + dt * v;
         } else {
-            kinematics(K, S->t, &x, &v, &a);
+            kinematics(K, t, &x, &v, &a);
         }
         S->xc = x;
         S->yc = K.y_c0;
@@ -858,7 +872,7 @@ __device__ __forceinline__ void b_kinematics(const Consts &K, const Bufs &B, con
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K.ng; k += blockDim.x) {
-        const double2 o = B.disk_off[k];
+        const double2 o = k == (int)threadIdx.x ? off0 : B.disk_off[k];
         B.gd_pos[k] = make_float2((float)(kin[0] + o.x), (float)(kin[1] + o.y));
     }
 }
@@ -2108,7 +2122,9 @@ template <int CL, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const int bx, const int nbx, int prime,
                                            int split = 0, int mode = 0)
 {
-    if (mode != 0 && !__ldcg(&B.S->close_pending)) return;   // nothing deferred
+    // (a deferred close returns before its first write when none is pending;
+    // the flag is loaded with its first reads, not before them)
+    const int pend = mode == 0 ? 1 : __ldcg(&B.S->close_pending);
     constexpr int NW = kFinalizeThreads / 32;
     __shared__ F2 redd[4][NW];
     __shared__ float redv[NW];
@@ -2162,16 +2178,14 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         __syncthreads();
     };
     if (probe_block) {
-        if (w == 0) {
-            const int q = bx - nb;
-            if (!prime) {
-                const float pv = probe_value<CL>(K, B, K.probe_x[q], K.probe_y[q]);
-                if (lane == 0) B.probe_now[q] = pv;
-            }
-            if (lane == 0) {
-                __threadfence();
-                is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
-            }
+        const int q = bx - nb;
+        float pv = 0.0f;
+        if (w == 0 && !prime) pv = probe_value<CL>(K, B, K.probe_x[q], K.probe_y[q]);
+        if (!pend) return;
+        if (w == 0 && lane == 0) {
+            if (!prime) B.probe_now[q] = pv;
+            __threadfence();
+            is_last = atomicAdd(B.fin_ticket, 1) == nbx - 1;
         }
     } else if (SKIP_EMPTY && bx * (int)blockDim.x >= max(K.n_pass_blocks, K.n_ghost_blocks)) {
         // a slice past every partial: its sums are zero (what the reduction
@@ -2217,6 +2231,7 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
                  b += nb * blockDim.x)
                 vmax = fmaxf(vmax, B.ghost_vmax[b]);
         block_reduce(a0, a1, a2, a3, vmax, npen);
+        if (!pend) return;
         if (threadIdx.x == 0) {
             for (int k = 0; k < 4; ++k) {
                 B.fin_part[bx * 8 + 2 * k] = tot[k].hi;
@@ -2335,7 +2350,7 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
         const int bits = S.status & (ST_PENETRATION | ST_PROBEFULL);
         if (bits) atomicOr(&G->status, bits);
         G->close_pending = 0;
-        if (mode == 2) advance_dt(K, G);
+        if (mode == 2) advance_dt(K, G, G->vmax_bits, G->dt_f, G->dt);
     }
 }
 
