@@ -285,7 +285,9 @@ int hr_debug_neighbors(hr_case *c, int64_t *offsets, int32_t *ids, int64_t cap,
                        int64_t *n_pairs);
 
 /* Durations (ms) of the last replayed step's kernel groups when the case was
- * created with HR_FLAG_TIMING: drift, sort, ghost, pass, finalize. */
+ * created with HR_FLAG_TIMING: drift, sort, ghost, pass, finalize.  With the
+ * deferred close (no HR_FLAG_CLOSE_INLINE) the drift group holds the previous
+ * step's close and the finalize group is empty. */
 int hr_kernel_times(hr_case *c, float *ms, int n);
 
 /* Checkpoint / resume of the full state (positions, velocities, densities,

@@ -637,6 +637,21 @@ void make_consts(hr_case *c)
                              : 0.0;
     K.dt_mode = P.dt_mode;
     K.motion = P.motion;
+    // motion 0 (ramp, then exponential decay with tau > 0): after the ramp
+    // x(t) = x_c0 + (v0/t_r)(tau^2 - tau (t_r + tau) E) + v0 tau (E - e(t)),
+    // E = exp(-t_r/tau), e(t) = exp(-t/tau) (without a ramp: x_c0 + v0 tau (1 - e))
+    K.m2d = (double)K.m * (double)K.m;
+    K.kin_fast = P.motion == 0 && P.tau > 0.0 ? 1 : 0;
+    if (K.kin_fast) {
+        const double tr = P.t_ramp > 0.0 ? P.t_ramp : 0.0, tau = P.tau;
+        const double E = tr > 0.0 ? std::exp(-tr / tau) : 1.0;
+        K.kin_inv_tau = 1.0 / tau;
+        K.kin_q = P.v0 * tau;
+        K.kin_x1 = P.x_c0 + (tr > 0.0 ? (P.v0 / tr) * (tau * tau - tau * (tr + tau) * E) : 0.0) +
+                   K.kin_q * E;
+    } else {
+        K.kin_inv_tau = K.kin_x1 = K.kin_q = 0.0;
+    }
     K.n_probes = P.n_probes;
     for (int k = 0; k < P.n_probes; ++k) {
         K.probe_x[k] = (float)P.probe_xy[2 * k];

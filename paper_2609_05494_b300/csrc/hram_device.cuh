@@ -105,6 +105,12 @@ struct Consts {
     int sr;                 // stencil reach in cells: 1 (cells of side >= 2h, 3 x 3) or 2 (side >= h, 5 x 5)
     int n3, n3_tiles_max;   // the Newton-3 pass variant, and its tile capacity
     int split;              // the interaction pass runs split (interior / boundary particles)
+    // motion 0 with tau > 0 after the ramp: x(t) = kin_x1 - kin_q e, v = v0 e,
+    // a = -v0 e / tau, e = exp(-t kin_inv_tau), the t-independent parts of the
+    // closed form formed once on the host (kin_fast)
+    int kin_fast;
+    double kin_inv_tau, kin_x1, kin_q;
+    double m2d;             // (double) m * (double) m, the step close's scale of the force sums
 };
 
 // Device-resident scalars of the case.
@@ -522,6 +528,16 @@ __device__ __forceinline__ double advance_dt(const Consts &K, Scalars *S, unsign
 // by the fluid force in b_kinematics (two-way coupling).
 __device__ inline void kinematics(const Consts &K, double t, double *xo, double *vo, double *ao)
 {
+    if (K.kin_fast && !(K.t_ramp > 0.0 && t < K.t_ramp)) {
+        // motion 0 after the ramp: one exponential per step (an FP64 operation
+        // holds a warp's issue for many cycles on this GPU, and this chain is
+        // the longest block of the scan launch)
+        const double e = exp(-t * K.kin_inv_tau);
+        *vo = K.v0 * e;
+        *ao = K.v0 * (-e * K.kin_inv_tau);
+        *xo = K.kin_x1 - K.kin_q * e;
+        return;
+    }
     const double v0 = K.v0, tr = K.t_ramp, tau = K.motion == 3 ? 0.0 : K.tau;
     double x = K.x_c0, v, a;
     if (K.motion == 2) {
@@ -901,37 +917,67 @@ __device__ __forceinline__ void scan_overflow(const Consts &K, const Bufs &B, in
 // first barrier, in one round trip.
 __device__ __forceinline__ void b_scan_apply(const Consts &K, const Bufs &B, const int bx, const int nbx)
 {
-    __shared__ int wsum[kScanThreads / 32];
+    static_assert(kScanItems == 4 && kScanThreads == 1024, "one int4 of counts per thread, 32 warps");
+    __shared__ int wsum[32];
     __shared__ int offset;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int n = K.ncell + 1;
     const int base = bx * kScanTile + threadIdx.x * kScanItems;
+    const bool whole = base + kScanItems <= n;   // (the arrays are 16-byte aligned)
     int v[kScanItems];
+    if (whole) {
+        const int4 q = *reinterpret_cast<const int4 *>(B.cell_count + base);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
+        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? B.cell_count[base + k] : 0;
+    }
     int o = 0;
     for (int t = threadIdx.x; t < (int)bx; t += blockDim.x) o += B.tile_sum[t];
     const int no = *B.ovf_count;
+    // the warp's inclusive scan of the thread sums, and its part of the tile sums
+    const int s = v[0] + v[1] + v[2] + v[3];
+    int x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
     o = warp_sum(o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = o;
+    __shared__ int wtile[32];
+    if (lane == 31) wsum[w] = x;
+    if (lane == 0) wtile[w] = o;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int k = 0; k < kScanThreads / 32; ++k) t += wsum[k];
-        offset = t;
+    if (w == 0) {
+        // inclusive scan of the warp totals, plus the tiles before this one
+        int t = wsum[lane];
+        const int tt = warp_sum(wtile[lane]);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        wsum[lane] = t + tt;
+        if (lane == 0) offset = tt;
     }
     __syncthreads();
-    int s = 0;
+    int ex = (w > 0 ? wsum[w - 1] : offset) + x - s;
+    if (whole) {
+        const int e0 = ex, e1 = e0 + v[0], e2 = e1 + v[1], e3 = e2 + v[2];
+        *reinterpret_cast<int4 *>(B.cell_start + base) = make_int4(e0, e1, e2, e3);
+        *reinterpret_cast<int4 *>(B.cell_count + base) = make_int4(0, 0, 0, 0);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) s += v[k];
-    int total;
-    int ex = block_exclusive_scan(s, wsum, &total) + offset;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) {
-            B.cell_start[base + k] = ex;
-            B.cell_count[base + k] = 0;
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < n) {
+                B.cell_start[base + k] = ex;
+                B.cell_count[base + k] = 0;
+            }
+            ex += v[k];
         }
-        ex += v[k];
     }
     if (base <= n && n < base + kScanItems) B.cell_start[n] = K.nf;
     if (no > 0) scan_overflow(K, B, bx * kScanTile, min((bx + 1) * kScanTile, n), no);
@@ -2267,7 +2313,15 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     // the step's own dt and index, read by every thread before any update
     const double dt = S.dt;
     const long long k = S.step;
-    const double m2 = (double)K.m * (double)K.m;
+    // the four global sums in FP64, one per lane of warp 0 (an FP64
+    // operation holds its warp's issue for many cycles on this GPU, so
+    // threads 0 and 32 below take them formed)
+    __shared__ double sum4[4];
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        const double v = (double)tot[q].hi + (double)tot[q].lo;
+        sum4[q] = q < 3 ? K.m2d * v : v;
+    }
     __syncthreads();
     if (K.split) {
         // every block has read the marks: clear them and the lists
@@ -2279,10 +2333,10 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     }
     if (threadIdx.x == 0) {
         *B.fin_ticket = 0;
-        S.Fdx = m2 * ((double)tot[0].hi + (double)tot[0].lo);
-        S.Fdy = m2 * ((double)tot[1].hi + (double)tot[1].lo);
-        S.Fwall = m2 * ((double)tot[2].hi + (double)tot[2].lo);
-        S.diss_rate = (double)tot[3].hi + (double)tot[3].lo;
+        S.Fdx = sum4[0];
+        S.Fdy = sum4[1];
+        S.Fwall = sum4[2];
+        S.diss_rate = sum4[3];
         if (totn > 0) S.status |= ST_PENETRATION;
         if (!prime) {
             if (k < K.probe_cap) {
@@ -2315,10 +2369,9 @@ __device__ __forceinline__ void b_finalize(const Consts &K, const Bufs &B, const
     } else if (threadIdx.x == 32) {
         // the FP64 time integrals, beside thread 0 (another warp)
         if (!prime) {
-            const double F0 = m2 * ((double)tot[0].hi + (double)tot[0].lo);
-            S.Wb += dt * (F0 * S.vproj);
-            S.impulse += dt * (m2 * ((double)tot[2].hi + (double)tot[2].lo));
-            S.diss += dt * ((double)tot[3].hi + (double)tot[3].lo);
+            S.Wb += dt * (sum4[0] * S.vproj);
+            S.impulse += dt * sum4[2];
+            S.diss += dt * sum4[3];
         }
     } else if (threadIdx.x >= 64 && threadIdx.x < 64 + K.n_probes) {
         // one probe per thread: its history entry and its impulse
