@@ -966,8 +966,10 @@ cudaError_t launch_prio(void (*kern)(KArgs...), int grid, int block, cudaStream_
 // pass: after the reorder (and the summed density), the boundary lists, the
 // ghost pass and the boundary particles' pass and partials run on a
 // high-priority branch while the interior particles' pass runs on the main
-// stream; both join before k_finalize.  (With HR_FLAG_TIMING the "ghost"
-// group is then empty and the "pass" group holds both branches.)
+// stream; both join before the step's close.  (With HR_FLAG_TIMING the
+// "ghost" group is then empty and the "pass" group holds both branches.)
+// defer: the step's close is left to the next step's drift launch
+// (k_close_drift) or to settle(); otherwise k_finalize ends the step.
 int launch_step(hr_case *c, cudaStream_t s, int prime, bool with_events, cudaStream_t side,
                 bool defer = false)
 {
