@@ -117,9 +117,11 @@ def test_deferred_close_save_load_and_set_state():
     _same(a, b)
 
 
-def test_deferred_close_then_batch_and_back():
-    # a case with a pending close taken into a batch continues as the
-    # inline-closed case does, and steps alone again after
+@pytest.mark.parametrize("persistent", [False, True])
+def test_deferred_close_then_batch_and_back(persistent):
+    # a case with a pending close taken into a batch (a graph of batched
+    # launches, or one persistent launch) continues as the inline-closed
+    # case does, and steps alone again after
     p, xy = impact_case()
     a = Case(p, xy, close_inline=True)
     b = Case(p, xy)
@@ -128,7 +130,7 @@ def test_deferred_close_then_batch_and_back():
         c.step()
     t_end = a.scalars()["t"] + 2e-6
     for c in (a, b):
-        with Batch([c], t_end) as bt:
+        with Batch([c], t_end, persistent=persistent) as bt:
             bt.run()
         c.run(5)
     _same(a, b)
