@@ -94,6 +94,8 @@ struct ABufs {
     float2 *sums;            // ka_reduce's block sums (two-float) [kAReduceBlocks x kASums]
     double *sc;              // ASC_* accumulators
     int *status;             // the case's status word (bounds-checked build)
+    double *cpart;           // ka_close's warp sums [kAReduceBlocks / 32 x kASums]
+    int *ctick;              // ka_close's ticket (0 between launches)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -929,7 +931,7 @@ __global__ void ka_kin(Consts K, const Scalars *S, double *kin)
     kin[5] = ak.d[2];
 }
 
-// Closes the step's reverse sweep (one block of kAReduceBlocks threads):
+// Closes the step's reverse sweep (kASums blocks of kAReduceBlocks threads):
 // adds the ka_reduce sums in a fixed order (thread b reads block b's sums;
 // FP64 across the block), transposes the disk kinematics at t^{n+1} (x_c,
 // v_w, a_w as functions of t and tau, from the tangent's FP64 duals),
@@ -938,39 +940,52 @@ __global__ void ka_kin(Consts K, const Scalars *S, double *kin)
 __global__ void __launch_bounds__(kAReduceBlocks) ka_close(Consts K, Bufs B, ABufs A, int prime,
                                                           const float2 *sums, const double *kin)
 {
-    __shared__ double red[kAReduceBlocks / 32][kASums];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int e = 0; e < kASums; ++e) {
+    // One block per sum e (kASums blocks): its warps form the FP64 lane sums
+    // of e over the kAReduceBlocks partials; the block that finishes last
+    // (atomic ticket) adds them across warps, one lane per sum, and closes
+    // the two components on two lanes.  (An FP64 instruction holds its warp
+    // for many cycles on this GPU; spread over blocks and lanes the same
+    // additions, in the same order, take a fraction of the time.)
+    __shared__ int last;
+    __shared__ double tot[kASums];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, e = blockIdx.x;
+    {
         const float2 v = sums[threadIdx.x * kASums + e];
         const double x = lane_sum((double)v.x + (double)v.y);
-        if (lane == 0) red[w][e] = x;
+        if (lane == 0) A.cpart[w * kASums + e] = x;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double tot[kASums];
-    for (int e = 0; e < kASums; ++e) {
-        double v = 0.0;
-        for (int k = 0; k < kAReduceBlocks / 32; ++k) v += red[k][e];
-        tot[e] = v;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(A.ctick, 1) == (int)gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < kASums) {
+        double v = 0.0;
+        for (int k = 0; k < kAReduceBlocks / 32; ++k) v += __ldcg(&A.cpart[k * kASums + threadIdx.x]);
+        tot[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *A.ctick = 0;
+    if (threadIdx.x >= kOut) return;
     double *sc = A.sc;
     // kinematics derivatives at this step's time (t^{n+1}; 0 for the priming
-    // pass), formed by ka_kin when the step was recorded
-    for (int c = 0; c < kOut; ++c) {
-        const double *q = tot + c * 6;
-        sc[ASC_ALPHA + c] += q[0];
-        sc[ASC_C0 + c] += q[1];
-        double dtb = q[2];
-        const double xb = q[3], vb = q[4], ab = q[5];
-        if (K.ng > 0) sc[ASC_TAU + c] += xb * kin[3] + vb * kin[4] + ab * kin[5];
-        if (!prime) {
-            if (K.ng > 0) sc[ASC_TBAR + c] += xb * kin[0] + vb * kin[1] + ab * kin[2];
-            dtb += sc[ASC_TBAR + c];
-            if (c == 1) dtb += B.S->Fwall;   // J = sum_n dt F_wall^{n+1}
-        }
-        sc[ASC_DT + c] += dtb;
+    // pass), formed by ka_kin when the step was recorded; component c on lane c
+    const int c = threadIdx.x;
+    const double *q = tot + c * 6;
+    sc[ASC_ALPHA + c] += q[0];
+    sc[ASC_C0 + c] += q[1];
+    double dtb = q[2];
+    const double xb = q[3], vb = q[4], ab = q[5];
+    if (K.ng > 0) sc[ASC_TAU + c] += xb * kin[3] + vb * kin[4] + ab * kin[5];
+    if (!prime) {
+        if (K.ng > 0) sc[ASC_TBAR + c] += xb * kin[0] + vb * kin[1] + ab * kin[2];
+        dtb += sc[ASC_TBAR + c];
+        if (c == 1) dtb += B.S->Fwall;   // J = sum_n dt F_wall^{n+1}
     }
+    sc[ASC_DT + c] += dtb;
 }
 
 // The uploaded state in fluid-ID order, rebuilt from the primed state (the

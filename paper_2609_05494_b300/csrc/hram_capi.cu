@@ -1381,6 +1381,8 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     const size_t bk = Lo.add((size_t)a->bk_blocks * kOut * 16);
     const size_t sums = Lo.add((size_t)kAReduceBlocks * kASums * 8);
     const size_t sc = Lo.add(ASC_N * 8);
+    const size_t cpart = Lo.add((size_t)(kAReduceBlocks / 32) * kASums * 8);
+    const size_t ctick = Lo.add(4);
     a->bytes = Lo.total;
     if (cudaMalloc(&a->mem, a->bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1446,6 +1448,8 @@ int adj_alloc(hr_case *c, long long n_steps, int L)
     A.sums = at<float2>(w, sums);
     A.sc = at<double>(w, sc);
     A.status = &c->B.S->status;
+    A.cpart = at<double>(w, cpart);
+    A.ctick = at<int>(w, ctick);
     return HR_OK;
 }
 
@@ -1552,7 +1556,7 @@ int adjoint_step(hr_case *c, cudaStream_t s, const Slot &cur, const Slot &prev, 
     ka_back<<<a->bk_blocks, kAThreads, 0, s>>>(K, Bc, Bp, a->A, prime);
     ka_reduce<<<kAReduceBlocks, kAReduceThreads, 0, s>>>(K, a->A, a->ep_blocks, a->bk_blocks,
                                                           a->A.sums);
-    ka_close<<<1, kAReduceBlocks, 0, s>>>(K, Bc, a->A, prime, a->A.sums, cur.kin);
+    ka_close<<<kASums, kAReduceBlocks, 0, s>>>(K, Bc, a->A, prime, a->A.sums, cur.kin);
     CK(cudaGetLastError());
     std::swap(a->A.cur, a->A.prv);
     return HR_OK;
@@ -2281,6 +2285,7 @@ int hr_adjoint_backward(hr_case *c, double *out, int n)
     for (float2 *p : {z.r, z.v, z.a, z.X}) CK(cudaMemsetAsync(p, 0, nq * 8, s));
     for (float *p : {z.d, z.D, z.E}) CK(cudaMemsetAsync(p, 0, nq * 4, s));
     CK(cudaMemsetAsync(a->A.sc, 0, ASC_N * 8, s));
+    CK(cudaMemsetAsync(a->A.ctick, 0, 4, s));
     const long long N = a->n_steps;
     const int L = a->L;
     int rc;
