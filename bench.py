@@ -914,9 +914,13 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # the interaction pass runs split at this size (interior particles beside
-    # the ghost pass, boundary particles after it): 8 launches per step, else 6
+    # the ghost pass, boundary particles after it): close + drift, scan,
+    # reorder, ghost, boundary pass and sums, interior pass = 7 launches per
+    # step (5 unsplit); the step's close runs in the next step's drift launch
+    # (one launch more per step when a case closes inline)
     split = bool(case.info()["split"])
-    launches_per_step = 8 if split else 6
+    deferred = bool(case.info()["close_deferred"])
+    launches_per_step = (7 if split else 5) + (0 if deferred else 1)
     # pairs per step (for the flop count), from the neighbour lists of the start state
     off, _ = case.neighbours()
     pairs_fluid_rows = int(off[n] - off[0])
